@@ -1,0 +1,183 @@
+"""Tight-binding lattices and Hamiltonians for the FP64 oracle.
+
+The paper's operator is a sparse tight-binding Hamiltonian H with nearest-neighbour
+hopping t and on-site terms (Sec. II.B defines its density D_H as the mean number
+of non-zeros per row; Fig. 1 uses nearest-neighbour graphene).  The paper prints no
+lattice code, so the site numbering, neighbour order, disorder and vacancy rules
+below are this library's own convention, fixed bit for bit by golden files:
+
+* square  Lx x Ly:  site i = y*Lx + x; neighbours (x+1,y), (x-1,y), (x,y+1), (x,y-1).
+* honeycomb Lx x Ly cells: site i = 2*(y*Lx + x) + s, s=0 (A) or 1 (B).
+  A(x,y) bonds to B(x,y), B(x-1,y), B(x,y-1);  B(x,y) bonds to A(x,y), A(x+1,y), A(x,y+1).
+* simple cubic Lx x Ly x Lz: site i = (z*Ly + y)*Lx + x; neighbours +-x, +-y, +-z.
+Periodic directions wrap by modulo; open directions drop the bond.
+H_ij = t for every bond (bonds that coincide under wrapping add up), H_ii = V_i.
+
+Anderson disorder: V_i = W * ((u >> 8) * 2^-24 - 1/2), u = Philox draw of site i in the
+disorder stream, so V_i is uniform on [-W/2, W/2).  Vacancies: site i is removed when
+its vacancy-stream draw u < floor(p * 2^32).  Active sites are renumbered in order.
+
+Spectral bounds (the paper takes H0 and |H| "typically" from Lanczos, Sec. II.A; the
+reading used here is Gershgorin, which never underestimates):
+    E_max = max_i (V_i + deg_i |t|),  E_min = min_i (V_i - deg_i |t|)
+    H0 = (E_max + E_min) / 2,  |H| = (1 + 0.01) (E_max - E_min) / 2.
+
+Part of the FP64 oracle: test infrastructure only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from .philox import draw_u32, STREAM_DISORDER, STREAM_VACANCY
+
+SQUARE, HONEYCOMB, CUBIC = 0, 1, 2
+COORDINATION = {SQUARE: 4, HONEYCOMB: 3, CUBIC: 6}
+BOUND_MARGIN = 0.01
+
+
+def full_site_count(kind: int, L) -> int:
+    Lx, Ly, Lz = L
+    if kind == SQUARE:
+        return Lx * Ly
+    if kind == HONEYCOMB:
+        return 2 * Lx * Ly
+    if kind == CUBIC:
+        return Lx * Ly * Lz
+    raise ValueError(f"unknown lattice kind {kind}")
+
+
+def _wrap(v, n, periodic):
+    """Coordinate v in [-1, n] mapped into the box; -1 marks a dropped (open) bond."""
+    if periodic:
+        return np.mod(v, n), np.ones_like(v, dtype=bool)
+    ok = (v >= 0) & (v < n)
+    return np.where(ok, v, 0), ok
+
+
+def neighbour_table(kind: int, L, pbc) -> np.ndarray:
+    """int64 array [n_full, z] of neighbour site indices in the fixed neighbour order;
+    -1 where an open boundary drops the bond."""
+    Lx, Ly, Lz = L
+    n = full_site_count(kind, L)
+    i = np.arange(n, dtype=np.int64)
+    cols = []
+    if kind == SQUARE:
+        x, y = i % Lx, i // Lx
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            xx, okx = _wrap(x + dx, Lx, pbc[0])
+            yy, oky = _wrap(y + dy, Ly, pbc[1])
+            cols.append(np.where(okx & oky, yy * Lx + xx, -1))
+    elif kind == HONEYCOMB:
+        s, c = i % 2, i // 2
+        x, y = c % Lx, c // Lx
+        # (dx, dy) to the partner cell for A (s=0) and for B (s=1)
+        for (dxa, dya), (dxb, dyb) in (((0, 0), (0, 0)), ((-1, 0), (1, 0)), ((0, -1), (0, 1))):
+            dx = np.where(s == 0, dxa, dxb)
+            dy = np.where(s == 0, dya, dyb)
+            xx, okx = _wrap(x + dx, Lx, pbc[0])
+            yy, oky = _wrap(y + dy, Ly, pbc[1])
+            cols.append(np.where(okx & oky, 2 * (yy * Lx + xx) + (1 - s), -1))
+    elif kind == CUBIC:
+        x, y, z = i % Lx, (i // Lx) % Ly, i // (Lx * Ly)
+        for dx, dy, dz in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+            xx, okx = _wrap(x + dx, Lx, pbc[0])
+            yy, oky = _wrap(y + dy, Ly, pbc[1])
+            zz, okz = _wrap(z + dz, Lz, pbc[2])
+            cols.append(np.where(okx & oky & okz, (zz * Ly + yy) * Lx + xx, -1))
+    else:
+        raise ValueError(f"unknown lattice kind {kind}")
+    return np.stack(cols, axis=1).astype(np.int64)
+
+
+def disorder_potential(seed: int, W: float, n_full: int) -> np.ndarray:
+    """Anderson on-site energies V_i, uniform on [-W/2, W/2), FP64, by full site index."""
+    u = draw_u32(seed, np.arange(n_full, dtype=np.uint64), STREAM_DISORDER).astype(np.float64)
+    frac = np.floor(u / 256.0) * 2.0 ** -24          # (u >> 8) * 2^-24, exact
+    return W * (frac - 0.5)
+
+
+def vacancy_threshold(p: float) -> int:
+    return int(np.floor(np.float64(p) * 4294967296.0))
+
+
+def vacancy_mask(seed: int, p: float, n_full: int) -> np.ndarray:
+    """True where the site is removed."""
+    if p <= 0.0:
+        return np.zeros(n_full, dtype=bool)
+    u = draw_u32(seed, np.arange(n_full, dtype=np.uint64), STREAM_VACANCY).astype(np.int64)
+    return u < vacancy_threshold(p)
+
+
+@dataclass
+class Lattice:
+    kind: int
+    L: tuple
+    pbc: tuple
+    t: float
+    W: float
+    vacancy_frac: float
+    seed: int
+    n_full: int
+    nbr_full: np.ndarray      # [n_full, z] full-index neighbours (-1 = none)
+    active: np.ndarray        # [n_full] bool
+    compact: np.ndarray       # [n_full] compact index or -1
+    V: np.ndarray             # [n_active] FP64 on-site energies
+    H: sp.csr_matrix          # [n_active, n_active] FP64
+    degree: np.ndarray        # [n_active] bonds to active sites
+    E_min: float
+    E_max: float
+    H0: float
+    half_width: float
+
+    @property
+    def n(self) -> int:
+        return int(self.V.shape[0])
+
+
+def build_lattice(kind: int, L, t: float, W: float = 0.0, vacancy_frac: float = 0.0,
+                  seed: int = 0, pbc=(1, 1, 1)) -> Lattice:
+    L = tuple(int(v) for v in L) + (1,) * (3 - len(L))
+    pbc = tuple(bool(v) for v in pbc) + (True,) * (3 - len(pbc))
+    n_full = full_site_count(kind, L)
+    nbr = neighbour_table(kind, L, pbc)
+    vac = vacancy_mask(seed, vacancy_frac, n_full)
+    active = ~vac
+    compact = np.full(n_full, -1, dtype=np.int64)
+    compact[active] = np.arange(int(active.sum()), dtype=np.int64)
+    V_full = disorder_potential(seed, W, n_full) if W != 0.0 else np.zeros(n_full)
+
+    rows, cols = [], []
+    full_idx = np.flatnonzero(active)
+    for k in range(nbr.shape[1]):
+        j = nbr[full_idx, k]
+        keep = j >= 0
+        keep[keep] &= active[j[keep]]
+        rows.append(compact[full_idx[keep]])
+        cols.append(compact[j[keep]])
+    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+    n = full_idx.size
+    V = V_full[full_idx].astype(np.float64)
+    hop = sp.coo_matrix((np.full(rows.size, float(t)), (rows, cols)), shape=(n, n)).tocsr()
+    H = (hop + sp.diags(V)).tocsr()
+    H.sum_duplicates()
+    degree = np.bincount(rows, minlength=n).astype(np.int64)
+
+    if n == 0:
+        raise ValueError("lattice has no active sites")
+    E_max = float(np.max(V + degree * abs(t)))
+    E_min = float(np.min(V - degree * abs(t)))
+    if not E_max > E_min:
+        raise ValueError("degenerate spectrum: no hopping")
+    H0 = (E_max + E_min) / 2.0
+    half = (1.0 + BOUND_MARGIN) * (E_max - E_min) / 2.0
+    return Lattice(kind, L, pbc, float(t), float(W), float(vacancy_frac), int(seed), n_full,
+                   nbr, active, compact, V, H, degree, E_min, E_max, H0, half)
+
+
+def rescaled_apply(lat: Lattice, x: np.ndarray) -> np.ndarray:
+    """H~ x with H~ = (H - H0) / |H| (Sec. II.A)."""
+    return (lat.H @ x - lat.H0 * x) / lat.half_width
