@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark of the concurrent Chebyshev propagation hot path on GB300.
+
+Default workload: graphene honeycomb 2048 x 2048 cells (8,388,608 sites), t = -2.7 eV, clean,
+8 random-phase complex64 states with FP64 moment reductions, 4096 Chebyshev moments by the
+moment-based concurrent form with the cost-halving identity (2048 matrix applications), and the
+Jackson DOS on 8192 energies.  One step = lattice build + states + recurrence with fused moments
++ reconstruction, through the C ABI.
+
+Metric: site-updates/s, one site-update = one Chebyshev recurrence step applied to one site of one
+state.  Printed as one JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+WORKLOADS = {
+    "graphene2048": wl.GRAPHENE_2048,
+    "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
+                               n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
+}
+CHEB_SRC = os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", "cheb.cu")
+TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="tbpm", choices=["tbpm", "reference"])
+    p.add_argument("--workload", default="graphene2048", choices=sorted(WORKLOADS))
+    p.add_argument("--recon", default="fp64", choices=["fp64", "tensor"])
+    p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks during the timed region
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [v.strip() for v in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for k, name in enumerate(names):
+                    if parts[5 + k].lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import lattice as L, propagate as P
+kind, dims, t, W, seed, seconds, reps = {kind}, {dims}, {t}, {W}, {seed}, {seconds}, {reps}
+lat = L.build_lattice(kind, dims, t=t, W=W, seed=seed)
+psi = P.random_phase_states(lat, 1, 1)[0]
+t0 = time.perf_counter(); P.moments(lat, psi, psi, 4); one = (time.perf_counter() - t0) / 4
+k = int(max(4, min(4096, seconds / max(one, 1e-6))))
+out = []
+for _ in range(reps):
+    t0 = time.perf_counter(); P.moments(lat, psi, psi, k); dt = time.perf_counter() - t0
+    out.append(dict(steps=k, seconds=dt, site_updates=k * lat.n))
+print(json.dumps(out))
+"""
+
+
+def oracle_sample(work: wl.Workload, seconds: float, reps: int = 1):
+    spec = work.lattice
+    code = ORACLE_SAMPLE.format(root=ROOT, kind=spec.kind, dims=tuple(spec.L), t=spec.t, W=spec.W, seed=spec.seed,
+                                seconds=seconds, reps=reps)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(work: wl.Workload, samples):
+    su = sum(s["site_updates"] for s in samples)
+    sec = sum(s["seconds"] for s in samples)
+    return {"value": su / sec, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle (numpy/scipy CSR matvec), 1 state, {samples[0]['steps']} plain Chebyshev "
+                      f"steps per sample on the full {wl.KIND_NAMES[work.lattice.kind]} "
+                      f"{work.lattice.L[0]}x{work.lattice.L[1]} lattice ({work.lattice.n_full} sites), "
+                      f"{len(samples)} sample(s), {sec:.1f} s"}
+
+
+# ---------------------------------------------------------------- roofline inputs
+def measured_hbm_peak():
+    try:
+        with open(PEAKS) as f:
+            v = json.load(f).get("hbm_gbs")
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        with open(TRAFFIC) as f:
+            rec = json.load(f)
+        sha = hashlib.sha256(open(CHEB_SRC, "rb").read()).hexdigest()
+        ent = rec.get(kernel_key)
+        if ent and ent.get("source_sha256") == sha:
+            return float(ent["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, work):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps = []
+    per_step = max(2.0, min(10.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(work, per_step / 4)
+    samples = oracle_sample(work, per_step, reps=args.steps)
+    for s in samples:
+        steps.append(s)
+    su = sum(s["site_updates"] for s in steps)
+    sec = sum(s["seconds"] for s in steps)
+    value = su / sec
+    cpu = cpu_baseline_obj(work, steps)
+    print(json.dumps({
+        "impl": "reference", "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * sec / len(steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Philox random-phase state)",
+        "config": {"workload": work.name, "sites": work.lattice.n_full, "states_per_sample": 1,
+                   "form": "plain Chebyshev recurrence (oracle)"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args, work):
+    import torch
+    from paper_2510_17432_gb300 import capi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    ctx = capi.tbpm_create(local)
+    spec = work.lattice
+    desc = capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, vacancy_frac=spec.vacancy_frac,
+                             seed=spec.seed, pbc=spec.pbc, path=spec.path)
+    lat0 = capi.tbpm_lattice_create(ctx, desc)
+    info = capi.tbpm_lattice_info(lat0)
+    capi.tbpm_lattice_destroy(lat0)
+    S, M, nE = work.n_states, work.n_moments, work.n_energies
+    E = wl.uniform_energy_grid(nE, info.H0 - info.half_width, info.H0 + info.half_width)
+    recon = capi.RECON_TENSOR if args.recon == "tensor" else capi.RECON_FP64
+    req = capi.request(n_states=S, precision=capi.C64, form=capi.CONCURRENT_M, n_moments=M,
+                       state_seed=1 + 1000 * rank, dos_method=capi.DOS_JACKSON, recon=recon)
+    dev = torch.device("cuda", local)
+    d_E = torch.tensor(E, device=dev, dtype=torch.float64)
+    d_D = torch.empty((S, nE), device=dev, dtype=torch.float64)
+    torch.cuda.synchronize()
+    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
+    site_updates = (M // 2) * info.n_sites * S
+
+    def step_device():
+        lat = capi.tbpm_lattice_create(ctx, desc)
+        capi.tbpm_dos_device(ctx, lat, req, d_E, nE, d_D)
+        capi.tbpm_lattice_destroy(lat)
+
+    def barrier():
+        torch.cuda.synchronize()
+        capi.tbpm_sync(ctx)
+        if pg is not None:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = capi.tbpm_launch_count(ctx)
+    capi.tbpm_profile(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    ev1.record(stream)
+    barrier()
+    dev_ms = ev0.elapsed_time(ev1)
+    prof = capi.tbpm_profile_read(ctx)
+    capi.tbpm_profile(ctx, False)
+    launches = capi.tbpm_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    if pg is not None:
+        t = torch.tensor([dev_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        dev_ms = float(t.item())
+    ms_per_step = dev_ms / args.steps
+    value = world * site_updates / (ms_per_step / 1e3)
+
+    # parity of this run's output against the oracle is covered by the tests; sanity here
+    D = d_D.cpu().numpy()
+    assert np.all(np.isfinite(D))
+
+    # ---- end to end through the public API with pinned host buffers
+    hE = torch.tensor(E, dtype=torch.float64).pin_memory()
+    hD = torch.empty((S, nE), dtype=torch.float64).pin_memory()
+    hE_np, hD_np = hE.numpy(), hD.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat = capi.tbpm_lattice_create(ctx, desc)
+        capi.tbpm_dos(ctx, lat, req, hE_np, hD_np)
+        capi.tbpm_lattice_destroy(lat)
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if pg is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * site_updates / e2e_s, "unit": "site-updates/s",
+           "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
+
+    # ---- roofline of the dominant kernel (the recurrence pass), from the live events
+    per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
+    bytes_per_launch = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    peak, peak_kind = measured_hbm_peak()
+    traffic = kernel_traffic(f"k_moment_step/{work.name}")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "k_moment_step<honeycomb, complex64 x2 per thread>",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "avg_launch_us": per_launch_ms * 1e3,
+                "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+
+    out = {
+        "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded Philox random-phase states on a clean honeycomb lattice)",
+        "config": {"workload": work.name, "sites": info.n_sites, "states": S, "moments": M, "energies": nE,
+                   "form": "concurrent moment-based, cost-halving (M/2 matrix applications)",
+                   "precision": "complex64 states, FP64 reductions",
+                   "reconstruction": args.recon, "l2": "inputs larger than L2 (2 state blocks of "
+                   f"{info.n_sites * S * 8 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # ---- sequential form on the same GPU: wall time per converged spectrum
+    if not args.no_sequential and rank == 0 and work.n_steps:
+        Nt = work.n_steps
+        Ef = wl.uniform_energy_grid(512, info.H0 - info.half_width, info.H0 + info.half_width)
+        res = {}
+        for name, form in (("concurrent_m", capi.CONCURRENT_M), ("sequential", capi.SEQUENTIAL)):
+            r = capi.request(n_states=S, precision=capi.C64, form=form, n_steps=Nt, state_seed=1,
+                             dos_method=capi.DOS_FOURIER, window=capi.WINDOW_HANN)
+            Dout = np.zeros((S, Ef.size))
+            lat = capi.tbpm_lattice_create(ctx, desc)
+            c0 = capi.tbpm_launch_count(ctx)
+            t0 = time.perf_counter()
+            capi.tbpm_dos(ctx, lat, r, Ef, Dout)
+            res[name] = (time.perf_counter() - t0, capi.tbpm_launch_count(ctx) - c0, Dout)
+            capi.tbpm_lattice_destroy(lat)
+        Ntrunc = capi.tbpm_truncation_order(math.pi)
+        Mtot = capi.tbpm_truncation_order(Nt * math.pi)
+        seq_su = Nt * (Ntrunc - 1) * info.n_sites * S
+        conc_su = (Mtot + (Mtot & 1)) // 2 * info.n_sites * S
+        diff = float(np.max(np.abs(res["concurrent_m"][2] - res["sequential"][2])) /
+                     np.max(np.abs(res["sequential"][2])))
+        out["sequential"] = {
+            "n_steps": Nt, "tau": "pi", "dos": "Hann-windowed Fourier DOS on 512 energies",
+            "wall_s_concurrent": res["concurrent_m"][0], "wall_s_sequential": res["sequential"][0],
+            "speedup_wall": res["sequential"][0] / res["concurrent_m"][0],
+            "matrix_applications_concurrent": conc_su // (info.n_sites * S),
+            "matrix_applications_sequential": seq_su // (info.n_sites * S),
+            "site_updates_per_s_sequential": seq_su / res["sequential"][0],
+            "site_updates_per_s_concurrent": conc_su / res["concurrent_m"][0],
+            "max_rel_dos_difference": diff}
+
+    if rank == 0 and not args.no_cpu and world == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline_obj(work, oracle_sample(work, args.cpu_seconds))
+        except Exception as exc:  # the GPU number stands; say why the baseline is missing
+            out["cpu_baseline"] = {"value": None, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"failed: {exc!r}"[:300]}
+    elif rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = None
+
+    capi.tbpm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    work = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, work)
+    else:
+        run_gpu(args, work)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,228 @@
+/*
+ * tbpm.h -- C ABI of the GB300 (sm_103a) Chebyshev stochastic-propagation library.
+ *
+ * The library computes, on one GPU, the hot path of the concurrent stochastic
+ * propagation method of Fu, Li, Zhou and Yuan, "Large-scale stochastic propagation
+ * method beyond the sequential approach" (arXiv 2510.17432):
+ *
+ *   - a tight-binding Hamiltonian H on a square, honeycomb or simple-cubic lattice
+ *     (nearest-neighbour hopping t, Anderson on-site disorder of width W, optional
+ *     random vacancies), rescaled to H~ = (H - H0)/|H| (Sec. II.A);
+ *   - blocks of S random-phase states (or site states |r> for the LDOS, Sec. III);
+ *   - the Chebyshev recurrence T_{k+1} = 2 H~ T_k - T_{k-1} (App. B, Eq. cheb_relation)
+ *     applied to all S states at once, fused with the inner products that give
+ *     Chebyshev moments m_n = <psi|T_n(H~)|psi> (Sec. II.A, moment-based form, with the
+ *     cost-halving identity of Eq. cheby_prod) or time-correlation values;
+ *   - the sequential form and the state-based concurrent form with time blocks of b
+ *     steps (Sec. II.A Eq. TE, Sec. II.B), both driven by Bessel coefficients
+ *     c_n(tau~) = 2(-i)^n J_n(tau~) (App. B);
+ *   - reconstruction of C(t_j) and of the DOS on an energy grid (Sec. III).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a tbpm_status (0 = success, negative = error).  On error the
+ *     thread-local message of tbpm_last_error() says what failed.  No exception
+ *     crosses the ABI.
+ *   - Units: hbar = 1; energies in the unit of the hopping t; times in 1/energy.
+ *   - Handles (tbpm_ctx, tbpm_lattice) are created and freed by the library.  Inputs
+ *     are read during the call and never retained.  Host output buffers are
+ *     caller-allocated with the lengths stated per call.
+ *   - Complex numbers are stored as (re, im) pairs.  Host outputs are FP64.
+ *   - "_device" entry points take device pointers on the context's device and enqueue
+ *     work on the context's stream without synchronising; everything else
+ *     synchronises before returning.
+ *   - Device memory is allocated by the library (stream-ordered) and cached in the
+ *     context; it is released by tbpm_destroy().
+ */
+#ifndef TBPM_H
+#define TBPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TBPM_OK = 0,
+  TBPM_EINVAL = -1,       /* invalid argument: a message names it */
+  TBPM_ENOMEM = -2,       /* device allocation failed / request exceeds the HBM budget */
+  TBPM_ECUDA = -3,        /* a CUDA runtime call failed: the message carries its text */
+  TBPM_ETIMEOUT = -4,     /* a bounded wait expired */
+  TBPM_EUNSUPPORTED = -5, /* valid but not implemented combination */
+  TBPM_EBUSY = -6,        /* serving queue full */
+  TBPM_ECANCELLED = -7    /* request cancelled */
+} tbpm_status;
+
+/* lattice kinds and Hamiltonian storage paths */
+enum { TBPM_SQUARE = 0, TBPM_HONEYCOMB = 1, TBPM_CUBIC = 2 };
+enum { TBPM_PATH_AUTO = 0, TBPM_PATH_STENCIL = 1, TBPM_PATH_CSR = 2 };
+/* state precision: complex64 states with FP64 reductions, or complex128 throughout */
+enum { TBPM_C64 = 0, TBPM_C128 = 1 };
+/* initial states: random phases (Sec. II.A) or site states |r> (LDOS, Sec. III) */
+enum { TBPM_STATES_RANDOM = 0, TBPM_STATES_SITES = 1 };
+/* propagation form (Sec. II.A): sequential, moment-based concurrent, state-based concurrent */
+enum { TBPM_SEQUENTIAL = 0, TBPM_CONCURRENT_M = 1, TBPM_CONCURRENT_S = 2 };
+/* DOS reconstruction: Jackson-damped Chebyshev series, or windowed Fourier transform of C(t) */
+enum { TBPM_DOS_JACKSON = 0, TBPM_DOS_FOURIER = 1 };
+enum { TBPM_WINDOW_NONE = 0, TBPM_WINDOW_HANN = 1 };
+/* reconstruction arithmetic: FP64 CUDA cores, or tensor cores (bf16x3 split, FP32 MMA, FP64 sums) */
+enum { TBPM_RECON_FP64 = 0, TBPM_RECON_TENSOR = 1 };
+
+typedef struct tbpm_ctx tbpm_ctx;
+typedef struct tbpm_lattice tbpm_lattice;
+
+/*
+ * Lattice description.  Site numbering (the paper prints none; this is the library's):
+ *   square     i = y*Lx + x,             neighbours (x+1,y) (x-1,y) (x,y+1) (x,y-1)
+ *   honeycomb  i = 2*(y*Lx + x) + s,     A(x,y)-B(x,y), A(x,y)-B(x-1,y), A(x,y)-B(x,y-1)
+ *   cubic      i = (z*Ly + y)*Lx + x,    neighbours +-x, +-y, +-z
+ * H_ij = t on every bond, H_ii = V_i = W*((u>>8)*2^-24 - 1/2) with u the Philox4x32-10
+ * draw (key = seed, counter = (i, 0, 0, 0) in 32-bit words (i_lo, i_hi, stream 0, 0)).
+ * Vacancies (vacancy_frac > 0): site i is removed when its stream-1 draw u < floor(p*2^32);
+ * the remaining sites are renumbered in order and stored on the CSR/ELL path.
+ * Spectral bounds (Gershgorin; Sec. II.A uses Lanczos): E_max = max_i(V_i + deg_i|t|),
+ * E_min = min_i(V_i - deg_i|t|), H0 = (E_max+E_min)/2, |H| = 1.01*(E_max-E_min)/2.
+ */
+typedef struct {
+  int32_t kind;        /* TBPM_SQUARE / TBPM_HONEYCOMB / TBPM_CUBIC */
+  int32_t path;        /* TBPM_PATH_*; AUTO picks STENCIL unless vacancy_frac > 0 */
+  int64_t L[3];        /* Lx, Ly, Lz (unit cells for the honeycomb; unused entries 1) */
+  int32_t pbc[3];      /* 1 = periodic, 0 = open, per direction */
+  int32_t reserved;
+  double t;            /* hopping */
+  double W;            /* disorder width: V_i uniform on [-W/2, W/2) */
+  double vacancy_frac; /* probability that a site is removed */
+  uint64_t seed;       /* Philox key of the disorder and vacancy streams */
+} tbpm_lattice_desc;
+
+typedef struct {
+  int64_t n_full;      /* sites before vacancy removal */
+  int64_t n_sites;     /* active sites N (the state length) */
+  int64_t n_bonds;     /* directed bonds (off-diagonal non-zeros of H) */
+  int32_t path;        /* resolved TBPM_PATH_STENCIL or TBPM_PATH_CSR */
+  int32_t coordination;
+  double E_min, E_max; /* Gershgorin bounds */
+  double H0;           /* spectral centre */
+  double half_width;   /* |H| */
+} tbpm_lattice_props;
+
+/*
+ * One spectral request.  S = n_states random-phase states drawn from Philox with
+ * key = state_seed and counter (i_lo, i_hi, 2, s) for full site index i and state s,
+ * psi_i = exp(2 pi i u/2^32)/sqrt(N); or, with states = TBPM_STATES_SITES, the S site
+ * states |sites[s]> (compact site indices).
+ */
+typedef struct {
+  int32_t precision;    /* TBPM_C64 or TBPM_C128 */
+  int32_t states;       /* TBPM_STATES_RANDOM or TBPM_STATES_SITES */
+  int32_t n_states;     /* S >= 1 (for SITES: the number of entries in sites) */
+  int32_t form;         /* TBPM_SEQUENTIAL / TBPM_CONCURRENT_M / TBPM_CONCURRENT_S */
+  uint64_t state_seed;
+  const int64_t* sites; /* host array [n_states] for TBPM_STATES_SITES, else NULL */
+  int64_t n_moments;    /* M (even); 0 = derive from n_steps as N(n_steps*tau~) */
+  int64_t n_steps;      /* N_t time steps for correlation requests */
+  double tau;           /* rescaled time step tau~; 0 means pi (the Nyquist step, Sec. II.A) */
+  int32_t time_block;   /* b for TBPM_CONCURRENT_S; 0 = from the Tab. I cost model */
+  int32_t dos_method;   /* TBPM_DOS_JACKSON or TBPM_DOS_FOURIER */
+  int32_t window;       /* TBPM_WINDOW_* for the Fourier DOS */
+  int32_t recon;        /* TBPM_RECON_FP64 or TBPM_RECON_TENSOR */
+} tbpm_request;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`: a stream and a cached workspace.
+ * *out receives the handle.  Fails with TBPM_ECUDA if the device is unusable. */
+int tbpm_create(tbpm_ctx** out, int device);
+/* Free the context and all device memory it holds.  NULL is accepted. */
+int tbpm_destroy(tbpm_ctx* ctx);
+/* Thread-local text of the last error (never NULL; empty after success). */
+const char* tbpm_last_error(void);
+/* The context's cudaStream_t, returned as void*, for event timing by the caller. */
+void* tbpm_stream(tbpm_ctx* ctx);
+/* Block until all work enqueued on the context's stream has finished. */
+int tbpm_sync(tbpm_ctx* ctx);
+/* Number of kernels the library has launched on this context since creation. */
+int64_t tbpm_launch_count(const tbpm_ctx* ctx);
+/* Phase timing.  tbpm_profile(ctx, 1) clears the record and starts recording CUDA events
+ * on the context stream around every recurrence loop (kind 0: the Chebyshev passes of a
+ * moment request) and every DOS reconstruction (kind 1); tbpm_profile(ctx, 0) stops.
+ * tbpm_profile_read() synchronises and returns out[0] = recurrence milliseconds,
+ * out[1] = recurrence kernel launches, out[2] = reconstruction milliseconds,
+ * out[3] = reconstruction kernel launches, summed over the recorded phases. */
+int tbpm_profile(tbpm_ctx* ctx, int enable);
+int tbpm_profile_read(tbpm_ctx* ctx, double out[4]);
+
+/* ---------------------------------------------------------------- lattice */
+
+/* Build H on the device: disorder, vacancies, CSR/ELL neighbour lists and bounds.
+ * The lattice stays valid until tbpm_lattice_destroy() and must be destroyed before
+ * its context.  Sizes: every L >= 1, product of sites < 2^31 * 2 (see n_sites). */
+int tbpm_lattice_create(tbpm_ctx* ctx, const tbpm_lattice_desc* desc, tbpm_lattice** out);
+int tbpm_lattice_destroy(tbpm_lattice* lat);
+int tbpm_lattice_info(const tbpm_lattice* lat, tbpm_lattice_props* out);
+/* Debug export for bit-exact tests (any pointer may be NULL):
+ *   compact  [n_full]        compact index of every full site, -1 if vacant
+ *   V        [n_sites]       FP64 on-site energies
+ *   nbr      [n_sites * z]   neighbour compact indices in the fixed order, -1 if none */
+int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, int32_t* nbr);
+
+/* ---------------------------------------------------------------- states */
+
+/* Initial state block as stored for the recurrence, exported to the host:
+ * out = [S][n_sites] complex, FP64 pairs (C128) or FP32 pairs (C64).
+ * draws (optional) = [S][n_sites] uint32 Philox phase draws (random states only). */
+int tbpm_states_export(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+                       void* out, uint32_t* draws);
+
+/* Adjacency operator y_i = sum over the neighbours j of i of x_j, applied by the same
+ * recurrence kernel as the hot path (first-term mode, zero diagonal, unit hopping).
+ * x, y = host [n_sites][S] interleaved complex (FP32 pairs for C64, FP64 for C128);
+ * S must be a power of two <= 32.  For exact tests of the stencil and ELL indexing. */
+int tbpm_apply_hopping(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int n_states,
+                       const void* x, void* y);
+
+/* ---------------------------------------------------------------- hot path */
+
+/* Chebyshev moments m_n = <psi_s|T_n(H~)|psi_s>, n = 0..M-1, of every state s, from
+ * M/2 matrix applications (cost-halving identity Eq. cheby_prod, with
+ * m_{2k} = 2<phi_k|phi_k> - m_0 and m_{2k+1} = 2<phi_{k+1}|phi_k> - m_1).
+ * mu = host [S][M][2] (re, im).  M must be even and >= 2. */
+int tbpm_moments(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, double* mu);
+/* Same, into device memory d_mu [S][M][2] doubles; asynchronous on the context stream. */
+int tbpm_moments_device(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+                        double* d_mu);
+
+/* Correlation C_s(t_j) = <psi_s|exp(-i H t_j)|psi_s>, t_j = j*tau~/|H|, j = 0..N_t, by the
+ * request's form: SEQUENTIAL (step by step), CONCURRENT_M (moments, then
+ * C(t_j) = exp(-i H0 t_j) sum_{n<N(j tau~)} c_n(j tau~) m_n), or CONCURRENT_S (time blocks
+ * of b steps, Eq. TE).  C = host [S][N_t+1][2]. */
+int tbpm_correlation(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, double* C);
+int tbpm_correlation_device(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+                            double* d_C);
+
+/* DOS (or LDOS for site states) of every state on the energies [n_energies] (host):
+ *   TBPM_DOS_JACKSON: D(E) = [g_0 m_0 + 2 sum_{n>=1} g_n Re m_n T_n(E~)] / (pi |H| sqrt(1-E~^2))
+ *     with Jackson factors g_n (Weisse et al., Rev. Mod. Phys. 78, 275 (2006), Eq. 71);
+ *   TBPM_DOS_FOURIER: D(E) = (tau/2pi)[w_0 C(0) + 2 Re sum_j w_j exp(i E t_j) C(t_j)] (Sec. III).
+ * D = host [S][n_energies].  Energies outside (H0-|H|, H0+|H|) give 0 for Jackson. */
+int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+             const double* energies, int64_t n_energies, double* D);
+/* Same with device energies [n_energies] and device output [S][n_energies]; async. */
+int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+                    const double* d_energies, int64_t n_energies, double* d_D);
+
+/* ---------------------------------------------------------------- cost model */
+
+/* Truncation order N(tau~) = 1 + max{n : |c_n(tau~)| > 1e-14} (Sec. II.A), FP64 host. */
+int64_t tbpm_truncation_order(double tau);
+/* Tab. I counts of the state-based form with blocks of b steps over N_t steps:
+ * out[0] = amxsy (Chebyshev terms generated), out[1] = axpy, out[2] = dot. */
+int tbpm_block_counts(int64_t n_steps, int64_t b, double tau, int64_t out[3]);
+/* b_opt = argmin_b N_amxsy(b) t_amxsy + N_axpy(b) t_axpy over 1 <= b <= b_max (Sec. II.B). */
+int64_t tbpm_block_opt(int64_t n_steps, double tau, double t_amxsy, double t_axpy, int64_t b_max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TBPM_H */

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of the C ABI declared in include/tbpm.h (argument marshalling only).
+
+Every function keeps the C name and forwards to libtbpm.so; a negative status raises
+TbpmError with the library's message.  Host buffers are numpy arrays; device buffers
+are anything with a `data_ptr()` (torch tensors) or a raw integer address.
+There is no fallback: if libtbpm.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from ._build import LIB
+
+SQUARE, HONEYCOMB, CUBIC = 0, 1, 2
+PATH_AUTO, PATH_STENCIL, PATH_CSR = 0, 1, 2
+C64, C128 = 0, 1
+STATES_RANDOM, STATES_SITES = 0, 1
+SEQUENTIAL, CONCURRENT_M, CONCURRENT_S = 0, 1, 2
+DOS_JACKSON, DOS_FOURIER = 0, 1
+WINDOW_NONE, WINDOW_HANN = 0, 1
+RECON_FP64, RECON_TENSOR = 0, 1
+
+STATUS = {0: "TBPM_OK", -1: "TBPM_EINVAL", -2: "TBPM_ENOMEM", -3: "TBPM_ECUDA", -4: "TBPM_ETIMEOUT",
+          -5: "TBPM_EUNSUPPORTED", -6: "TBPM_EBUSY", -7: "TBPM_ECANCELLED"}
+
+
+class TbpmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class LatticeDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("path", C.c_int32), ("L", C.c_int64 * 3), ("pbc", C.c_int32 * 3),
+                ("reserved", C.c_int32), ("t", C.c_double), ("W", C.c_double),
+                ("vacancy_frac", C.c_double), ("seed", C.c_uint64)]
+
+
+class LatticeProps(C.Structure):
+    _fields_ = [("n_full", C.c_int64), ("n_sites", C.c_int64), ("n_bonds", C.c_int64),
+                ("path", C.c_int32), ("coordination", C.c_int32), ("E_min", C.c_double),
+                ("E_max", C.c_double), ("H0", C.c_double), ("half_width", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("states", C.c_int32), ("n_states", C.c_int32),
+                ("form", C.c_int32), ("state_seed", C.c_uint64), ("sites", C.POINTER(C.c_int64)),
+                ("n_moments", C.c_int64), ("n_steps", C.c_int64), ("tau", C.c_double),
+                ("time_block", C.c_int32), ("dos_method", C.c_int32), ("window", C.c_int32),
+                ("recon", C.c_int32)]
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def load():
+    """Load libtbpm.so (built in-tree by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise ImportError(f"{LIB} is missing: build it with __graft_entry__.build() "
+                          "(there is no fallback implementation)")
+    lib = C.CDLL(LIB)
+    sig = {
+        "tbpm_create": (C.c_int, [C.POINTER(_P), C.c_int]),
+        "tbpm_destroy": (C.c_int, [_P]),
+        "tbpm_last_error": (C.c_char_p, []),
+        "tbpm_stream": (_P, [_P]),
+        "tbpm_sync": (C.c_int, [_P]),
+        "tbpm_launch_count": (C.c_int64, [_P]),
+        "tbpm_profile": (C.c_int, [_P, C.c_int]),
+        "tbpm_profile_read": (C.c_int, [_P, C.POINTER(C.c_double)]),
+        "tbpm_lattice_create": (C.c_int, [_P, C.POINTER(LatticeDesc), C.POINTER(_P)]),
+        "tbpm_lattice_destroy": (C.c_int, [_P]),
+        "tbpm_lattice_info": (C.c_int, [_P, C.POINTER(LatticeProps)]),
+        "tbpm_lattice_export": (C.c_int, [_P, _P, _P, _P]),
+        "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
+        "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
+        "tbpm_moments": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
+        "tbpm_moments_device": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
+        "tbpm_correlation": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
+        "tbpm_correlation_device": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
+        "tbpm_dos": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
+        "tbpm_dos_device": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
+        "tbpm_truncation_order": (C.c_int64, [C.c_double]),
+        "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
+        "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
+    return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
+            "tbpm_launch_count", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
+            "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
+            "tbpm_dos_device", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt"]
+
+
+def _check(status: int):
+    if status != 0:
+        raise TbpmError(status, load().tbpm_last_error().decode(errors="replace"))
+
+
+def _host_ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return C.c_void_p(t)
+    return C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- context
+def tbpm_create(device: int = 0):
+    h = _P()
+    _check(load().tbpm_create(C.byref(h), int(device)))
+    return h
+
+
+def tbpm_destroy(ctx):
+    _check(load().tbpm_destroy(ctx))
+
+
+def tbpm_last_error() -> str:
+    return load().tbpm_last_error().decode(errors="replace")
+
+
+def tbpm_stream(ctx) -> int:
+    return load().tbpm_stream(ctx) or 0
+
+
+def tbpm_sync(ctx):
+    _check(load().tbpm_sync(ctx))
+
+
+def tbpm_launch_count(ctx) -> int:
+    return int(load().tbpm_launch_count(ctx))
+
+
+def tbpm_profile(ctx, enable: bool):
+    _check(load().tbpm_profile(ctx, int(bool(enable))))
+
+
+def tbpm_profile_read(ctx) -> dict:
+    out = (C.c_double * 4)()
+    _check(load().tbpm_profile_read(ctx, out))
+    return {"recurrence_ms": out[0], "recurrence_launches": int(out[1]),
+            "recon_ms": out[2], "recon_launches": int(out[3])}
+
+
+# ---------------------------------------------------------------- lattice
+def lattice_desc(kind, L, t=1.0, W=0.0, vacancy_frac=0.0, seed=0, pbc=(1, 1, 1), path=PATH_AUTO) -> LatticeDesc:
+    L = tuple(int(v) for v in L) + (1,) * (3 - len(L))
+    pbc = tuple(int(bool(v)) for v in pbc) + (1,) * (3 - len(pbc))
+    return LatticeDesc(int(kind), int(path), (C.c_int64 * 3)(*L), (C.c_int32 * 3)(*pbc), 0,
+                       float(t), float(W), float(vacancy_frac), int(seed) & 0xFFFFFFFFFFFFFFFF)
+
+
+def tbpm_lattice_create(ctx, desc: LatticeDesc):
+    h = _P()
+    _check(load().tbpm_lattice_create(ctx, C.byref(desc), C.byref(h)))
+    return h
+
+
+def tbpm_lattice_destroy(lat):
+    _check(load().tbpm_lattice_destroy(lat))
+
+
+def tbpm_lattice_info(lat) -> LatticeProps:
+    p = LatticeProps()
+    _check(load().tbpm_lattice_info(lat, C.byref(p)))
+    return p
+
+
+def tbpm_lattice_export(lat, compact=None, V=None, nbr=None):
+    _check(load().tbpm_lattice_export(lat, _host_ptr(compact), _host_ptr(V), _host_ptr(nbr)))
+
+
+# ---------------------------------------------------------------- requests
+def request(n_states=1, precision=C64, form=CONCURRENT_M, n_moments=0, n_steps=0, state_seed=1,
+            sites=None, tau=0.0, time_block=0, dos_method=DOS_JACKSON, window=WINDOW_NONE,
+            recon=RECON_FP64):
+    """Build a Request; keeps a reference to the site array so the pointer stays valid."""
+    r = Request()
+    r.precision = precision
+    r.form = form
+    r.state_seed = int(state_seed) & 0xFFFFFFFFFFFFFFFF
+    r.n_moments = int(n_moments)
+    r.n_steps = int(n_steps)
+    r.tau = float(tau)
+    r.time_block = int(time_block)
+    r.dos_method = dos_method
+    r.window = window
+    r.recon = recon
+    if sites is not None:
+        arr = np.ascontiguousarray(sites, dtype=np.int64)
+        r.states = STATES_SITES
+        r.n_states = arr.size
+        r.sites = arr.ctypes.data_as(C.POINTER(C.c_int64))
+        r._sites_keepalive = arr
+    else:
+        r.states = STATES_RANDOM
+        r.n_states = int(n_states)
+        r.sites = None
+    return r
+
+
+def tbpm_states_export(ctx, lat, req: Request, out=None, draws=None):
+    _check(load().tbpm_states_export(ctx, lat, C.byref(req), _host_ptr(out), _host_ptr(draws)))
+
+
+def tbpm_apply_hopping(ctx, lat, precision: int, n_states: int, x: np.ndarray, y: np.ndarray):
+    _check(load().tbpm_apply_hopping(ctx, lat, int(precision), int(n_states), _host_ptr(x), _host_ptr(y)))
+
+
+def tbpm_moments(ctx, lat, req: Request, mu: np.ndarray):
+    _check(load().tbpm_moments(ctx, lat, C.byref(req), _host_ptr(mu)))
+
+
+def tbpm_moments_device(ctx, lat, req: Request, d_mu):
+    _check(load().tbpm_moments_device(ctx, lat, C.byref(req), _dev_ptr(d_mu)))
+
+
+def tbpm_correlation(ctx, lat, req: Request, Cout: np.ndarray):
+    _check(load().tbpm_correlation(ctx, lat, C.byref(req), _host_ptr(Cout)))
+
+
+def tbpm_correlation_device(ctx, lat, req: Request, d_C):
+    _check(load().tbpm_correlation_device(ctx, lat, C.byref(req), _dev_ptr(d_C)))
+
+
+def tbpm_dos(ctx, lat, req: Request, energies: np.ndarray, D: np.ndarray):
+    _check(load().tbpm_dos(ctx, lat, C.byref(req), _host_ptr(energies), int(energies.size), _host_ptr(D)))
+
+
+def tbpm_dos_device(ctx, lat, req: Request, d_energies, n_energies: int, d_D):
+    _check(load().tbpm_dos_device(ctx, lat, C.byref(req), _dev_ptr(d_energies), int(n_energies), _dev_ptr(d_D)))
+
+
+# ---------------------------------------------------------------- cost model
+def tbpm_truncation_order(tau: float) -> int:
+    return int(load().tbpm_truncation_order(float(tau)))
+
+
+def tbpm_block_counts(n_steps: int, b: int, tau: float) -> tuple:
+    out = (C.c_int64 * 3)()
+    _check(load().tbpm_block_counts(int(n_steps), int(b), float(tau), out))
+    return tuple(int(v) for v in out)
+
+
+def tbpm_block_opt(n_steps: int, tau: float, t_amxsy: float, t_axpy: float, b_max: int) -> int:
+    return int(load().tbpm_block_opt(int(n_steps), float(tau), float(t_amxsy), float(t_axpy), int(b_max)))

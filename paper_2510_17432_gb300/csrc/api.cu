@@ -1,0 +1,1229 @@
+// C ABI of the library: context, lattice construction on the device, initial states, and
+// the drivers of the three propagation forms of Sec. II.A (sequential, moment-based,
+// state-based with time blocks) and of the spectra of Sec. III.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+
+static thread_local char g_err[1024];
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+int ensure(tbpm_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return TBPM_OK;
+  if (b.p) {
+    TBPM_CK(cudaFreeAsync(b.p, ctx->stream));
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  const size_t want = std::max<size_t>(256, bytes + (bytes >> 4));
+  cudaError_t e = cudaMallocAsync(&b.p, want, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    return TBPM_ENOMEM;
+  }
+  b.cap = want;
+  return TBPM_OK;
+}
+
+static cudaEvent_t take_event(tbpm_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+int phase_begin(tbpm_ctx* ctx, int kind) {
+  if (!ctx->profiling) return -1;
+  tbpm_ctx::Phase ph;
+  ph.a = take_event(ctx);
+  ph.b = take_event(ctx);
+  ph.kind = kind;
+  ph.launches = ctx->launches;
+  cudaEventRecord(ph.a, ctx->stream);
+  ctx->phases.push_back(ph);
+  return (int)ctx->phases.size() - 1;
+}
+
+void phase_end(tbpm_ctx* ctx, int token) {
+  if (token < 0 || token >= (int)ctx->phases.size()) return;
+  tbpm_ctx::Phase& ph = ctx->phases[token];
+  ph.launches = ctx->launches - ph.launches;
+  cudaEventRecord(ph.b, ctx->stream);
+}
+
+static void release(tbpm_ctx* ctx, DevBuf& b) {
+  if (b.p) cudaFreeAsync(b.p, ctx->stream);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+template <typename T>
+static int dev_alloc(tbpm_ctx* ctx, T** p, size_t count) {
+  cudaError_t e = cudaMallocAsync((void**)p, std::max<size_t>(1, count) * sizeof(T), ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_error("device allocation of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return TBPM_ENOMEM;
+  }
+  return TBPM_OK;
+}
+
+static int grid_for(tbpm_ctx* ctx, int64_t n, int threads, int per_sm = 16) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)ctx->num_sms * per_sm));
+}
+
+// ------------------------------------------------------------------ lattice kernels
+constexpr int kT = 256;
+
+__device__ __forceinline__ double disorder_value(uint64_t seed, double W, int64_t i) {
+  const uint32_t u = draw_u32(seed, (uint64_t)i, STREAM_DISORDER, 0);
+  return W * ((double)(u >> 8) * 0x1p-24 - 0.5);
+}
+
+__device__ __forceinline__ bool vacant(uint64_t seed, uint64_t thr, int64_t i) {
+  return (uint64_t)draw_u32(seed, (uint64_t)i, STREAM_VACANCY, 0) < thr;
+}
+
+struct Bounds3 {
+  double emax, emin, deg;
+};
+
+__device__ __forceinline__ void block_bounds(Bounds3 v, Bounds3* part) {
+  __shared__ Bounds3 sh[kT / 32];
+  for (int off = 16; off >= 1; off >>= 1) {
+    v.emax = fmax(v.emax, __shfl_xor_sync(0xffffffffu, v.emax, off));
+    v.emin = fmin(v.emin, __shfl_xor_sync(0xffffffffu, v.emin, off));
+    v.deg += __shfl_xor_sync(0xffffffffu, v.deg, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Bounds3 r = sh[0];
+    for (int w = 1; w < kT / 32; ++w) {
+      r.emax = fmax(r.emax, sh[w].emax);
+      r.emin = fmin(r.emin, sh[w].emin);
+      r.deg += sh[w].deg;
+    }
+    part[blockIdx.x] = r;
+  }
+}
+
+// Stencil path: V_i (FP64), degree and Gershgorin terms for every site.
+__global__ void __launch_bounds__(kT) k_lattice_stencil(Geom g, uint64_t seed, double W, double abs_t,
+                                                        double* v64, Bounds3* part) {
+  Bounds3 acc{-INFINITY, INFINITY, 0.0};
+  for (int64_t i = (int64_t)blockIdx.x * kT + threadIdx.x; i < g.n_full; i += (int64_t)gridDim.x * kT) {
+    int deg = 0;
+    for (int d = 0; d < g.z; ++d) deg += neighbour_full(g, i, d) >= 0;
+    const double v = (W != 0.0) ? disorder_value(seed, W, i) : 0.0;
+    if (v64) v64[i] = v;
+    acc.emax = fmax(acc.emax, v + deg * abs_t);
+    acc.emin = fmin(acc.emin, v - deg * abs_t);
+    acc.deg += deg;
+  }
+  block_bounds(acc, part);
+}
+
+__global__ void k_bounds_final(const Bounds3* part, int n, double* out) {
+  __shared__ Bounds3 sh[kT];
+  Bounds3 acc{-INFINITY, INFINITY, 0.0};
+  for (int i = threadIdx.x; i < n; i += kT) {
+    acc.emax = fmax(acc.emax, part[i].emax);
+    acc.emin = fmin(acc.emin, part[i].emin);
+    acc.deg += part[i].deg;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Bounds3 r = sh[0];
+    for (int w = 1; w < kT; ++w) {
+      r.emax = fmax(r.emax, sh[w].emax);
+      r.emin = fmin(r.emin, sh[w].emin);
+      r.deg += sh[w].deg;
+    }
+    out[0] = r.emax;
+    out[1] = r.emin;
+    out[2] = r.deg;
+  }
+}
+
+// CSR path, pass 1: active-site counts per chunk of kChunk sites.
+constexpr int kPer = 16;
+constexpr int kChunk = kT * kPer;
+
+__global__ void __launch_bounds__(kT) k_count_active(int64_t n_full, uint64_t seed, uint64_t thr,
+                                                     int64_t* counts) {
+  __shared__ int64_t sh[kT / 32];
+  const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kPer;
+  int64_t c = 0;
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t i = base + q;
+    if (i < n_full && !vacant(seed, thr, i)) ++c;
+  }
+  for (int off = 16; off >= 1; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kT / 32; ++w) t += sh[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the chunk counts by one block: offs[0..n], offs[n] = total.
+__global__ void k_scan_counts(const int64_t* counts, int64_t n, int64_t* offs) {
+  __shared__ int64_t sh[1024];
+  const int64_t per = (n + 1023) / 1024;
+  const int64_t lo = threadIdx.x * per, hi = std::min<int64_t>(n, lo + per);
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += counts[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t run = sh[threadIdx.x] - s;  // exclusive prefix of this thread's segment
+  for (int64_t i = lo; i < hi; ++i) {
+    offs[i] = run;
+    run += counts[i];
+  }
+  if (threadIdx.x == 1023) offs[n] = sh[1023];
+}
+
+// CSR path, pass 2: compact index of every site (-1 if vacant) and full index of every active site.
+__global__ void __launch_bounds__(kT) k_compact(int64_t n_full, uint64_t seed, uint64_t thr,
+                                                const int64_t* offs, int64_t* compact, int64_t* full_of) {
+  __shared__ int64_t sh[kT];
+  const int64_t base = (int64_t)blockIdx.x * kChunk + (int64_t)threadIdx.x * kPer;
+  unsigned flags = 0;
+  int c = 0;
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t i = base + q;
+    if (i < n_full && !vacant(seed, thr, i)) {
+      flags |= 1u << q;
+      ++c;
+    }
+  }
+  sh[threadIdx.x] = c;
+  __syncthreads();
+  for (int off = 1; off < kT; off <<= 1) {
+    const int64_t v = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int64_t k = offs[blockIdx.x] + sh[threadIdx.x] - c;
+  for (int q = 0; q < kPer; ++q) {
+    const int64_t i = base + q;
+    if (i >= n_full) break;
+    if (flags & (1u << q)) {
+      compact[i] = k;
+      full_of[k] = i;
+      ++k;
+    } else {
+      compact[i] = -1;
+    }
+  }
+}
+
+// CSR path, pass 3: ELL neighbour lists, V_i and Gershgorin terms of every active site.
+__global__ void __launch_bounds__(kT) k_build_ell(Geom g, int64_t n, const int64_t* full_of,
+                                                  const int64_t* compact, uint64_t seed, double W,
+                                                  double abs_t, int32_t* ell, double* v64, Bounds3* part) {
+  Bounds3 acc{-INFINITY, INFINITY, 0.0};
+  for (int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kT) {
+    const int64_t i = full_of[k];
+    int deg = 0;
+    for (int d = 0; d < g.z; ++d) {
+      const int64_t j = neighbour_full(g, i, d);
+      const int64_t cj = j >= 0 ? compact[j] : -1;
+      ell[k * g.z + d] = (int32_t)cj;
+      deg += cj >= 0;
+    }
+    const double v = (W != 0.0) ? disorder_value(seed, W, i) : 0.0;
+    if (v64) v64[k] = v;
+    acc.emax = fmax(acc.emax, v + deg * abs_t);
+    acc.emin = fmin(acc.emin, v - deg * abs_t);
+    acc.deg += deg;
+  }
+  block_bounds(acc, part);
+}
+
+// D_i = (V_i - H0)/|H| in FP64 and rounded once to FP32.
+__global__ void k_make_diag(int64_t n, const double* v64, double H0, double half, double* d64, float* d32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (v64[i] - H0) / half;
+    if (d64) d64[i] = d;
+    if (d32) d32[i] = (float)d;
+  }
+}
+
+// ------------------------------------------------------------------ initial states
+// Random phases psi_i = exp(2 pi i u / 2^32) / sqrt(N), u = Philox(state_seed; i, 2, s).
+template <typename R>
+__global__ void k_init_random(int64_t n, int Spad, int logS, int S, uint64_t seed, const int64_t* full_of,
+                              double inv_sqrt_n, R* out, uint32_t* draws) {
+  const int64_t total = n * Spad;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e >> logS;
+    const int s = (int)(e & (Spad - 1));
+    R re = R(0), im = R(0);
+    if (s < S) {
+      const int64_t f = full_of ? full_of[k] : k;
+      const uint32_t u = draw_u32(seed, (uint64_t)f, STREAM_PHASE, (uint32_t)s);
+      double sn, cs;
+      sincospi((double)u * 0x1p-31, &sn, &cs);
+      re = (R)(cs * inv_sqrt_n);
+      im = (R)(sn * inv_sqrt_n);
+      if (draws) draws[(int64_t)s * n + k] = u;
+    }
+    out[2 * e] = re;
+    out[2 * e + 1] = im;
+  }
+}
+
+template <typename R>
+__global__ void k_init_sites(int64_t n, int Spad, int S, const int64_t* sites, R* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  out[2 * (sites[s] * Spad + s)] = R(1);
+}
+
+}  // namespace tbpm
+
+using namespace tbpm;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* tbpm_last_error(void) { return g_err; }
+
+int tbpm_create(tbpm_ctx** out, int device) {
+  clear_error();
+  if (!out) {
+    set_error("tbpm_create: out is NULL");
+    return TBPM_EINVAL;
+  }
+  *out = nullptr;
+  int count = 0;
+  TBPM_CK(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) {
+    set_error("tbpm_create: device %d out of range (%d devices)", device, count);
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaSetDevice(device));
+  tbpm_ctx* ctx = new tbpm_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->pinned, 4096);
+  if (e != cudaSuccess) {
+    set_error("tbpm_create: %s", cudaGetErrorString(e));
+    delete ctx;
+    return TBPM_ECUDA;
+  }
+  ctx->pinned_cap = 4096;
+  *out = ctx;
+  return TBPM_OK;
+}
+
+int tbpm_destroy(tbpm_ctx* ctx) {
+  clear_error();
+  if (!ctx) return TBPM_OK;
+  cudaSetDevice(ctx->device);
+  DevBuf* bufs[] = {&ctx->ws_phi[0], &ctx->ws_phi[1], &ctx->ws_psi, &ctx->ws_acc, &ctx->ws_partials,
+                    &ctx->ws_counter, &ctx->ws_mu, &ctx->ws_table, &ctx->ws_aux, &ctx->ws_out,
+                    &ctx->ws_energies, &ctx->ws_recon};
+  for (DevBuf* b : bufs) release(ctx, *b);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& ph : ctx->phases) {
+    cudaEventDestroy(ph.a);
+    cudaEventDestroy(ph.b);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return TBPM_OK;
+}
+
+void* tbpm_stream(tbpm_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int tbpm_sync(tbpm_ctx* ctx) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_sync: ctx is NULL");
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int64_t tbpm_launch_count(const tbpm_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int tbpm_profile(tbpm_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_profile: ctx is NULL");
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& ph : ctx->phases) {
+    ctx->event_pool.push_back(ph.a);
+    ctx->event_pool.push_back(ph.b);
+  }
+  ctx->phases.clear();
+  ctx->profiling = enable != 0;
+  return TBPM_OK;
+}
+
+int tbpm_profile_read(tbpm_ctx* ctx, double out[4]) {
+  clear_error();
+  if (!ctx || !out) {
+    set_error("tbpm_profile_read: NULL argument");
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < 4; ++k) out[k] = 0.0;
+  for (auto& ph : ctx->phases) {
+    float ms = 0.f;
+    TBPM_CK(cudaEventElapsedTime(&ms, ph.a, ph.b));
+    out[2 * ph.kind] += ms;
+    out[2 * ph.kind + 1] += (double)ph.launches;
+  }
+  return TBPM_OK;
+}
+
+int64_t tbpm_truncation_order(double tau) { return truncation_order_host(tau); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ lattice construction
+static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
+  const tbpm_lattice_desc& d = lat->desc;
+  Geom& g = lat->geom;
+  g.kind = d.kind;
+  g.Lx = d.L[0];
+  g.Ly = d.kind == TBPM_CUBIC || d.kind == TBPM_SQUARE || d.kind == TBPM_HONEYCOMB ? d.L[1] : 1;
+  g.Lz = d.kind == TBPM_CUBIC ? d.L[2] : 1;
+  g.pbc_x = d.pbc[0] != 0;
+  g.pbc_y = d.pbc[1] != 0;
+  g.pbc_z = d.pbc[2] != 0;
+  g.z = d.kind == TBPM_SQUARE ? 4 : d.kind == TBPM_HONEYCOMB ? 3 : 6;
+  g.row_sites = d.kind == TBPM_HONEYCOMB ? 2 * g.Lx : g.Lx;
+  g.n_rows = g.Ly * g.Lz;
+  g.n_full = g.row_sites * g.n_rows;
+  const double abs_t = fabs(d.t);
+  const bool vac = d.vacancy_frac > 0.0;
+  lat->path = (d.path == TBPM_PATH_AUTO) ? (vac ? TBPM_PATH_CSR : TBPM_PATH_STENCIL) : d.path;
+  if (vac && lat->path == TBPM_PATH_STENCIL) {
+    set_error("vacancies need the CSR path");
+    return TBPM_EINVAL;
+  }
+  lat->has_v = d.W != 0.0;
+  const uint64_t thr = vac ? (uint64_t)floor(d.vacancy_frac * 4294967296.0) : 0;
+
+  TBPM_TRY(ensure(ctx, ctx->ws_aux, sizeof(Bounds3) * (size_t)ctx->num_sms * 16 + 64));
+  Bounds3* part = (Bounds3*)ctx->ws_aux.p;
+  int nb = 0;
+  if (lat->path == TBPM_PATH_STENCIL) {
+    lat->n_sites = g.n_full;
+    if (lat->has_v) TBPM_TRY(dev_alloc(ctx, &lat->v64, lat->n_sites));
+    nb = grid_for(ctx, g.n_full, kT);
+    k_lattice_stencil<<<nb, kT, 0, ctx->stream>>>(g, d.seed, d.W, abs_t, lat->v64, part);
+    TBPM_CK_LAUNCH(ctx);
+  } else {
+    const int64_t nchunks = (g.n_full + kChunk - 1) / kChunk;
+    int64_t *counts = nullptr, *offs = nullptr;
+    TBPM_TRY(dev_alloc(ctx, &counts, nchunks));
+    TBPM_TRY(dev_alloc(ctx, &offs, nchunks + 1));
+    k_count_active<<<(unsigned)nchunks, kT, 0, ctx->stream>>>(g.n_full, d.seed, thr, counts);
+    TBPM_CK_LAUNCH(ctx);
+    k_scan_counts<<<1, 1024, 0, ctx->stream>>>(counts, nchunks, offs);
+    TBPM_CK_LAUNCH(ctx);
+    int64_t n_active = 0;
+    TBPM_CK(cudaMemcpyAsync(&n_active, offs + nchunks, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
+    if (n_active <= 0) {
+      cudaFreeAsync(counts, ctx->stream);
+      cudaFreeAsync(offs, ctx->stream);
+      set_error("lattice has no active sites");
+      return TBPM_EINVAL;
+    }
+    if (n_active >= (int64_t)INT32_MAX) {
+      set_error("CSR path supports fewer than 2^31 active sites");
+      return TBPM_EUNSUPPORTED;
+    }
+    lat->n_sites = n_active;
+    TBPM_TRY(dev_alloc(ctx, &lat->compact, g.n_full));
+    TBPM_TRY(dev_alloc(ctx, &lat->full_of, n_active));
+    TBPM_TRY(dev_alloc(ctx, &lat->ell, (size_t)n_active * g.z));
+    if (lat->has_v) TBPM_TRY(dev_alloc(ctx, &lat->v64, n_active));
+    k_compact<<<(unsigned)nchunks, kT, 0, ctx->stream>>>(g.n_full, d.seed, thr, offs, lat->compact, lat->full_of);
+    TBPM_CK_LAUNCH(ctx);
+    cudaFreeAsync(counts, ctx->stream);
+    cudaFreeAsync(offs, ctx->stream);
+    nb = grid_for(ctx, n_active, kT);
+    k_build_ell<<<nb, kT, 0, ctx->stream>>>(g, n_active, lat->full_of, lat->compact, d.seed, d.W, abs_t,
+                                             lat->ell, lat->v64, part);
+    TBPM_CK_LAUNCH(ctx);
+  }
+  double* res = (double*)((char*)ctx->ws_aux.p + sizeof(Bounds3) * (size_t)ctx->num_sms * 16);
+  k_bounds_final<<<1, kT, 0, ctx->stream>>>(part, nb, res);
+  TBPM_CK_LAUNCH(ctx);
+  TBPM_CK(cudaMemcpyAsync(ctx->pinned, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  lat->E_max = ctx->pinned[0];
+  lat->E_min = ctx->pinned[1];
+  lat->n_bonds = (int64_t)ctx->pinned[2];
+  if (!(lat->E_max > lat->E_min)) {
+    set_error("degenerate spectrum (no hopping between active sites)");
+    return TBPM_EINVAL;
+  }
+  lat->H0 = (lat->E_max + lat->E_min) / 2.0;
+  lat->half = (1.0 + 0.01) * (lat->E_max - lat->E_min) / 2.0;
+  if (lat->has_v) {
+    TBPM_TRY(dev_alloc(ctx, &lat->d32, lat->n_sites));
+    k_make_diag<<<grid_for(ctx, lat->n_sites, kT), kT, 0, ctx->stream>>>(lat->n_sites, lat->v64, lat->H0,
+                                                                        lat->half, nullptr, lat->d32);
+    TBPM_CK_LAUNCH(ctx);
+  }
+  return TBPM_OK;
+}
+
+static int ensure_d64(tbpm_lattice* lat) {
+  if (!lat->has_v || lat->d64) return TBPM_OK;
+  tbpm_ctx* ctx = lat->ctx;
+  TBPM_TRY(dev_alloc(ctx, &lat->d64, lat->n_sites));
+  k_make_diag<<<grid_for(ctx, lat->n_sites, kT), kT, 0, ctx->stream>>>(lat->n_sites, lat->v64, lat->H0, lat->half,
+                                                                      lat->d64, nullptr);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
+static void free_lattice_mem(tbpm_lattice* lat) {
+  tbpm_ctx* ctx = lat->ctx;
+  void* ps[] = {lat->d32, lat->d64, lat->v64, lat->ell, lat->compact, lat->full_of};
+  for (void* p : ps)
+    if (p) cudaFreeAsync(p, ctx->stream);
+}
+
+extern "C" {
+
+int tbpm_lattice_create(tbpm_ctx* ctx, const tbpm_lattice_desc* desc, tbpm_lattice** out) {
+  clear_error();
+  if (!ctx || !desc || !out) {
+    set_error("tbpm_lattice_create: NULL argument");
+    return TBPM_EINVAL;
+  }
+  *out = nullptr;
+  const tbpm_lattice_desc& d = *desc;
+  if (d.kind < TBPM_SQUARE || d.kind > TBPM_CUBIC) {
+    set_error("unknown lattice kind %d", d.kind);
+    return TBPM_EINVAL;
+  }
+  const int dims = d.kind == TBPM_CUBIC ? 3 : 2;
+  for (int k = 0; k < dims; ++k)
+    if (d.L[k] < 1 || d.L[k] > (1LL << 31)) {
+      set_error("lattice size L[%d] = %lld out of range", k, (long long)d.L[k]);
+      return TBPM_EINVAL;
+    }
+  if (!(d.t == d.t) || d.t == 0.0 || !isfinite(d.t) || !isfinite(d.W) || d.W < 0.0) {
+    set_error("hopping t must be finite and non-zero, W finite and >= 0");
+    return TBPM_EINVAL;
+  }
+  if (!(d.vacancy_frac >= 0.0 && d.vacancy_frac < 1.0)) {
+    set_error("vacancy_frac must lie in [0, 1)");
+    return TBPM_EINVAL;
+  }
+  if (d.path < TBPM_PATH_AUTO || d.path > TBPM_PATH_CSR) {
+    set_error("unknown path %d", d.path);
+    return TBPM_EINVAL;
+  }
+  double nf = (double)d.L[0] * (double)d.L[1] * (d.kind == TBPM_CUBIC ? (double)d.L[2] : 1.0) *
+              (d.kind == TBPM_HONEYCOMB ? 2.0 : 1.0);
+  if (nf > 4.0e9) {
+    set_error("lattice too large (%.3g sites)", nf);
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaSetDevice(ctx->device));
+  tbpm_lattice* lat = new tbpm_lattice();
+  lat->ctx = ctx;
+  lat->desc = d;
+  if (d.kind != TBPM_CUBIC) lat->desc.L[2] = 1;
+  int r = build_lattice(ctx, lat);
+  if (r != TBPM_OK) {
+    free_lattice_mem(lat);
+    delete lat;
+    return r;
+  }
+  *out = lat;
+  return TBPM_OK;
+}
+
+int tbpm_lattice_destroy(tbpm_lattice* lat) {
+  clear_error();
+  if (!lat) return TBPM_OK;
+  cudaSetDevice(lat->ctx->device);
+  free_lattice_mem(lat);
+  cudaStreamSynchronize(lat->ctx->stream);
+  delete lat;
+  return TBPM_OK;
+}
+
+int tbpm_lattice_info(const tbpm_lattice* lat, tbpm_lattice_props* out) {
+  clear_error();
+  if (!lat || !out) {
+    set_error("tbpm_lattice_info: NULL argument");
+    return TBPM_EINVAL;
+  }
+  out->n_full = lat->geom.n_full;
+  out->n_sites = lat->n_sites;
+  out->n_bonds = lat->n_bonds;
+  out->path = lat->path;
+  out->coordination = lat->geom.z;
+  out->E_min = lat->E_min;
+  out->E_max = lat->E_max;
+  out->H0 = lat->H0;
+  out->half_width = lat->half;
+  return TBPM_OK;
+}
+
+int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, int32_t* nbr) {
+  clear_error();
+  if (!lat) {
+    set_error("tbpm_lattice_export: NULL lattice");
+    return TBPM_EINVAL;
+  }
+  tbpm_ctx* ctx = lat->ctx;
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const int64_t n = lat->n_sites, nf = lat->geom.n_full;
+  const int z = lat->geom.z;
+  if (compact) {
+    if (lat->compact) {
+      TBPM_CK(cudaMemcpyAsync(compact, lat->compact, nf * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+      for (int64_t i = 0; i < nf; ++i) compact[i] = i;
+    }
+  }
+  if (V) {
+    if (lat->v64) {
+      TBPM_CK(cudaMemcpyAsync(V, lat->v64, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+      for (int64_t i = 0; i < n; ++i) V[i] = 0.0;
+    }
+  }
+  if (nbr) {
+    if (lat->ell) {
+      TBPM_CK(cudaMemcpyAsync(nbr, lat->ell, n * z * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    } else {
+      for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < z; ++d) nbr[i * z + d] = (int32_t)neighbour_full(lat->geom, i, d);
+    }
+  }
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ request plumbing
+namespace {
+
+struct Plan {
+  int precision;
+  int S, Spad, logS, spt, P, logP;
+  size_t elem;        // bytes per complex element
+  size_t state_bytes; // one block of Spad states
+  double tau;
+};
+
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+int make_plan(const tbpm_lattice* lat, const tbpm_request* req, Plan* pl) {
+  if (!lat || !req) {
+    set_error("NULL lattice or request");
+    return TBPM_EINVAL;
+  }
+  if (req->precision != TBPM_C64 && req->precision != TBPM_C128) {
+    set_error("unknown precision %d", req->precision);
+    return TBPM_EINVAL;
+  }
+  if (req->n_states < 1 || req->n_states > 32) {
+    set_error("n_states must lie in [1, 32] (got %d)", req->n_states);
+    return TBPM_EINVAL;
+  }
+  if (req->states == TBPM_STATES_SITES) {
+    if (!req->sites) {
+      set_error("site states need a site list");
+      return TBPM_EINVAL;
+    }
+    for (int s = 0; s < req->n_states; ++s)
+      if (req->sites[s] < 0 || req->sites[s] >= lat->n_sites) {
+        set_error("site %lld out of range", (long long)req->sites[s]);
+        return TBPM_EINVAL;
+      }
+  } else if (req->states != TBPM_STATES_RANDOM) {
+    set_error("unknown state kind %d", req->states);
+    return TBPM_EINVAL;
+  }
+  pl->precision = req->precision;
+  pl->S = req->n_states;
+  pl->logS = ilog2(pl->S);
+  pl->Spad = 1 << pl->logS;
+  pl->spt = (req->precision == TBPM_C64 && pl->Spad >= 2) ? 2 : 1;
+  pl->P = pl->Spad / pl->spt;
+  pl->logP = ilog2(pl->P);
+  pl->elem = req->precision == TBPM_C64 ? 8 : 16;
+  pl->state_bytes = (size_t)lat->n_sites * pl->Spad * pl->elem;
+  pl->tau = req->tau == 0.0 ? M_PI : req->tau;
+  if (!(pl->tau > 0.0) || !isfinite(pl->tau)) {
+    set_error("tau must be positive");
+    return TBPM_EINVAL;
+  }
+  return TBPM_OK;
+}
+
+int init_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, void* dst,
+                uint32_t* draws) {
+  const int64_t n = lat->n_sites;
+  if (req->states == TBPM_STATES_RANDOM) {
+    const double inv = 1.0 / sqrt((double)n);
+    const int nb = grid_for(ctx, n * pl.Spad, kT, 32);
+    if (pl.precision == TBPM_C64)
+      k_init_random<float><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, req->state_seed, lat->full_of,
+                                                       inv, (float*)dst, draws);
+    else
+      k_init_random<double><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, req->state_seed, lat->full_of,
+                                                        inv, (double*)dst, draws);
+    TBPM_CK_LAUNCH(ctx);
+  } else {
+    TBPM_CK(cudaMemsetAsync(dst, 0, pl.state_bytes, ctx->stream));
+    TBPM_TRY(ensure(ctx, ctx->ws_aux, sizeof(int64_t) * 32));
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_aux.p, req->sites, sizeof(int64_t) * pl.S, cudaMemcpyHostToDevice, ctx->stream));
+    if (pl.precision == TBPM_C64)
+      k_init_sites<float><<<1, 32, 0, ctx->stream>>>(n, pl.Spad, pl.S, (const int64_t*)ctx->ws_aux.p, (float*)dst);
+    else
+      k_init_sites<double><<<1, 32, 0, ctx->stream>>>(n, pl.Spad, pl.S, (const int64_t*)ctx->ws_aux.p, (double*)dst);
+    TBPM_CK_LAUNCH(ctx);
+  }
+  return TBPM_OK;
+}
+
+int64_t tiles_of(const tbpm_lattice* lat, const Plan& pl) {
+  if (lat->path == TBPM_PATH_CSR) return (lat->n_sites * pl.P + 255) / 256;
+  return lat->geom.n_rows * ((lat->geom.row_sites * pl.P + 255) / 256);
+}
+
+int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* a, int comps) {
+  memset(a, 0, sizeof(*a));
+  a->geom = lat->geom;
+  a->path = lat->path;
+  a->ell = lat->ell;
+  if (lat->has_v) {
+    if (pl.precision == TBPM_C128) TBPM_TRY(ensure_d64(lat));
+    a->diag = pl.precision == TBPM_C128 ? (const void*)lat->d64 : (const void*)lat->d32;
+  } else {
+    a->diag = nullptr;
+  }
+  a->diag_const = (0.0 - lat->H0) / lat->half;
+  a->thop = lat->desc.t / lat->half;
+  a->n_sites = lat->n_sites;
+  a->S = pl.Spad;
+  a->P = pl.P;
+  a->logP = pl.logP;
+  a->n_tiles = tiles_of(lat, pl);
+  a->nblocks = recurrence_blocks(ctx, pl.precision, pl.Spad);
+  TBPM_TRY(ensure(ctx, ctx->ws_partials, sizeof(double) * (size_t)a->nblocks * pl.Spad * comps));
+  a->partials = (double*)ctx->ws_partials.p;
+  if (!ctx->ws_counter.p) {
+    TBPM_TRY(ensure(ctx, ctx->ws_counter, 256));
+    TBPM_CK(cudaMemsetAsync(ctx->ws_counter.p, 0, ctx->ws_counter.cap, ctx->stream));
+  }
+  a->counter = (unsigned*)ctx->ws_counter.p;
+  return TBPM_OK;
+}
+
+// Moments of all Spad states into d_mu [Spad][M][2].
+int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t M,
+                double* d_mu) {
+  if (M < 2 || (M & 1)) {
+    set_error("n_moments must be even and >= 2 (got %lld)", (long long)M);
+    return TBPM_EINVAL;
+  }
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+  RecurrenceArgs a;
+  TBPM_TRY(base_args(ctx, lat, pl, &a, 3));
+  a.mu = d_mu;
+  a.M = (int)M;
+  const int tok = phase_begin(ctx, 0);
+  for (int64_t n = 0; n < M / 2; ++n) {
+    a.cur = ctx->ws_phi[n & 1].p;
+    a.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+    a.step = (int)n;
+    TBPM_TRY(launch_moment_step(ctx, a, pl.precision, n == 0));
+  }
+  phase_end(ctx, tok);
+  return TBPM_OK;
+}
+
+// Coefficient table of one time block of bb steps: coef[n][j] = exp(-i shift (j+1) tau) c_n((j+1) tau),
+// zero once n >= N((j+1) tau).  n_per[j] = N((j+1) tau).
+void block_coefficients(double tau, double shift, int bb, std::vector<double>* coef, std::vector<int>* n_per) {
+  n_per->resize(bb);
+  for (int j = 0; j < bb; ++j) (*n_per)[j] = (int)truncation_order_host((j + 1) * tau);
+  const int nt = *std::max_element(n_per->begin(), n_per->end());
+  coef->assign((size_t)nt * bb * 2, 0.0);
+  std::vector<double> J(nt + 1);
+  for (int j = 0; j < bb; ++j) {
+    const double x = (j + 1) * tau;
+    bessel_j_host(x, nt, J.data());
+    double ps, pc;
+    sincos(-shift * x, &ps, &pc);
+    for (int n = 0; n < (*n_per)[j]; ++n) {
+      const double a = n == 0 ? J[0] : 2.0 * J[n];
+      double cr = 0, ci = 0;
+      switch (n & 3) {
+        case 0: cr = a; break;
+        case 1: ci = -a; break;
+        case 2: cr = -a; break;
+        default: ci = a; break;
+      }
+      (*coef)[((size_t)n * bb + j) * 2] = pc * cr - ps * ci;
+      (*coef)[((size_t)n * bb + j) * 2 + 1] = pc * ci + ps * cr;
+    }
+  }
+}
+
+// b from the Tab. I cost model with per-site costs from the bytes each pass moves:
+// one term of the recurrence reads phi_n, phi_{n-1} and writes phi_{n+1} (24 B per complex64
+// site-state), one axpy reads and writes an accumulator (16 B).  Capped by free memory.
+int64_t choose_block(const tbpm_lattice* lat, const Plan& pl, int64_t n_steps) {
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const int64_t by_mem = (int64_t)std::max<double>(1.0, 0.8 * (double)free_b / (double)pl.state_bytes - 4.0);
+  const int64_t cap = std::min<int64_t>(std::min<int64_t>(by_mem, 256), n_steps);
+  return tbpm_block_opt(n_steps, pl.tau, 3.0, 2.0, cap);
+}
+
+// State-based propagation in blocks of b steps; b = 1 is the sequential form.
+// d_C [Spad][n_steps+1][2].
+int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t n_steps,
+               int64_t b, double* d_C) {
+  if (n_steps < 1) {
+    set_error("n_steps must be >= 1");
+    return TBPM_EINVAL;
+  }
+  b = std::max<int64_t>(1, std::min<int64_t>(b, n_steps));
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_acc, pl.state_bytes * (size_t)b));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, ctx->ws_psi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+
+  AccumArgs g;
+  memset(&g, 0, sizeof(g));
+  TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
+  const int C_len = (int)(n_steps + 1);
+  // C(0) = <psi|psi>
+  TBPM_TRY(launch_dot(ctx, g.r, pl.precision, ctx->ws_psi.p, ctx->ws_psi.p, d_C, C_len));
+
+  const double shift = lat->H0 / lat->half;
+  std::vector<double> coef_full, coef_last;
+  std::vector<int> nper_full, nper_last;
+  block_coefficients(pl.tau, shift, (int)b, &coef_full, &nper_full);
+  const int64_t last_len = n_steps % b;
+  if (last_len) block_coefficients(pl.tau, shift, (int)last_len, &coef_last, &nper_last);
+  const size_t tab_bytes = (coef_full.size() + coef_last.size()) * sizeof(double);
+  TBPM_TRY(ensure(ctx, ctx->ws_table, tab_bytes));
+  double* tab_full = (double*)ctx->ws_table.p;
+  double* tab_last = tab_full + coef_full.size();
+  TBPM_CK(cudaMemcpyAsync(tab_full, coef_full.data(), coef_full.size() * sizeof(double), cudaMemcpyHostToDevice,
+                          ctx->stream));
+  if (last_len)
+    TBPM_CK(cudaMemcpyAsync(tab_last, coef_last.data(), coef_last.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));  // host vectors go out of scope below
+
+  g.acc = ctx->ws_acc.p;
+  g.acc_stride = lat->n_sites * (int64_t)pl.Spad;
+  g.psi = ctx->ws_psi.p;
+  g.C = d_C;
+  g.C_len = C_len;
+  int64_t start = 0;
+  while (start < n_steps) {
+    const int bb = (int)std::min<int64_t>(b, n_steps - start);
+    const std::vector<int>& nper = (bb == b) ? nper_full : nper_last;
+    const double* tab = (bb == b) ? tab_full : tab_last;
+    const int Nb = *std::max_element(nper.begin(), nper.end());
+    g.b = bb;
+    for (int n = 0; n < Nb; ++n) {
+      int j_lo = 0;
+      while (j_lo < bb && nper[j_lo] <= n) ++j_lo;
+      std::vector<int> done;
+      for (int j = j_lo; j < bb; ++j)
+        if (nper[j] - 1 == n) done.push_back(j);
+      const int mode = (n == Nb - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
+      g.r.cur = ctx->ws_phi[n & 1].p;
+      g.r.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+      g.coef = tab + (size_t)n * bb * 2;
+      g.j_lo = j_lo;
+      g.first_term = n == 0;
+      g.j_done = done.empty() ? -1 : done[0];
+      g.j_global = done.empty() ? 0 : (int)(start + done[0] + 1);
+      TBPM_TRY(launch_accum_step(ctx, g, pl.precision, mode));
+      for (size_t q = 1; q < done.size(); ++q) {
+        const int j = done[q];
+        const char* accj = (const char*)ctx->ws_acc.p + (size_t)j * pl.state_bytes;
+        TBPM_TRY(launch_dot(ctx, g.r, pl.precision, ctx->ws_psi.p, accj, d_C + (start + j + 1) * 2, C_len));
+      }
+    }
+    // the block's last state starts the next block
+    const char* last = (const char*)ctx->ws_acc.p + (size_t)(bb - 1) * pl.state_bytes;
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, last, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    start += bb;
+  }
+  return TBPM_OK;
+}
+
+// Correlation of all Spad states into d_C [Spad][n_steps+1][2].
+int run_correlation(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, double* d_C) {
+  const int64_t n_steps = req->n_steps;
+  if (n_steps < 1 || n_steps > (1 << 24)) {
+    set_error("n_steps out of range");
+    return TBPM_EINVAL;
+  }
+  if (req->form == TBPM_CONCURRENT_M) {
+    const int64_t need = truncation_order_host(n_steps * pl.tau);
+    int64_t M = std::max<int64_t>(req->n_moments, need);
+    M += (M & 1);
+    TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 2 * (size_t)M * pl.Spad));
+    double* mu = (double*)ctx->ws_mu.p;
+    TBPM_TRY(run_moments(ctx, lat, req, pl, M, mu));
+    const int n_terms = (int)need + 8;
+    const size_t tab = sizeof(double) * (size_t)n_terms * (n_steps + 1);
+    TBPM_TRY(ensure(ctx, ctx->ws_table, tab + sizeof(int) * (n_steps + 1)));
+    double* table = (double*)ctx->ws_table.p;
+    int* nper = (int*)((char*)ctx->ws_table.p + tab);
+    TBPM_TRY(launch_bessel_table(ctx, pl.tau, (int)n_steps, n_terms, table, nper));
+    TBPM_TRY(launch_corr_from_moments(ctx, table, nper, (int)n_steps, n_terms, mu, pl.Spad, (int)M,
+                                      lat->H0 / lat->half, pl.tau, d_C));
+    return TBPM_OK;
+  }
+  if (req->form == TBPM_SEQUENTIAL) return run_blocks(ctx, lat, req, pl, n_steps, 1, d_C);
+  if (req->form == TBPM_CONCURRENT_S) {
+    const int64_t b = req->time_block > 0 ? req->time_block : choose_block(lat, pl, n_steps);
+    return run_blocks(ctx, lat, req, pl, n_steps, b, d_C);
+  }
+  set_error("unknown form %d", req->form);
+  return TBPM_EINVAL;
+}
+
+int copy_rows(tbpm_ctx* ctx, double* dst, const double* src, int S, size_t row_doubles, cudaMemcpyKind kind) {
+  TBPM_CK(cudaMemcpyAsync(dst, src, sizeof(double) * row_doubles * S, kind, ctx->stream));
+  return TBPM_OK;
+}
+
+int run_dos(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, const double* d_E,
+            int64_t nE, double* d_D) {
+  if (nE < 1) {
+    set_error("n_energies must be >= 1");
+    return TBPM_EINVAL;
+  }
+  if (req->dos_method == TBPM_DOS_JACKSON) {
+    const int64_t M = req->n_moments;
+    TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 2 * (size_t)std::max<int64_t>(M, 2) * pl.Spad));
+    double* mu = (double*)ctx->ws_mu.p;
+    TBPM_TRY(run_moments(ctx, lat, req, pl, M, mu));
+    const int tok = phase_begin(ctx, 1);
+    const int r = (req->recon == TBPM_RECON_TENSOR)
+                      ? launch_dos_jackson_tensor(ctx, mu, pl.S, (int)M, d_E, nE, lat->H0, lat->half, d_D)
+                      : launch_dos_jackson_fp64(ctx, mu, pl.S, (int)M, d_E, nE, lat->H0, lat->half, d_D);
+    phase_end(ctx, tok);
+    return r;
+  }
+  if (req->dos_method == TBPM_DOS_FOURIER) {
+    TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)(req->n_steps + 1) * pl.Spad));
+    double* C = (double*)ctx->ws_out.p;
+    TBPM_TRY(run_correlation(ctx, lat, req, pl, C));
+    return launch_dos_fourier(ctx, C, pl.S, (int)req->n_steps, d_E, nE, pl.tau / lat->half, req->window, d_D);
+  }
+  set_error("unknown dos_method %d", req->dos_method);
+  return TBPM_EINVAL;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI: hot path
+extern "C" {
+
+int tbpm_states_export(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, void* out,
+                       uint32_t* draws) {
+  clear_error();
+  if (!ctx) {
+    set_error("NULL context");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const int64_t n = lat->n_sites;
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  uint32_t* d_draws = nullptr;
+  if (draws && req->states == TBPM_STATES_RANDOM) {
+    TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(uint32_t) * (size_t)n * pl.Spad));
+    d_draws = (uint32_t*)ctx->ws_out.p;
+  }
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, d_draws));
+  if (out) {
+    for (int s = 0; s < pl.S; ++s)
+      TBPM_CK(cudaMemcpy2DAsync((char*)out + (size_t)s * n * pl.elem, pl.elem, (const char*)ctx->ws_phi[0].p + s * pl.elem,
+                                pl.Spad * pl.elem, pl.elem, n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (d_draws)
+    TBPM_CK(cudaMemcpyAsync(draws, d_draws, sizeof(uint32_t) * n * pl.S, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_moments_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_mu) {
+  clear_error();
+  if (!ctx || !d_mu) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const int64_t M = req->n_moments;
+  if (pl.Spad == pl.S) return run_moments(ctx, lat, req, pl, M, d_mu);
+  TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 2 * (size_t)std::max<int64_t>(M, 2) * pl.Spad));
+  TBPM_TRY(run_moments(ctx, lat, req, pl, M, (double*)ctx->ws_mu.p));
+  return copy_rows(ctx, d_mu, (double*)ctx->ws_mu.p, pl.S, 2 * (size_t)M, cudaMemcpyDeviceToDevice);
+}
+
+int tbpm_moments(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* mu) {
+  clear_error();
+  if (!ctx || !mu) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const int64_t M = req->n_moments;
+  TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 2 * (size_t)std::max<int64_t>(M, 2) * pl.Spad));
+  TBPM_TRY(run_moments(ctx, lat, req, pl, M, (double*)ctx->ws_mu.p));
+  TBPM_TRY(copy_rows(ctx, mu, (double*)ctx->ws_mu.p, pl.S, 2 * (size_t)M, cudaMemcpyDeviceToHost));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_correlation_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_C) {
+  clear_error();
+  if (!ctx || !d_C) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const size_t row = 2 * (size_t)(req->n_steps + 1);
+  if (pl.Spad == pl.S) return run_correlation(ctx, lat, req, pl, d_C);
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * row * pl.Spad));
+  TBPM_TRY(run_correlation(ctx, lat, req, pl, (double*)ctx->ws_out.p));
+  return copy_rows(ctx, d_C, (double*)ctx->ws_out.p, pl.S, row, cudaMemcpyDeviceToDevice);
+}
+
+int tbpm_correlation(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* C) {
+  clear_error();
+  if (!ctx || !C) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  if (req->n_steps < 1) {
+    set_error("n_steps must be >= 1");
+    return TBPM_EINVAL;
+  }
+  const size_t row = 2 * (size_t)(req->n_steps + 1);
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * row * pl.Spad));
+  TBPM_TRY(run_correlation(ctx, lat, req, pl, (double*)ctx->ws_out.p));
+  TBPM_TRY(copy_rows(ctx, C, (double*)ctx->ws_out.p, pl.S, row, cudaMemcpyDeviceToHost));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* d_E,
+                    int64_t nE, double* d_D) {
+  clear_error();
+  if (!ctx || !d_E || !d_D) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  return run_dos(ctx, lat, req, pl, d_E, nE, d_D);
+}
+
+int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* energies,
+             int64_t nE, double* D) {
+  clear_error();
+  if (!ctx || !energies || !D) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  if (nE < 1) {
+    set_error("n_energies must be >= 1");
+    return TBPM_EINVAL;
+  }
+  TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)nE * (1 + pl.S)));
+  double* dE = (double*)ctx->ws_energies.p;
+  double* dD = dE + nE;
+  TBPM_CK(cudaMemcpyAsync(dE, energies, sizeof(double) * nE, cudaMemcpyHostToDevice, ctx->stream));
+  TBPM_TRY(run_dos(ctx, lat, req, pl, dE, nE, dD));
+  TBPM_CK(cudaMemcpyAsync(D, dD, sizeof(double) * nE * pl.S, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+// Adjacency operator y_i = sum_{j in nbr(i)} x_j through the hot-path recurrence kernel
+// (first-term mode with zero diagonal and unit hopping); debug export for exact index tests.
+int tbpm_apply_hopping(tbpm_ctx* ctx, const tbpm_lattice* lat_c, int precision, int n_states, const void* x,
+                       void* y) {
+  clear_error();
+  if (!ctx || !lat_c || !x || !y) {
+    set_error("NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  tbpm_request req;
+  memset(&req, 0, sizeof(req));
+  req.precision = precision;
+  req.n_states = n_states;
+  req.states = TBPM_STATES_RANDOM;
+  Plan pl;
+  TBPM_TRY(make_plan(lat, &req, &pl));
+  if (pl.Spad != pl.S) {
+    set_error("tbpm_apply_hopping needs a power-of-two number of states");
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaSetDevice(ctx->device));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 4 * pl.Spad));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, x, pl.state_bytes, cudaMemcpyHostToDevice, ctx->stream));
+  RecurrenceArgs a;
+  TBPM_TRY(base_args(ctx, lat, pl, &a, 3));
+  a.diag = nullptr;
+  a.diag_const = 0.0;
+  a.thop = 1.0;
+  a.mu = (double*)ctx->ws_mu.p;
+  a.M = 2;
+  a.cur = ctx->ws_phi[0].p;
+  a.prev_out = ctx->ws_phi[1].p;
+  TBPM_TRY(launch_moment_step(ctx, a, pl.precision, true));
+  TBPM_CK(cudaMemcpyAsync(y, ctx->ws_phi[1].p, pl.state_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+// ---------------------------------------------------------------- cost model (Sec. II.B, Tab. I)
+int tbpm_block_counts(int64_t n_steps, int64_t b, double tau, int64_t out[3]) {
+  clear_error();
+  if (n_steps < 1 || b < 1 || !out || !(tau > 0)) {
+    set_error("tbpm_block_counts: invalid argument");
+    return TBPM_EINVAL;
+  }
+  int64_t amxsy = 0, axpy = 0;
+  std::vector<int64_t> N(std::min(b, n_steps) + 1);
+  for (int64_t j = 1; j <= std::min(b, n_steps); ++j) N[j] = truncation_order_host(j * tau);
+  for (int64_t start = 0; start < n_steps; start += b) {
+    const int64_t bb = std::min(b, n_steps - start);
+    int64_t mx = 0;
+    for (int64_t j = 1; j <= bb; ++j) {
+      axpy += N[j];
+      mx = std::max(mx, N[j]);
+    }
+    amxsy += mx;
+  }
+  out[0] = amxsy;
+  out[1] = axpy;
+  out[2] = n_steps;
+  return TBPM_OK;
+}
+
+int64_t tbpm_block_opt(int64_t n_steps, double tau, double t_amxsy, double t_axpy, int64_t b_max) {
+  clear_error();
+  if (n_steps < 1 || !(tau > 0)) return 1;
+  b_max = std::max<int64_t>(1, std::min(b_max, n_steps));
+  std::vector<int64_t> N(b_max + 1), pre(b_max + 1, 0);
+  for (int64_t j = 1; j <= b_max; ++j) {
+    N[j] = truncation_order_host(j * tau);
+    pre[j] = pre[j - 1] + N[j];
+  }
+  int64_t best = 1;
+  double best_c = -1;
+  for (int64_t b = 1; b <= b_max; ++b) {
+    const int64_t full = n_steps / b, rest = n_steps % b;
+    const double am = (double)full * N[b] + (rest ? (double)N[rest] : 0.0);
+    const double ax = (double)full * pre[b] + (rest ? (double)pre[rest] : 0.0);
+    const double c = am * t_amxsy + ax * t_axpy;
+    if (best_c < 0 || c < best_c) {
+      best_c = c;
+      best = b;
+    }
+  }
+  return best;
+}
+
+}  // extern "C"

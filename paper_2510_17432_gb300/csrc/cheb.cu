@@ -1,0 +1,554 @@
+// Chebyshev recurrence kernels for blocks of S states (App. B, Eq. cheb_relation):
+//     phi_1 = H~ phi_0,   phi_{n+1} = 2 H~ phi_n - phi_{n-1},   H~ = (H - H0)/|H|,
+// with H applied matrix-free on square / honeycomb / simple-cubic stencils, or from
+// compact ELL neighbour lists on vacancy lattices (CSR/ELL path).
+//
+// States are interleaved [site][state] so one thread unit moves 16 bytes (two complex64
+// states, or one complex128 state) and the neighbour loads of all S states of a site are
+// contiguous.  Each pass is fused with the inner products the method needs:
+//   * moment pass (Sec. II.A, moment-based form, cost halving of Eq. cheby_prod):
+//       A_n = <phi_n|phi_n>, B_n = <phi_{n+1}|phi_n>  ->  m_{2n} = 2A_n - m_0, m_{2n+1} = 2B_n - m_1;
+//   * accumulation pass (Sec. II.A Eq. TE, time blocks of Sec. II.B; b = 1 is the sequential
+//     form): acc_j += c_n(j tau~) phi_n for every step j of the block still open at term n,
+//     and C(t_j) = <psi|acc_j> when term n closes step j.
+// Reductions are deterministic: compensated FP32 (Neumaier) per thread for complex64,
+// then FP64 warp and block trees, per-block partials, and a fixed-order sum by the last
+// block to finish.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// ------------------------------------------------------------------ 16-byte state packs
+template <typename R, int SPT>
+struct Pack {
+  R v[2 * SPT];
+};
+
+template <typename R, int SPT>
+__device__ __forceinline__ Pack<R, SPT> ld(const Pack<R, SPT>* p) {
+  Pack<R, SPT> r;
+  if constexpr (sizeof(Pack<R, SPT>) == 16) {
+    if constexpr (sizeof(R) == 4) {
+      const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
+      const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+      r.v[0] = q.x; r.v[1] = q.y;
+    }
+  } else {
+    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+
+template <typename R, int SPT>
+__device__ __forceinline__ Pack<R, SPT> ld_stream(const Pack<R, SPT>* p) {
+  Pack<R, SPT> r;
+  if constexpr (sizeof(Pack<R, SPT>) == 16) {
+    if constexpr (sizeof(R) == 4) {
+      const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
+      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
+    } else {
+      const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
+      r.v[0] = q.x; r.v[1] = q.y;
+    }
+  } else {
+    const float2 q = __ldcs(reinterpret_cast<const float2*>(p));
+    r.v[0] = q.x; r.v[1] = q.y;
+  }
+  return r;
+}
+
+template <typename R, int SPT>
+__device__ __forceinline__ void st(Pack<R, SPT>* p, const Pack<R, SPT>& r) {
+  if constexpr (sizeof(Pack<R, SPT>) == 16) {
+    if constexpr (sizeof(R) == 4) {
+      *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    } else {
+      *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+    }
+  } else {
+    *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
+  }
+}
+
+// ------------------------------------------------------------------ accumulators
+// Neumaier-compensated FP32 sum (complex64 path) or plain FP64 sum (complex128 path).
+template <typename R>
+struct Acc;
+
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// ------------------------------------------------------------------ grid reduction
+// Every thread holds NV values for its states (states p*SPT .. p*SPT+SPT-1, C values each,
+// p = threadIdx.x % P).  Sums them over the grid and calls fin(q, total) for q = s*C + c in
+// the last block.  Deterministic: fixed trees and a fixed block order.
+template <int NV, int SPT, int C, typename Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], int P, int S, double* partials,
+                                            unsigned* counter, int nblocks, Fin fin) {
+  static_assert(NV == SPT * C, "values per thread");
+  __shared__ double red[kWarps][32][NV];
+  __shared__ unsigned ticket;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    for (int off = 16; off >= P; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  }
+  if (lane < P) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp][lane][k] = v[k];
+  }
+  __syncthreads();
+  const int SC = S * C;
+  if (threadIdx.x < SC) {
+    const int q = threadIdx.x, s = q / C, c = q - s * C;
+    const int p = s / SPT, k = (s - p * SPT) * C + c;
+    double acc = 0.0;
+    for (int w = 0; w < kWarps; ++w) acc += red[w][p][k];
+    partials[(size_t)blockIdx.x * SC + q] = acc;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
+  __syncthreads();
+  if (ticket != (unsigned)(nblocks - 1)) return;
+  // last block: sum the partials in block order, one warp per output value
+  __threadfence();
+  for (int q = warp; q < SC; q += kWarps) {
+    double acc = 0.0;
+    for (int b = lane; b < nblocks; b += 32) acc += __ldcg(partials + (size_t)b * SC + q);
+    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) fin(q, acc);
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+// ------------------------------------------------------------------ H~ phi for one unit
+// Computes hphi = sum over neighbours of phi_j and the per-site diagonal term.
+template <int KIND, bool CSR, typename R, int SPT>
+struct Row {
+  int64_t base, up, dn, zup, zdn;
+};
+
+template <int KIND, bool CSR, typename R, int SPT>
+__device__ __forceinline__ void neighbour_sum(const RecurrenceArgs& a, const Pack<R, SPT>* cur,
+                                              int64_t site, int64_t x, int64_t sir, const Row<KIND, CSR, R, SPT>& rw,
+                                              int p, Pack<R, SPT>& h) {
+#pragma unroll
+  for (int k = 0; k < 2 * SPT; ++k) h.v[k] = R(0);
+  auto add = [&](int64_t j) {
+    if (j >= 0) {
+      const Pack<R, SPT> q = ld(cur + j * a.P + p);
+#pragma unroll
+      for (int k = 0; k < 2 * SPT; ++k) h.v[k] += q.v[k];
+    }
+  };
+  if constexpr (CSR) {
+    const int z = a.geom.z;
+    for (int d = 0; d < z; ++d) add((int64_t)__ldg(a.ell + site * z + d));
+  } else if constexpr (KIND == TBPM_HONEYCOMB) {
+    const int64_t Lx = a.geom.Lx;
+    const int64_t xc = sir >> 1;
+    const int s = (int)(sir & 1);
+    add(rw.base + (sir ^ 1));                         // partner in the same cell
+    int64_t xn = xc + (s ? 1 : -1);                   // A: B(x-1,y); B: A(x+1,y)
+    bool ok = true;
+    xn = wrap_coord(xn, Lx, a.geom.pbc_x, &ok);
+    add(ok ? rw.base + 2 * xn + (1 - s) : -1);
+    const int64_t nrow = s ? rw.up : rw.dn;           // A: B(x,y-1); B: A(x,y+1)
+    add(nrow >= 0 ? nrow + 2 * xc + (1 - s) : -1);
+  } else {
+    const int64_t Lx = a.geom.Lx;
+    bool ok = true;
+    int64_t xp = wrap_coord(x + 1, Lx, a.geom.pbc_x, &ok);
+    add(ok ? rw.base + xp : -1);
+    ok = true;
+    int64_t xm = wrap_coord(x - 1, Lx, a.geom.pbc_x, &ok);
+    add(ok ? rw.base + xm : -1);
+    add(rw.up >= 0 ? rw.up + x : -1);
+    add(rw.dn >= 0 ? rw.dn + x : -1);
+    if constexpr (KIND == TBPM_CUBIC) {
+      add(rw.zup >= 0 ? rw.zup + x : -1);
+      add(rw.zdn >= 0 ? rw.zdn + x : -1);
+    }
+  }
+}
+
+// Site base index of the row (y, z) and of its neighbouring rows (-1 when dropped).
+template <int KIND, bool CSR, typename R, int SPT>
+__device__ __forceinline__ Row<KIND, CSR, R, SPT> row_info(const Geom& g, int64_t row) {
+  Row<KIND, CSR, R, SPT> rw{};
+  const int64_t rs = g.row_sites;
+  int64_t y = row, zc = 0;
+  if constexpr (KIND == TBPM_CUBIC) {
+    y = row % g.Ly;
+    zc = row / g.Ly;
+  }
+  rw.base = row * rs;
+  bool ok = true;
+  int64_t yy = wrap_coord(y + 1, g.Ly, g.pbc_y, &ok);
+  rw.up = ok ? (zc * g.Ly + yy) * rs : -1;
+  ok = true;
+  yy = wrap_coord(y - 1, g.Ly, g.pbc_y, &ok);
+  rw.dn = ok ? (zc * g.Ly + yy) * rs : -1;
+  if constexpr (KIND == TBPM_CUBIC) {
+    ok = true;
+    int64_t zz = wrap_coord(zc + 1, g.Lz, g.pbc_z, &ok);
+    rw.zup = ok ? (zz * g.Ly + y) * rs : -1;
+    ok = true;
+    zz = wrap_coord(zc - 1, g.Lz, g.pbc_z, &ok);
+    rw.zdn = ok ? (zz * g.Ly + y) * rs : -1;
+  }
+  return rw;
+}
+
+// Iterates over the thread's units: f(site, x, sir, row) for every valid unit.
+// Stencil: tiles of kThreads units along one x-line; CSR: linear tiles.
+template <int KIND, bool CSR, typename R, int SPT, typename F>
+__device__ __forceinline__ void for_each_unit(const RecurrenceArgs& a, F f) {
+  const int tid = threadIdx.x;
+  if constexpr (CSR) {
+    const int64_t n_units = a.n_sites * a.P;
+    const int64_t n_tiles = (n_units + kThreads - 1) / kThreads;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int64_t u = t * kThreads + tid;
+      if (u < n_units) {
+        Row<KIND, CSR, R, SPT> rw{};
+        f(u >> a.logP, (int64_t)0, (int64_t)0, rw);
+      }
+    }
+  } else {
+    const int64_t upr = a.geom.row_sites * a.P;
+    const int64_t tpr = (upr + kThreads - 1) / kThreads;
+    const int64_t n_tiles = a.geom.n_rows * tpr;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+      const int64_t row = t / tpr;
+      const int64_t u = (t - row * tpr) * kThreads + tid;
+      if (u < upr) {
+        const Row<KIND, CSR, R, SPT> rw = row_info<KIND, CSR, R, SPT>(a.geom, row);
+        const int64_t sir = u >> a.logP;
+        const int64_t x = (KIND == TBPM_HONEYCOMB) ? (sir >> 1) : sir;
+        f(rw.base + sir, x, sir, rw);
+      }
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R site_diag(const RecurrenceArgs& a, int64_t site) {
+  if (a.diag == nullptr) return (R)a.diag_const;
+  return __ldg(reinterpret_cast<const R*>(a.diag) + site);
+}
+
+// ------------------------------------------------------------------ moment pass
+template <int KIND, bool CSR, typename R, int SPT, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_moment_step(RecurrenceArgs a) {
+  using PK = Pack<R, SPT>;
+  const PK* cur = reinterpret_cast<const PK*>(a.cur);
+  PK* po = reinterpret_cast<PK*>(a.prev_out);
+  const int p = threadIdx.x & (a.P - 1);
+  const R th = FIRST ? (R)a.thop : (R)(2.0 * a.thop);
+  Acc<R> A[SPT], Br[SPT], Bi[SPT];
+
+  for_each_unit<KIND, CSR, R, SPT>(a, [&](int64_t site, int64_t x, int64_t sir,
+                                          const Row<KIND, CSR, R, SPT>& rw) {
+    const int64_t off = site * a.P + p;
+    const PK ph = ld(cur + off);
+    PK h;
+    neighbour_sum<KIND, CSR, R, SPT>(a, cur, site, x, sir, rw, p, h);
+    R d = site_diag<R>(a, site);
+    if (!FIRST) d = d + d;
+    PK o;
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int k = 0; k < 2 * SPT; ++k) o.v[k] = d * ph.v[k] + th * h.v[k];
+    } else {
+      const PK pv = ld_stream(po + off);
+#pragma unroll
+      for (int k = 0; k < 2 * SPT; ++k) o.v[k] = d * ph.v[k] + th * h.v[k] - pv.v[k];
+    }
+    st(po + off, o);
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      const R pr = ph.v[2 * k], pi = ph.v[2 * k + 1], orr = o.v[2 * k], oi = o.v[2 * k + 1];
+      A[k].add(pr * pr + pi * pi);
+      Br[k].add(orr * pr + oi * pi);
+      Bi[k].add(orr * pi - oi * pr);
+    }
+  });
+
+  double v[3 * SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    v[3 * k] = A[k].value();
+    v[3 * k + 1] = Br[k].value();
+    v[3 * k + 2] = Bi[k].value();
+  }
+  double* mu = a.mu;
+  const int M = a.M, n = a.step;
+  grid_reduce<3 * SPT, SPT, 3>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+    const int s = q / 3, c = q - 3 * s;
+    double* ms = mu + (size_t)s * M * 2;
+    if (FIRST) {
+      if (c == 0) { ms[0] = val; ms[1] = 0.0; }
+      else if (c == 1) ms[2] = val;
+      else ms[3] = val;
+    } else {
+      if (c == 0) { ms[4 * n] = 2.0 * val - ms[0]; ms[4 * n + 1] = -ms[1]; }
+      else if (c == 1) ms[4 * n + 2] = 2.0 * val - ms[2];
+      else ms[4 * n + 3] = 2.0 * val - ms[3];
+    }
+  });
+}
+
+// ------------------------------------------------------------------ accumulation pass
+// MODE: ACC_FIRST (phi_1 = H~ phi_0), ACC_REGULAR, ACC_NOSPMV (last term: accumulate only).
+template <int KIND, bool CSR, typename R, int SPT, int MODE>
+__global__ void __launch_bounds__(kThreads) k_accum_step(AccumArgs g) {
+  using PK = Pack<R, SPT>;
+  const RecurrenceArgs& a = g.r;
+  const PK* cur = reinterpret_cast<const PK*>(a.cur);
+  PK* po = reinterpret_cast<PK*>(a.prev_out);
+  PK* acc = reinterpret_cast<PK*>(g.acc);
+  const PK* psi = reinterpret_cast<const PK*>(g.psi);
+  const int p = threadIdx.x & (a.P - 1);
+  const R th = (MODE == ACC_FIRST) ? (R)a.thop : (R)(2.0 * a.thop);
+  const int64_t astr = g.acc_stride / SPT;  // in packs
+  Acc<R> Cr[SPT], Ci[SPT];
+
+  for_each_unit<KIND, CSR, R, SPT>(a, [&](int64_t site, int64_t x, int64_t sir,
+                                          const Row<KIND, CSR, R, SPT>& rw) {
+    const int64_t off = site * a.P + p;
+    const PK ph = ld(cur + off);
+    if constexpr (MODE != ACC_NOSPMV) {
+      PK h;
+      neighbour_sum<KIND, CSR, R, SPT>(a, cur, site, x, sir, rw, p, h);
+      R d = site_diag<R>(a, site);
+      if (MODE != ACC_FIRST) d = d + d;
+      PK o;
+      if constexpr (MODE == ACC_FIRST) {
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) o.v[k] = d * ph.v[k] + th * h.v[k];
+      } else {
+        const PK pv = ld_stream(po + off);
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) o.v[k] = d * ph.v[k] + th * h.v[k] - pv.v[k];
+      }
+      st(po + off, o);
+    }
+    for (int j = g.j_lo; j < g.b; ++j) {
+      const R cr = (R)__ldg(g.coef + 2 * j), ci = (R)__ldg(g.coef + 2 * j + 1);
+      PK* aj = acc + (int64_t)j * astr + off;
+      PK av;
+      if (g.first_term) {
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) av.v[k] = R(0);
+      } else {
+        av = ld(aj);
+      }
+#pragma unroll
+      for (int k = 0; k < SPT; ++k) {
+        const R pr = ph.v[2 * k], pi = ph.v[2 * k + 1];
+        av.v[2 * k] += cr * pr - ci * pi;
+        av.v[2 * k + 1] += cr * pi + ci * pr;
+      }
+      st(aj, av);
+      if (j == g.j_done) {
+        const PK s0 = ld(psi + off);
+#pragma unroll
+        for (int k = 0; k < SPT; ++k) {
+          const R sr = s0.v[2 * k], si = s0.v[2 * k + 1];
+          Cr[k].add(sr * av.v[2 * k] + si * av.v[2 * k + 1]);
+          Ci[k].add(sr * av.v[2 * k + 1] - si * av.v[2 * k]);
+        }
+      }
+    }
+  });
+
+  if (g.j_done < 0) return;
+  double v[2 * SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    v[2 * k] = Cr[k].value();
+    v[2 * k + 1] = Ci[k].value();
+  }
+  double* C = g.C;
+  const int len = g.C_len, jg = g.j_global;
+  grid_reduce<2 * SPT, SPT, 2>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+    const int s = q >> 1, c = q & 1;
+    C[((size_t)s * len + jg) * 2 + c] = val;
+  });
+}
+
+// ------------------------------------------------------------------ plain dot <x|y> per state
+template <typename R, int SPT>
+__global__ void __launch_bounds__(kThreads) k_dot(RecurrenceArgs a, const void* xv, const void* yv,
+                                                  double* out, int out_stride) {
+  using PK = Pack<R, SPT>;
+  const PK* X = reinterpret_cast<const PK*>(xv);
+  const PK* Y = reinterpret_cast<const PK*>(yv);
+  const int p = threadIdx.x & (a.P - 1);
+  Acc<R> Cr[SPT], Ci[SPT];
+  const int64_t n_units = a.n_sites * a.P;
+  for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < n_units;
+       u += (int64_t)gridDim.x * kThreads) {
+    const PK xs = ld(X + u), ys = ld(Y + u);
+#pragma unroll
+    for (int k = 0; k < SPT; ++k) {
+      Cr[k].add(xs.v[2 * k] * ys.v[2 * k] + xs.v[2 * k + 1] * ys.v[2 * k + 1]);
+      Ci[k].add(xs.v[2 * k] * ys.v[2 * k + 1] - xs.v[2 * k + 1] * ys.v[2 * k]);
+    }
+  }
+  double v[2 * SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    v[2 * k] = Cr[k].value();
+    v[2 * k + 1] = Ci[k].value();
+  }
+  grid_reduce<2 * SPT, SPT, 2>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+    const int s = q >> 1, c = q & 1;
+    out[(size_t)s * out_stride * 2 + c] = val;
+  });
+}
+
+// ------------------------------------------------------------------ dispatch
+template <typename R, int SPT>
+static void* moment_kernel(int kind, bool csr, bool first) {
+  if (csr) return first ? (void*)k_moment_step<0, true, R, SPT, true> : (void*)k_moment_step<0, true, R, SPT, false>;
+  switch (kind) {
+    case TBPM_SQUARE:
+      return first ? (void*)k_moment_step<TBPM_SQUARE, false, R, SPT, true>
+                   : (void*)k_moment_step<TBPM_SQUARE, false, R, SPT, false>;
+    case TBPM_HONEYCOMB:
+      return first ? (void*)k_moment_step<TBPM_HONEYCOMB, false, R, SPT, true>
+                   : (void*)k_moment_step<TBPM_HONEYCOMB, false, R, SPT, false>;
+    default:
+      return first ? (void*)k_moment_step<TBPM_CUBIC, false, R, SPT, true>
+                   : (void*)k_moment_step<TBPM_CUBIC, false, R, SPT, false>;
+  }
+}
+
+template <typename R, int SPT, int MODE>
+static void* accum_kernel_m(int kind, bool csr) {
+  if (csr) return (void*)k_accum_step<0, true, R, SPT, MODE>;
+  switch (kind) {
+    case TBPM_SQUARE: return (void*)k_accum_step<TBPM_SQUARE, false, R, SPT, MODE>;
+    case TBPM_HONEYCOMB: return (void*)k_accum_step<TBPM_HONEYCOMB, false, R, SPT, MODE>;
+    default: return (void*)k_accum_step<TBPM_CUBIC, false, R, SPT, MODE>;
+  }
+}
+
+template <typename R, int SPT>
+static void* accum_kernel(int kind, bool csr, int mode) {
+  if (mode == ACC_FIRST) return accum_kernel_m<R, SPT, ACC_FIRST>(kind, csr);
+  if (mode == ACC_REGULAR) return accum_kernel_m<R, SPT, ACC_REGULAR>(kind, csr);
+  return accum_kernel_m<R, SPT, ACC_NOSPMV>(kind, csr);
+}
+
+static int spt_of(int precision, int S) { return (precision == TBPM_C64 && S >= 2) ? 2 : 1; }
+
+// Upper bound of the persistent grid (partials are sized for it).
+int recurrence_blocks(tbpm_ctx* ctx, int precision, int S) {
+  (void)precision;
+  (void)S;
+  return ctx->num_sms * 8;
+}
+
+// Resident 256-thread blocks per SM of one kernel (occupancy API, cached per kernel).
+static int resident_per_sm(void* fn) {
+  static std::mutex mu;
+  static std::unordered_map<void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(fn);
+  if (it != cache.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kThreads, 0) != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  nb = nb > 8 ? 8 : nb;
+  cache[fn] = nb;
+  return nb;
+}
+
+// Persistent grid: every resident slot filled once, never more blocks than tiles.
+static int persistent_grid(tbpm_ctx* ctx, void* fn, int64_t n_tiles) {
+  const int64_t g = (int64_t)ctx->num_sms * resident_per_sm(fn);
+  return (int)(n_tiles < g ? (n_tiles > 0 ? n_tiles : 1) : g);
+}
+
+static int launch(tbpm_ctx* ctx, void* fn, int nblocks, void** args) {
+  cudaError_t e = cudaLaunchKernel(fn, dim3(nblocks), dim3(kThreads), args, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("kernel launch: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  return TBPM_OK;
+}
+
+int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first) {
+  const bool csr = a.path == TBPM_PATH_CSR;
+  const int spt = spt_of(precision, a.S);
+  void* fn;
+  if (precision == TBPM_C128) fn = moment_kernel<double, 1>(a.geom.kind, csr, first);
+  else if (spt == 2) fn = moment_kernel<float, 2>(a.geom.kind, csr, first);
+  else fn = moment_kernel<float, 1>(a.geom.kind, csr, first);
+  RecurrenceArgs aa = a;
+  aa.nblocks = persistent_grid(ctx, fn, a.n_tiles);
+  void* args[] = {&aa};
+  return launch(ctx, fn, aa.nblocks, args);
+}
+
+int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode) {
+  const bool csr = g.r.path == TBPM_PATH_CSR;
+  const int spt = spt_of(precision, g.r.S);
+  void* fn;
+  if (precision == TBPM_C128) fn = accum_kernel<double, 1>(g.r.geom.kind, csr, mode);
+  else if (spt == 2) fn = accum_kernel<float, 2>(g.r.geom.kind, csr, mode);
+  else fn = accum_kernel<float, 1>(g.r.geom.kind, csr, mode);
+  AccumArgs gg = g;
+  gg.r.nblocks = persistent_grid(ctx, fn, g.r.n_tiles);
+  void* args[] = {&gg};
+  return launch(ctx, fn, gg.r.nblocks, args);
+}
+
+int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
+               double* out, int out_stride) {
+  const int spt = spt_of(precision, a.S);
+  void* fn;
+  if (precision == TBPM_C128) fn = (void*)k_dot<double, 1>;
+  else if (spt == 2) fn = (void*)k_dot<float, 2>;
+  else fn = (void*)k_dot<float, 1>;
+  RecurrenceArgs aa = a;
+  aa.nblocks = persistent_grid(ctx, fn, (a.n_sites * a.P + kThreads - 1) / kThreads);
+  void* args[] = {&aa, &x, &y, &out, &out_stride};
+  return launch(ctx, fn, aa.nblocks, args);
+}
+
+}  // namespace tbpm

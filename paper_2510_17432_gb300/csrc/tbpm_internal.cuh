@@ -1,0 +1,263 @@
+// Internal declarations shared by the library's translation units.
+//
+// Device-side building blocks:
+//   * Philox4x32-10 (Salmon et al., SC'11): the counter-based generator behind the
+//     disorder, vacancy and random-phase draws.
+//   * lattice geometry: full site index -> neighbour full index for the square,
+//     honeycomb and simple-cubic stencils in their fixed neighbour order.
+//   * the grid-wide deterministic reduction used by every fused inner product:
+//     per-thread compensated FP32 sums -> FP64 warp/block trees -> per-block partials
+//     -> the last block to finish sums the partials in block order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tbpm.h"
+
+namespace tbpm {
+
+// ------------------------------------------------------------------ error reporting
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define TBPM_CK(call)                                                                  \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      ::tbpm::set_error("%s:%d %s: %s", __FILE_NAME__, __LINE__, #call, cudaGetErrorString(e_)); \
+      return TBPM_ECUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+
+#define TBPM_CK_LAUNCH(ctx)                                                            \
+  do {                                                                                 \
+    (ctx)->launches++;                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) {                                                           \
+      ::tbpm::set_error("%s:%d kernel launch: %s", __FILE_NAME__, __LINE__, cudaGetErrorString(e_)); \
+      return TBPM_ECUDA;                                                               \
+    }                                                                                  \
+  } while (0)
+
+#define TBPM_TRY(expr)            \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != TBPM_OK) return r_; \
+  } while (0)
+
+// ------------------------------------------------------------------ Philox4x32-10
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+// 10 rounds of the Philox S-box: (c0,c1,c2,c3) -> (hi(M1 c2)^c1^k0, lo(M1 c2), hi(M0 c0)^c3^k1, lo(M0 c0)),
+// key advanced by the Weyl constants between rounds.
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = mulhi32(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+enum { STREAM_DISORDER = 0, STREAM_VACANCY = 1, STREAM_PHASE = 2 };
+
+// First output word at counter (index, stream, sub) under the 64-bit seed.
+__host__ __device__ __forceinline__ uint32_t draw_u32(uint64_t seed, uint64_t index, uint32_t stream,
+                                                      uint32_t sub) {
+  return philox10(make_uint4((uint32_t)index, (uint32_t)(index >> 32), stream, sub), (uint32_t)seed,
+                  (uint32_t)(seed >> 32))
+      .x;
+}
+
+// ------------------------------------------------------------------ lattice geometry
+struct Geom {
+  int kind;          // TBPM_SQUARE / TBPM_HONEYCOMB / TBPM_CUBIC
+  int64_t Lx, Ly, Lz;
+  int pbc_x, pbc_y, pbc_z;
+  int z;             // coordination
+  int64_t n_full;
+  int64_t row_sites; // sites on one x-line: Lx, or 2*Lx for the honeycomb
+  int64_t n_rows;    // Ly * Lz
+};
+
+__host__ __device__ __forceinline__ int64_t wrap_coord(int64_t v, int64_t n, int periodic, bool* ok) {
+  if (v < 0) {
+    if (!periodic) { *ok = false; return 0; }
+    return v + n;
+  }
+  if (v >= n) {
+    if (!periodic) { *ok = false; return 0; }
+    return v - n;
+  }
+  return v;
+}
+
+// Neighbour d (fixed order) of full site i, or -1 when an open boundary drops it.
+__host__ __device__ __forceinline__ int64_t neighbour_full(const Geom& g, int64_t i, int d) {
+  bool ok = true;
+  if (g.kind == TBPM_SQUARE) {
+    const int64_t x = i % g.Lx, y = i / g.Lx;
+    const int dx = (d == 0) ? 1 : (d == 1) ? -1 : 0;
+    const int dy = (d == 2) ? 1 : (d == 3) ? -1 : 0;
+    const int64_t xx = wrap_coord(x + dx, g.Lx, g.pbc_x, &ok);
+    const int64_t yy = wrap_coord(y + dy, g.Ly, g.pbc_y, &ok);
+    return ok ? yy * g.Lx + xx : -1;
+  } else if (g.kind == TBPM_HONEYCOMB) {
+    const int64_t s = i & 1, c = i >> 1;
+    const int64_t x = c % g.Lx, y = c / g.Lx;
+    // A: B(x,y), B(x-1,y), B(x,y-1);  B: A(x,y), A(x+1,y), A(x,y+1)
+    const int sg = s == 0 ? -1 : 1;
+    const int dx = (d == 1) ? sg : 0;
+    const int dy = (d == 2) ? sg : 0;
+    const int64_t xx = wrap_coord(x + dx, g.Lx, g.pbc_x, &ok);
+    const int64_t yy = wrap_coord(y + dy, g.Ly, g.pbc_y, &ok);
+    return ok ? 2 * (yy * g.Lx + xx) + (1 - s) : -1;
+  } else {
+    const int64_t x = i % g.Lx, y = (i / g.Lx) % g.Ly, zc = i / (g.Lx * g.Ly);
+    const int dx = (d == 0) ? 1 : (d == 1) ? -1 : 0;
+    const int dy = (d == 2) ? 1 : (d == 3) ? -1 : 0;
+    const int dz = (d == 4) ? 1 : (d == 5) ? -1 : 0;
+    const int64_t xx = wrap_coord(x + dx, g.Lx, g.pbc_x, &ok);
+    const int64_t yy = wrap_coord(y + dy, g.Ly, g.pbc_y, &ok);
+    const int64_t zz = wrap_coord(zc + dz, g.Lz, g.pbc_z, &ok);
+    return ok ? (zz * g.Ly + yy) * g.Lx + xx : -1;
+  }
+}
+
+// ------------------------------------------------------------------ context & lattice
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace tbpm
+
+struct tbpm_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  // cached workspaces (grow-only, stream-ordered allocations)
+  tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
+      ws_energies, ws_recon;
+  double* pinned = nullptr;
+  size_t pinned_cap = 0;
+  // phase timing with CUDA events on the context stream (tbpm_profile)
+  bool profiling = false;
+  struct Phase {
+    cudaEvent_t a, b;
+    int kind;        // 0 = recurrence, 1 = reconstruction
+    int64_t launches;
+  };
+  std::vector<Phase> phases;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+struct tbpm_lattice {
+  tbpm_ctx* ctx = nullptr;
+  tbpm_lattice_desc desc{};
+  tbpm::Geom geom{};
+  int path = TBPM_PATH_STENCIL;
+  int64_t n_sites = 0;
+  int64_t n_bonds = 0;
+  double E_min = 0, E_max = 0, H0 = 0, half = 1;
+  bool has_v = false;
+  // rescaled on-site terms D_i = (V_i - H0)/|H| per active site (FP32 and FP64 copies)
+  float* d32 = nullptr;
+  double* d64 = nullptr;
+  double* v64 = nullptr;       // raw V_i (FP64) per active site, for export
+  // CSR/ELL path: compact neighbour lists [n_sites][z] (-1 = none)
+  int32_t* ell = nullptr;
+  int64_t* compact = nullptr;  // [n_full] compact index or -1 (CSR path only)
+  int64_t* full_of = nullptr;  // [n_sites] full index of each compact site (CSR path only)
+};
+
+namespace tbpm {
+
+// grow-only device workspace on the context stream
+int ensure(tbpm_ctx* ctx, DevBuf& b, size_t bytes);
+
+// phase timing: begin returns a token (-1 when profiling is off); end closes it
+int phase_begin(tbpm_ctx* ctx, int kind);
+void phase_end(tbpm_ctx* ctx, int token);
+
+// ------------------------------------------------------------------ launch plumbing
+struct RecurrenceArgs {
+  // states
+  const void* cur;     // phi_n      [n_sites][S]
+  void* prev_out;      // phi_{n-1} in, phi_{n+1} out
+  // lattice
+  Geom geom;
+  int path;
+  const int32_t* ell;  // CSR/ELL neighbour lists
+  const void* diag;    // per-site D_i (float* or double*), or null when the lattice is clean
+  double diag_const;   // D when diag == null
+  double thop;         // t / |H|
+  int64_t n_sites;
+  // states-per-thread layout: P = S / spt thread units per site
+  int S, P, logP;
+  int64_t n_tiles;     // work tiles of 256 thread units
+  // reduction
+  double* partials;
+  unsigned* counter;
+  int nblocks;
+  // moments output (device [S][M][2]) and step index
+  double* mu;
+  int M;
+  int step;
+};
+
+struct AccumArgs {
+  RecurrenceArgs r;     // recurrence part (cur, prev_out, lattice, reduction buffers)
+  void* acc;            // accumulators [b][n_sites][S]
+  int64_t acc_stride;   // elements (complex) between accumulators
+  const double* coef;   // [n_terms][b] complex (re, im) incl. the exp(-i H0 t) phase
+  int b;
+  int j_lo;             // first accumulator still active at this term
+  int j_done;           // accumulator whose last term this is, or -1
+  int first_term;       // 1: write acc = c phi (n == 0) instead of acc += c phi
+  const void* psi;      // initial states for <psi|acc_j>
+  double* C;            // device [S][n_steps+1][2]
+  int C_len;            // n_steps + 1
+  int j_global;         // time index of accumulator j_done
+};
+
+int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first);
+int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
+int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
+               double* out /* device [S][2] at stride out_stride */, int out_stride);
+int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
+
+enum { ACC_FIRST = 0, ACC_REGULAR = 1, ACC_NOSPMV = 2 };
+
+// reconstruction
+int launch_bessel_table(tbpm_ctx* ctx, double tau, int n_steps, int n_terms, double* table,
+                        int* n_per_step);
+int launch_corr_from_moments(tbpm_ctx* ctx, const double* table, const int* n_per_step, int n_steps,
+                             int n_terms, const double* mu, int S, int M, double shift, double tau,
+                             double* C);
+int launch_dos_jackson_fp64(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
+                            int64_t nE, double H0, double half, double* D);
+int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
+                              int64_t nE, double H0, double half, double* D);
+int launch_dos_fourier(tbpm_ctx* ctx, const double* C, int S, int n_steps, const double* energies,
+                       int64_t nE, double tau_phys, int window, double* D);
+
+// host-side FP64 Bessel (truncation orders, coefficient tables for the block forms)
+void bessel_j_host(double x, int n_max, double* out);
+int64_t truncation_order_host(double tau);
+
+}  // namespace tbpm

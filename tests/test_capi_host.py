@@ -1,0 +1,76 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every symbol the
+header declares, its structs match the header layout, and its host-only cost-model
+entry points agree with the oracle (Sec. II.A truncation, Tab. I counts, b_opt)."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from oracle import bessel, cost
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tbpm.h")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_17432_gb300 import capi as c
+    return c
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(tbpm_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("tbpm_create", "tbpm_lattice_create", "tbpm_moments", "tbpm_correlation", "tbpm_dos"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = capi.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (tbpm_[a-z_0-9]+)", out))
+    for name in declared_functions():
+        assert name in exported, name
+        assert hasattr(lib, name)
+    assert set(capi.exported_symbols()) <= set(declared_functions())
+
+
+def test_struct_layout_matches_header(capi):
+    # offsets follow the C declarations with natural alignment
+    assert ctypes.sizeof(capi.LatticeDesc) == 80
+    assert capi.LatticeDesc.t.offset == 48 and capi.LatticeDesc.seed.offset == 72
+    assert ctypes.sizeof(capi.Request) == 72
+    assert capi.Request.state_seed.offset == 16 and capi.Request.tau.offset == 48
+    assert ctypes.sizeof(capi.LatticeProps) == 64
+
+
+@pytest.mark.parametrize("tau", [0.5, math.pi, 4 * math.pi, 100.0, 1254 * math.pi, 2048 * math.pi])
+def test_truncation_order_matches_oracle(capi, tau):
+    assert capi.tbpm_truncation_order(tau) == bessel.truncation_order(tau)
+
+
+@pytest.mark.parametrize("nt,b", [(30, 1), (30, 5), (30, 7), (100, 40), (1024, 32)])
+def test_block_counts_match_table_one(capi, nt, b):
+    want = cost.block_counts(nt, b)
+    assert capi.tbpm_block_counts(nt, b, math.pi) == (want["amxsy"], want["axpy"], want["dot"])
+
+
+def test_block_opt_matches_oracle(capi):
+    for ta, tx in ((1.0, 0.2), (3.0, 2.0), (1.0, 1.0)):
+        assert capi.tbpm_block_opt(512, math.pi, ta, tx, 128) == cost.b_opt(512, ta, tx, b_max=128)
+
+
+def test_invalid_arguments_fail_cleanly(capi):
+    with pytest.raises(capi.TbpmError):
+        capi.tbpm_block_counts(0, 1, math.pi)
