@@ -212,6 +212,39 @@ int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
 int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
                     const double* d_energies, int64_t n_energies, double* d_D);
 
+/* ---------------------------------------------------------------- allocation-free step */
+
+/* One pass of the moment kernel with no device allocation at all.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library allocate
+ * device memory -- applications that reserve nearly all HBM in their own arena, loops
+ * where a cudaMalloc/cudaFree could synchronise the device, plugin hosts that only hand
+ * out buffers.  Every buffer is the caller's; the only scratch (per-block partial sums
+ * and a completion counter) lives in a fixed 1 MiB __device__ array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Matrix-free stencil lattices only (no vacancies).  Arguments:
+ *   kind, L[3], pbc[3]  lattice as in tbpm_lattice_desc (L[2] ignored unless cubic)
+ *   t_scaled            t / |H|
+ *   d_diag              device [N] rescaled on-site terms (V_i - H0)/|H| (float for C64,
+ *                       double for C128), or NULL to use diag_const for every site
+ *   precision, n_states C64 or C128; S a power of two <= 32
+ *   d_cur               device phi_n, [N][S] interleaved complex
+ *   d_prev_out          device phi_{n-1} on input (ignored when step == 0), phi_{n+1} on output
+ *   d_mu                device [S][n_moments][2]: step 0 writes m_0, m_1; step k >= 1 writes
+ *                       m_{2k} = 2<phi_k|phi_k> - m_0 and m_{2k+1} = 2<phi_{k+1}|phi_k> - m_1,
+ *                       reading m_0 and m_1 back from d_mu
+ *   step                k, 0 <= k < n_moments/2; stream = cudaStream_t or NULL
+ * Runs on the current device and returns without synchronising.  The first call on a device
+ * looks up the scratch array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one scratch array and every call resets
+ * its counter, so calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.  Sizes whose partial sums cannot fit the scratch are
+ * rejected with TBPM_EINVAL. */
+int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int32_t pbc[3], double t_scaled,
+                             double diag_const, const void* d_diag, int precision, int n_states,
+                             const void* d_cur, void* d_prev_out, double* d_mu, int64_t n_moments,
+                             int64_t step, void* stream);
+
 /* ---------------------------------------------------------------- cost model */
 
 /* Truncation order N(tau~) = 1 + max{n : |c_n(tau~)| > 1e-14} (Sec. II.A), FP64 host. */

@@ -87,6 +87,9 @@ def load():
         "tbpm_correlation_device": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
         "tbpm_dos": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
         "tbpm_dos_device": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
+        "tbpm_moment_step_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_double,
+                                                C.c_double, _P, C.c_int, C.c_int, _P, _P, _P, C.c_int64,
+                                                C.c_int64, _P]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -105,7 +108,7 @@ def exported_symbols():
             "tbpm_launch_count", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
-            "tbpm_dos_device", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt"]
+            "tbpm_dos_device", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt"]
 
 
 def _check(status: int):
@@ -254,6 +257,17 @@ def tbpm_dos(ctx, lat, req: Request, energies: np.ndarray, D: np.ndarray):
 
 def tbpm_dos_device(ctx, lat, req: Request, d_energies, n_energies: int, d_D):
     _check(load().tbpm_dos_device(ctx, lat, C.byref(req), _dev_ptr(d_energies), int(n_energies), _dev_ptr(d_D)))
+
+
+def tbpm_moment_step_noalloc(kind, L, pbc, t_scaled, diag_const, d_diag, precision, n_states, d_cur,
+                             d_prev_out, d_mu, n_moments, step, stream=0):
+    """One allocation-free moment pass; every buffer is the caller's (see include/tbpm.h)."""
+    L = tuple(int(v) for v in L) + (1,) * (3 - len(L))
+    pbc = tuple(int(bool(v)) for v in pbc) + (1,) * (3 - len(pbc))
+    _check(load().tbpm_moment_step_noalloc(int(kind), (C.c_int64 * 3)(*L), (C.c_int32 * 3)(*pbc), float(t_scaled),
+                                           float(diag_const), _dev_ptr(d_diag), int(precision), int(n_states),
+                                           _dev_ptr(d_cur), _dev_ptr(d_prev_out), _dev_ptr(d_mu), int(n_moments),
+                                           int(step), C.c_void_p(int(stream)) if stream else None))
 
 
 # ---------------------------------------------------------------- cost model

@@ -15,6 +15,7 @@
 // then FP64 warp and block trees, per-block partials, and a fixed-order sum by the last
 // block to finish.
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <mutex>
 #include <unordered_map>
@@ -552,3 +553,144 @@ int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void
 }
 
 }  // namespace tbpm
+
+// ====================================================================== allocation-free moment step
+// Some callers cannot let a library allocate device memory: applications that reserve nearly
+// all HBM up front in their own arena (a cudaMalloc from the library would fail or fragment
+// it), latency-critical loops where cudaMalloc/cudaFree may synchronise the device and stall
+// other streams, and plugin hosts that hand buffers to their plugins but forbid them to
+// allocate.  tbpm_moment_step_noalloc serves them: it runs one pass of the moment kernel on a
+// matrix-free stencil with every state buffer supplied by the caller, and keeps the kernel's
+// only scratch (per-block partial sums and the last-block counter) in the fixed array below.
+namespace tbpm {
+
+// Scratch of the allocation-free entry point: 256 bytes for the completion counter, then the
+// per-block FP64 partial sums.  Every GPU that loads the library holds this array until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = 1u << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that device current.
+static int noalloc_scratch_address(int device, unsigned char** out) {
+  static std::mutex mu;
+  static std::unordered_map<int, unsigned char*> addr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = addr.find(device);
+  if (it != addr.end()) {
+    *out = it->second;
+    return TBPM_OK;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    set_error("cudaGetSymbolAddress(g_noalloc_scratch) failed: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  addr[device] = (unsigned char*)p;
+  *out = (unsigned char*)p;
+  return TBPM_OK;
+}
+
+}  // namespace tbpm
+
+extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int32_t pbc[3], double t_scaled,
+                                        double diag_const, const void* d_diag, int precision, int n_states,
+                                        const void* d_cur, void* d_prev_out, double* d_mu, int64_t n_moments,
+                                        int64_t step, void* stream) {
+  using namespace tbpm;
+  clear_error();
+  if (!L || !pbc || !d_cur || !d_prev_out || !d_mu) {
+    set_error("tbpm_moment_step_noalloc: NULL argument");
+    return TBPM_EINVAL;
+  }
+  if (kind < TBPM_SQUARE || kind > TBPM_CUBIC || (precision != TBPM_C64 && precision != TBPM_C128)) {
+    set_error("tbpm_moment_step_noalloc: unknown lattice kind or precision");
+    return TBPM_EINVAL;
+  }
+  if (n_states < 1 || n_states > 32 || (n_states & (n_states - 1))) {
+    set_error("tbpm_moment_step_noalloc: n_states must be a power of two <= 32 (got %d)", n_states);
+    return TBPM_EINVAL;
+  }
+  if (n_moments < 2 || (n_moments & 1) || n_moments > INT32_MAX || step < 0 || step >= n_moments / 2) {
+    set_error("tbpm_moment_step_noalloc: need even n_moments >= 2 and 0 <= step < n_moments/2");
+    return TBPM_EINVAL;
+  }
+  Geom g{};
+  g.kind = kind;
+  g.Lx = L[0];
+  g.Ly = L[1];
+  g.Lz = kind == TBPM_CUBIC ? L[2] : 1;
+  if (g.Lx < 1 || g.Ly < 1 || g.Lz < 1) {
+    set_error("tbpm_moment_step_noalloc: lattice sizes must be >= 1");
+    return TBPM_EINVAL;
+  }
+  g.pbc_x = pbc[0] != 0;
+  g.pbc_y = pbc[1] != 0;
+  g.pbc_z = pbc[2] != 0;
+  g.z = kind == TBPM_SQUARE ? 4 : kind == TBPM_HONEYCOMB ? 3 : 6;
+  g.row_sites = kind == TBPM_HONEYCOMB ? 2 * g.Lx : g.Lx;
+  g.n_rows = g.Ly * g.Lz;
+  g.n_full = g.row_sites * g.n_rows;
+
+  int device = 0, n_sms = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    set_error("tbpm_moment_step_noalloc: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  unsigned char* scratch = nullptr;
+  TBPM_TRY(noalloc_scratch_address(device, &scratch));
+
+  RecurrenceArgs a;
+  memset(&a, 0, sizeof(a));
+  a.cur = d_cur;
+  a.prev_out = d_prev_out;
+  a.geom = g;
+  a.path = TBPM_PATH_STENCIL;
+  a.diag = d_diag;
+  a.diag_const = diag_const;
+  a.thop = t_scaled;
+  a.n_sites = g.n_full;
+  const int spt = (precision == TBPM_C64 && n_states >= 2) ? 2 : 1;
+  a.S = n_states;
+  a.P = n_states / spt;
+  a.logP = 0;
+  while ((1 << a.logP) < a.P) ++a.logP;
+  a.n_tiles = g.n_rows * ((g.row_sites * a.P + kThreads - 1) / kThreads);
+  a.mu = d_mu;
+  a.M = (int)n_moments;
+  a.step = (int)step;
+  const bool first = step == 0;
+  void* fn;
+  if (precision == TBPM_C128) fn = moment_kernel<double, 1>(kind, false, first);
+  else if (spt == 2) fn = moment_kernel<float, 2>(kind, false, first);
+  else fn = moment_kernel<float, 1>(kind, false, first);
+
+  // grid: the persistent grid, shrunk until its partial sums fit the fixed scratch
+  const size_t per_block = sizeof(double) * 3 * (size_t)n_states;
+  const int64_t fit = (int64_t)((kNoAllocScratchBytes - 256) / per_block);
+  int64_t grid = (int64_t)n_sms * resident_per_sm(fn);
+  if (grid > a.n_tiles) grid = a.n_tiles;
+  if (grid > fit) grid = fit;
+  if (grid < 1) {
+    set_error("tbpm_moment_step_noalloc: %d states need more than the %zu-byte scratch", n_states,
+              kNoAllocScratchBytes);
+    return TBPM_EINVAL;
+  }
+  a.nblocks = (int)grid;
+  a.counter = reinterpret_cast<unsigned*>(scratch);
+  a.partials = reinterpret_cast<double*>(scratch + 256);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the completion counter must start at zero; the partial sums are fully overwritten
+  e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) {
+    void* args[] = {&a};
+    e = cudaLaunchKernel(fn, dim3(a.nblocks), dim3(kThreads), args, 0, st);
+  }
+  if (e != cudaSuccess) {
+    set_error("tbpm_moment_step_noalloc: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  return TBPM_OK;
+}
