@@ -33,6 +33,8 @@ import workloads as wl  # noqa: E402
 
 WORKLOADS = {
     "graphene2048": wl.GRAPHENE_2048,
+    "graphene1024": wl.Workload("honeycomb1024x1024_S8_M256", wl.honeycomb(1024, 1024, t=-2.7), n_states=8,
+                                n_moments=256, precision=wl.C64, n_steps=70, n_energies=1024),
     "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
                                n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
 }
@@ -306,10 +308,10 @@ def run_gpu(args, work):
     bytes_per_launch = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = kernel_traffic(f"k_moment_step/{work.name}")
+    traffic = kernel_traffic(f"k_moment_stencil/{work.name}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "k_moment_step<honeycomb, complex64 x2 per thread>",
+                "kernel": "k_moment_stencil<honeycomb, complex64 x2 per thread>",
                 "algorithmic_bytes_per_launch": bytes_per_launch,
                 "avg_launch_us": per_launch_ms * 1e3,
                 "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}

@@ -82,6 +82,19 @@ __device__ __forceinline__ void st(Pack<R, SPT>* p, const Pack<R, SPT>& r) {
   }
 }
 
+template <typename R, int SPT>
+__device__ __forceinline__ void st_stream(Pack<R, SPT>* p, const Pack<R, SPT>& r) {
+  if constexpr (sizeof(Pack<R, SPT>) == 16) {
+    if constexpr (sizeof(R) == 4) {
+      __stcs(reinterpret_cast<float4*>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
+    } else {
+      __stcs(reinterpret_cast<double2*>(p), make_double2(r.v[0], r.v[1]));
+    }
+  } else {
+    __stcs(reinterpret_cast<float2*>(p), make_float2(r.v[0], r.v[1]));
+  }
+}
+
 // ------------------------------------------------------------------ accumulators
 // Neumaier-compensated FP32 sum (complex64 path) or plain FP64 sum (complex128 path).
 template <typename R>
@@ -327,6 +340,338 @@ __global__ void __launch_bounds__(kThreads) k_moment_step(RecurrenceArgs a) {
   });
 }
 
+// ------------------------------------------------------------------ stencil moment pass (fast path)
+// Matrix-free stencil version of the moment pass.  Work is walked in super-tiles of 2 x 256
+// thread units along one x-line, so each thread keeps two independent units in flight; the
+// line index advances incrementally (no division per unit) and neighbour offsets inside a
+// line are 32-bit.  The inner products are summed in FP32 over at most 32 units per thread
+// and then folded into FP64 (GB300 issues only 2 FP64 operations per clock per SM, so FP64
+// work per unit is kept to a fraction of an operation).
+template <typename R>
+struct Partial;
+template <>
+struct Partial<float> {
+  float f = 0.f;
+  double d = 0.0;
+  __device__ __forceinline__ void add(float x) { f += x; }
+  __device__ __forceinline__ void fold() { d += (double)f; f = 0.f; }
+  __device__ __forceinline__ double value() const { return d + (double)f; }
+};
+template <>
+struct Partial<double> {
+  double d = 0.0;
+  __device__ __forceinline__ void add(double x) { d += x; }
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ double value() const { return d; }
+};
+
+// Unit bases of the line and of its neighbouring lines (-1 when an open boundary drops them).
+struct LineBases {
+  int64_t own, up, dn, zup, zdn;
+};
+
+template <int KIND>
+__device__ __forceinline__ LineBases line_bases(const Geom& g, int64_t row, int64_t upr) {
+  LineBases b;
+  int64_t y = row, zc = 0;
+  if constexpr (KIND == TBPM_CUBIC) {
+    y = row % g.Ly;
+    zc = row / g.Ly;
+  }
+  b.own = row * upr;
+  int64_t r;
+  r = (y + 1 < g.Ly) ? row + 1 : (g.pbc_y ? row + 1 - g.Ly : -1);
+  b.up = r >= 0 ? r * upr : -1;
+  r = (y > 0) ? row - 1 : (g.pbc_y ? row - 1 + g.Ly : -1);
+  b.dn = r >= 0 ? r * upr : -1;
+  b.zup = b.zdn = -1;
+  if constexpr (KIND == TBPM_CUBIC) {
+    const int64_t plane = g.Ly, vol = g.Ly * g.Lz;
+    r = (zc + 1 < g.Lz) ? row + plane : (g.pbc_z ? row + plane - vol : -1);
+    b.zup = r >= 0 ? r * upr : -1;
+    r = (zc > 0) ? row - plane : (g.pbc_z ? row - plane + vol : -1);
+    b.zdn = r >= 0 ? r * upr : -1;
+  }
+  return b;
+}
+
+// Neighbour unit offsets of in-line unit u (absolute, -1 = none); returns the count.
+template <int KIND>
+__device__ __forceinline__ int stencil_neighbours(const Geom& g, const LineBases& b, int u, int P, int logP,
+                                                  int p, int upr, int64_t (&nb)[6]) {
+  const int64_t Lx = g.Lx;
+  if constexpr (KIND == TBPM_HONEYCOMB) {
+    const int sir = u >> logP, s = sir & 1, xc = sir >> 1;
+    nb[0] = b.own + (u ^ P);
+    if (s) {
+      nb[1] = (xc < Lx - 1) ? b.own + u + P : (g.pbc_x ? b.own + p : -1);
+      nb[2] = b.up >= 0 ? b.up + u - P : -1;
+    } else {
+      nb[1] = (xc > 0) ? b.own + u - P : (g.pbc_x ? b.own + u - P + upr : -1);
+      nb[2] = b.dn >= 0 ? b.dn + u + P : -1;
+    }
+    return 3;
+  } else {
+    const int xc = u >> logP;
+    nb[0] = (xc < Lx - 1) ? b.own + u + P : (g.pbc_x ? b.own + p : -1);
+    nb[1] = (xc > 0) ? b.own + u - P : (g.pbc_x ? b.own + u - P + upr : -1);
+    nb[2] = b.up >= 0 ? b.up + u : -1;
+    nb[3] = b.dn >= 0 ? b.dn + u : -1;
+    if constexpr (KIND == TBPM_CUBIC) {
+      nb[4] = b.zup >= 0 ? b.zup + u : -1;
+      nb[5] = b.zdn >= 0 ? b.zdn + u : -1;
+      return 6;
+    }
+    return 4;
+  }
+}
+
+template <int KIND, typename R, int SPT, bool FIRST>
+__global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a) {
+  using PK = Pack<R, SPT>;
+  constexpr int Z = KIND == TBPM_HONEYCOMB ? 3 : (KIND == TBPM_SQUARE ? 4 : 6);
+  constexpr int TU = 2 * kThreads;
+  const PK* __restrict__ cur = reinterpret_cast<const PK*>(a.cur);
+  PK* __restrict__ po = reinterpret_cast<PK*>(a.prev_out);
+  const R* __restrict__ diag = reinterpret_cast<const R*>(a.diag);
+  const Geom g = a.geom;
+  const int P = a.P, logP = a.logP, p = threadIdx.x & (P - 1);
+  const int upr = (int)(g.row_sites * P);
+  const int stpr = (upr + TU - 1) / TU;
+  const R th = FIRST ? (R)a.thop : (R)(2.0 * a.thop);
+  const R dc = FIRST ? (R)a.diag_const : (R)(2.0 * a.diag_const);
+  Partial<R> A[SPT], Br[SPT], Bi[SPT];
+
+  int64_t row = blockIdx.x / stpr;
+  int chunk = (int)(blockIdx.x - row * stpr);
+  const int64_t gq = gridDim.x / stpr;
+  const int gr = (int)(gridDim.x - gq * stpr);
+  int64_t cached = -1;
+  LineBases b{};
+  int fold = 0;
+  while (row < g.n_rows) {
+    if (row != cached) {
+      b = line_bases<KIND>(g, row, upr);
+      cached = row;
+    }
+    PK ph[2], h[2], pv[2];
+    bool valid[2];
+    int64_t own[2];
+    R d[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int u = chunk * TU + k * kThreads + threadIdx.x;
+      valid[k] = u < upr;
+#pragma unroll
+      for (int q = 0; q < 2 * SPT; ++q) h[k].v[q] = R(0);
+      if (valid[k]) {
+        own[k] = b.own + u;
+        ph[k] = ld(cur + own[k]);
+        int64_t nb[6];
+        stencil_neighbours<KIND>(g, b, u, P, logP, p, upr, nb);
+#pragma unroll
+        for (int q = 0; q < Z; ++q) {
+          if (nb[q] >= 0) {
+            const PK t = ld(cur + nb[q]);
+#pragma unroll
+            for (int w = 0; w < 2 * SPT; ++w) h[k].v[w] += t.v[w];
+          }
+        }
+        if (!FIRST) pv[k] = ld_stream(po + own[k]);
+        d[k] = dc;
+        if (diag) {
+          const R dd = __ldg(diag + (own[k] >> logP));
+          d[k] = FIRST ? dd : dd + dd;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!valid[k]) continue;
+      PK o;
+#pragma unroll
+      for (int w = 0; w < 2 * SPT; ++w) {
+        o.v[w] = d[k] * ph[k].v[w] + th * h[k].v[w];
+        if (!FIRST) o.v[w] -= pv[k].v[w];
+      }
+      st_stream(po + own[k], o);
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        const R pr = ph[k].v[2 * q], pi = ph[k].v[2 * q + 1], orr = o.v[2 * q], oi = o.v[2 * q + 1];
+        A[q].add(pr * pr + pi * pi);
+        Br[q].add(orr * pr + oi * pi);
+        Bi[q].add(orr * pi - oi * pr);
+      }
+    }
+    if (++fold == 16) {
+      fold = 0;
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        A[q].fold();
+        Br[q].fold();
+        Bi[q].fold();
+      }
+    }
+    chunk += gr;
+    row += gq;
+    if (chunk >= stpr) {
+      chunk -= stpr;
+      ++row;
+    }
+  }
+
+  double v[3 * SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    v[3 * k] = A[k].value();
+    v[3 * k + 1] = Br[k].value();
+    v[3 * k + 2] = Bi[k].value();
+  }
+  double* mu = a.mu;
+  const int M = a.M, n = a.step;
+  grid_reduce<3 * SPT, SPT, 3>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+    const int s = q / 3, c = q - 3 * s;
+    double* ms = mu + (size_t)s * M * 2;
+    if (FIRST) {
+      if (c == 0) { ms[0] = val; ms[1] = 0.0; }
+      else if (c == 1) ms[2] = val;
+      else ms[3] = val;
+    } else {
+      if (c == 0) { ms[4 * n] = 2.0 * val - ms[0]; ms[4 * n + 1] = -ms[1]; }
+      else if (c == 1) ms[4 * n + 2] = 2.0 * val - ms[2];
+      else ms[4 * n + 3] = 2.0 * val - ms[3];
+    }
+  });
+}
+
+// ------------------------------------------------------------------ stencil accumulation pass (fast path)
+// Same walk as k_moment_stencil (one unit per thread per tile); MODE as in k_accum_step.
+template <int KIND, typename R, int SPT, int MODE>
+__global__ void __launch_bounds__(kThreads, 4) k_accum_stencil(AccumArgs gargs) {
+  using PK = Pack<R, SPT>;
+  constexpr int Z = KIND == TBPM_HONEYCOMB ? 3 : (KIND == TBPM_SQUARE ? 4 : 6);
+  const RecurrenceArgs& a = gargs.r;
+  const PK* __restrict__ cur = reinterpret_cast<const PK*>(a.cur);
+  PK* __restrict__ po = reinterpret_cast<PK*>(a.prev_out);
+  PK* __restrict__ acc = reinterpret_cast<PK*>(gargs.acc);
+  const PK* __restrict__ psi = reinterpret_cast<const PK*>(gargs.psi);
+  const R* __restrict__ diag = reinterpret_cast<const R*>(a.diag);
+  const Geom g = a.geom;
+  const int P = a.P, logP = a.logP, p = threadIdx.x & (P - 1);
+  const int upr = (int)(g.row_sites * P);
+  const int tpr = (upr + kThreads - 1) / kThreads;
+  const R th = (MODE == ACC_FIRST) ? (R)a.thop : (R)(2.0 * a.thop);
+  const R dc = (MODE == ACC_FIRST) ? (R)a.diag_const : (R)(2.0 * a.diag_const);
+  const int64_t astr = gargs.acc_stride / SPT;
+  const int jlo = gargs.j_lo, jb = gargs.b, jdone = gargs.j_done;
+  const bool first_term = gargs.first_term != 0;
+  Partial<R> Cr[SPT], Ci[SPT];
+
+  int64_t row = blockIdx.x / tpr;
+  int chunk = (int)(blockIdx.x - row * tpr);
+  const int64_t gq = gridDim.x / tpr;
+  const int gr = (int)(gridDim.x - gq * tpr);
+  int64_t cached = -1;
+  LineBases b{};
+  int fold = 0;
+  while (row < g.n_rows) {
+    if (row != cached) {
+      b = line_bases<KIND>(g, row, upr);
+      cached = row;
+    }
+    const int u = chunk * kThreads + threadIdx.x;
+    if (u < upr) {
+      const int64_t own = b.own + u;
+      const PK ph = ld(cur + own);
+      if constexpr (MODE != ACC_NOSPMV) {
+        PK h;
+#pragma unroll
+        for (int w = 0; w < 2 * SPT; ++w) h.v[w] = R(0);
+        int64_t nb[6];
+        stencil_neighbours<KIND>(g, b, u, P, logP, p, upr, nb);
+#pragma unroll
+        for (int q = 0; q < Z; ++q) {
+          if (nb[q] >= 0) {
+            const PK t = ld(cur + nb[q]);
+#pragma unroll
+            for (int w = 0; w < 2 * SPT; ++w) h.v[w] += t.v[w];
+          }
+        }
+        R d = dc;
+        if (diag) {
+          const R dd = __ldg(diag + (own >> logP));
+          d = (MODE == ACC_FIRST) ? dd : dd + dd;
+        }
+        PK o;
+        if constexpr (MODE == ACC_FIRST) {
+#pragma unroll
+          for (int w = 0; w < 2 * SPT; ++w) o.v[w] = d * ph.v[w] + th * h.v[w];
+        } else {
+          const PK pv = ld_stream(po + own);
+#pragma unroll
+          for (int w = 0; w < 2 * SPT; ++w) o.v[w] = d * ph.v[w] + th * h.v[w] - pv.v[w];
+        }
+        st(po + own, o);
+      }
+      for (int j = jlo; j < jb; ++j) {
+        const R cr = (R)__ldg(gargs.coef + 2 * j), ci = (R)__ldg(gargs.coef + 2 * j + 1);
+        PK* aj = acc + (int64_t)j * astr + own;
+        PK av;
+        if (first_term) {
+#pragma unroll
+          for (int w = 0; w < 2 * SPT; ++w) av.v[w] = R(0);
+        } else {
+          av = ld_stream(aj);
+        }
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          const R pr = ph.v[2 * q], pi = ph.v[2 * q + 1];
+          av.v[2 * q] += cr * pr - ci * pi;
+          av.v[2 * q + 1] += cr * pi + ci * pr;
+        }
+        st_stream(aj, av);
+        if (j == jdone) {
+          const PK s0 = ld(psi + own);
+#pragma unroll
+          for (int q = 0; q < SPT; ++q) {
+            const R sr = s0.v[2 * q], si = s0.v[2 * q + 1];
+            Cr[q].add(sr * av.v[2 * q] + si * av.v[2 * q + 1]);
+            Ci[q].add(sr * av.v[2 * q + 1] - si * av.v[2 * q]);
+          }
+        }
+      }
+    }
+    if (++fold == 32) {
+      fold = 0;
+#pragma unroll
+      for (int q = 0; q < SPT; ++q) {
+        Cr[q].fold();
+        Ci[q].fold();
+      }
+    }
+    chunk += gr;
+    row += gq;
+    if (chunk >= tpr) {
+      chunk -= tpr;
+      ++row;
+    }
+  }
+
+  if (jdone < 0) return;
+  double v[2 * SPT];
+#pragma unroll
+  for (int k = 0; k < SPT; ++k) {
+    v[2 * k] = Cr[k].value();
+    v[2 * k + 1] = Ci[k].value();
+  }
+  double* C = gargs.C;
+  const int len = gargs.C_len, jg = gargs.j_global;
+  grid_reduce<2 * SPT, SPT, 2>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+    const int s = q >> 1, c = q & 1;
+    C[((size_t)s * len + jg) * 2 + c] = val;
+  });
+}
+
 // ------------------------------------------------------------------ accumulation pass
 // MODE: ACC_FIRST (phi_1 = H~ phi_0), ACC_REGULAR, ACC_NOSPMV (last term: accumulate only).
 template <int KIND, bool CSR, typename R, int SPT, int MODE>
@@ -443,24 +788,30 @@ static void* moment_kernel(int kind, bool csr, bool first) {
   if (csr) return first ? (void*)k_moment_step<0, true, R, SPT, true> : (void*)k_moment_step<0, true, R, SPT, false>;
   switch (kind) {
     case TBPM_SQUARE:
-      return first ? (void*)k_moment_step<TBPM_SQUARE, false, R, SPT, true>
-                   : (void*)k_moment_step<TBPM_SQUARE, false, R, SPT, false>;
+      return first ? (void*)k_moment_stencil<TBPM_SQUARE, R, SPT, true>
+                   : (void*)k_moment_stencil<TBPM_SQUARE, R, SPT, false>;
     case TBPM_HONEYCOMB:
-      return first ? (void*)k_moment_step<TBPM_HONEYCOMB, false, R, SPT, true>
-                   : (void*)k_moment_step<TBPM_HONEYCOMB, false, R, SPT, false>;
+      return first ? (void*)k_moment_stencil<TBPM_HONEYCOMB, R, SPT, true>
+                   : (void*)k_moment_stencil<TBPM_HONEYCOMB, R, SPT, false>;
     default:
-      return first ? (void*)k_moment_step<TBPM_CUBIC, false, R, SPT, true>
-                   : (void*)k_moment_step<TBPM_CUBIC, false, R, SPT, false>;
+      return first ? (void*)k_moment_stencil<TBPM_CUBIC, R, SPT, true>
+                   : (void*)k_moment_stencil<TBPM_CUBIC, R, SPT, false>;
   }
+}
+
+// super-tiles of the stencil moment pass (2 x 256 units along one line)
+static int64_t stencil_supertiles(const Geom& g, int P) {
+  const int64_t upr = g.row_sites * P;
+  return g.n_rows * ((upr + 2 * kThreads - 1) / (2 * kThreads));
 }
 
 template <typename R, int SPT, int MODE>
 static void* accum_kernel_m(int kind, bool csr) {
   if (csr) return (void*)k_accum_step<0, true, R, SPT, MODE>;
   switch (kind) {
-    case TBPM_SQUARE: return (void*)k_accum_step<TBPM_SQUARE, false, R, SPT, MODE>;
-    case TBPM_HONEYCOMB: return (void*)k_accum_step<TBPM_HONEYCOMB, false, R, SPT, MODE>;
-    default: return (void*)k_accum_step<TBPM_CUBIC, false, R, SPT, MODE>;
+    case TBPM_SQUARE: return (void*)k_accum_stencil<TBPM_SQUARE, R, SPT, MODE>;
+    case TBPM_HONEYCOMB: return (void*)k_accum_stencil<TBPM_HONEYCOMB, R, SPT, MODE>;
+    default: return (void*)k_accum_stencil<TBPM_CUBIC, R, SPT, MODE>;
   }
 }
 
@@ -521,7 +872,7 @@ int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bo
   else if (spt == 2) fn = moment_kernel<float, 2>(a.geom.kind, csr, first);
   else fn = moment_kernel<float, 1>(a.geom.kind, csr, first);
   RecurrenceArgs aa = a;
-  aa.nblocks = persistent_grid(ctx, fn, a.n_tiles);
+  aa.nblocks = persistent_grid(ctx, fn, csr ? a.n_tiles : stencil_supertiles(a.geom, a.P));
   void* args[] = {&aa};
   return launch(ctx, fn, aa.nblocks, args);
 }
@@ -534,7 +885,7 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode
   else if (spt == 2) fn = accum_kernel<float, 2>(g.r.geom.kind, csr, mode);
   else fn = accum_kernel<float, 1>(g.r.geom.kind, csr, mode);
   AccumArgs gg = g;
-  gg.r.nblocks = persistent_grid(ctx, fn, g.r.n_tiles);
+  gg.r.nblocks = persistent_grid(ctx, fn, g.r.n_tiles);  // stencil: tiles of 256 units along a line
   void* args[] = {&gg};
   return launch(ctx, fn, gg.r.nblocks, args);
 }
@@ -671,7 +1022,8 @@ extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int3
   const size_t per_block = sizeof(double) * 3 * (size_t)n_states;
   const int64_t fit = (int64_t)((kNoAllocScratchBytes - 256) / per_block);
   int64_t grid = (int64_t)n_sms * resident_per_sm(fn);
-  if (grid > a.n_tiles) grid = a.n_tiles;
+  const int64_t supertiles = stencil_supertiles(g, a.P);
+  if (grid > supertiles) grid = supertiles;
   if (grid > fit) grid = fit;
   if (grid < 1) {
     set_error("tbpm_moment_step_noalloc: %d states need more than the %zu-byte scratch", n_states,

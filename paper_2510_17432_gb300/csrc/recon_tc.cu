@@ -1,11 +1,477 @@
-// Tensor-core reconstruction of the Jackson DOS (placeholder until the tcgen05 path lands).
+// Tensor-core (tcgen05) reconstruction of the Jackson-damped Chebyshev DOS on an energy grid.
+//
+// The moment -> energy sum  D_s(E_k) = w_k sum_n K[k][n] Re m_n^s,
+//     K[k][n] = g_n (2 - delta_n0) T_n(E~_k),   w_k = 1/(pi |H| sqrt(1 - E~_k^2))
+// (kernel polynomial method with Jackson factors g_n, Weisse et al., Rev. Mod. Phys. 78, 275
+// (2006), Eqs. 71 and 81) is a dense contraction [n_E x M] x [M x S].  It runs on the 5th-gen
+// tensor cores in bf16 with an error-free three-way split of both operands,
+//     x = x1 + x2 + x3,  x1 = bf16(x), x2 = bf16(x - x1), x3 = bf16(x - x1 - x2),
+// keeping the six products K_i m_j with i + j <= 4 (1-based): this reproduces FP32-level
+// products, the FP32 tensor-core accumulator is restarted every 1024 reduction elements and
+// each chunk is folded into FP64 registers by the epilogue.  The six products are arranged
+// as one GEMM:  A' = [K1 | K2 | K3]  (n_E x 3M),  B' columns (c, s) hold m_{c+1} in the
+// reduction blocks i with i + c + 1 <= 4, so the column blocks c sum to the result.
+//
+// Kernel structure (one CTA = 128 energies x NP columns, split over the reduction):
+//   warp 0: TMA producer (cp.async.bulk.tensor, 128B swizzle) into an NSTAGE smem ring;
+//   warp 1: TMEM allocation and the single-thread tcgen05.mma issuer (kind::f16, bf16 in,
+//           FP32 accumulate, M=128, N=NP, K=16), tcgen05.commit to the ring and chunk barriers;
+//   warps 2-5: epilogue, tcgen05.ld of each accumulator chunk into FP64 sums.
+// Every mbarrier wait is bounded by a wall-clock budget; on expiry the kernel records an error
+// code, skips the rest of the work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <mutex>
+
 #include "tbpm_internal.cuh"
 
 namespace tbpm {
-int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
-                              int64_t nE, double H0, double half, double* D) {
-  (void)ctx; (void)mu; (void)S; (void)M; (void)energies; (void)nE; (void)H0; (void)half; (void)D;
-  set_error("tensor-core reconstruction not available in this build");
-  return TBPM_EUNSUPPORTED;
+namespace tc {
+
+constexpr int BM = 128;      // energies per CTA tile (TMEM lanes)
+constexpr int BK = 64;       // reduction elements per stage: 128 bytes of bf16
+constexpr int NSTAGE = 4;
+constexpr int CHUNK = 16;    // k-tiles per FP32 accumulation chunk (1024 elements)
+constexpr int kThreadsTC = 192;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false (and an error code) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (globaltimer() - t0 > kWaitNs) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile in the 128-byte swizzle layout
+// (rows of 128 B, 8-row groups 1024 B apart), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;            // leading-dimension byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride-dimension byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, bf16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+
+template <int NP>
+struct Smem {
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = NP * BK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int TOTAL = NSTAGE * STAGE + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+// One CTA: rows [m0, m0+128) of A', reduction tiles [kt0, kt0 + KT) ; writes FP64 partial sums
+// partials[(split * rows_pad + row) * NP + col].
+template <int NP>
+__global__ void __launch_bounds__(kThreadsTC, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int kt_per_split,
+              int kt_total, int rows_pad, double* partials, int* err) {
+  static_assert(NP % 16 == 0 && NP >= 16 && NP <= 64, "N of the MMA");
+  constexpr int TCOLS = (2 * NP <= 32) ? 32 : (2 * NP <= 64) ? 64 : 128;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + NSTAGE * Smem<NP>::STAGE);
+  // bars: full[NSTAGE], empty[NSTAGE], accf[2], acce[2]; then the TMEM base address
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * NSTAGE + 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int split = blockIdx.y;
+  const int kt0 = split * kt_per_split;
+  const int KT = min(kt_per_split, kt_total - kt0);
+  const int NC = (KT + CHUNK - 1) / CHUNK;
+
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + NSTAGE + s); };
+  auto accf = [&](int b) { return smem_u32(bars + 2 * NSTAGE + b); };
+  auto acce = [&](int b) { return smem_u32(bars + 2 * NSTAGE + 2 + b); };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf(b), 1);
+      mbar_init(acce(b), 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0 && KT > 0) {
+      for (int kt = 0; kt < KT; ++kt) {
+        const int s = kt % NSTAGE;
+        const uint32_t use = (uint32_t)(kt / NSTAGE);
+        if (kt >= NSTAGE && !mbar_wait(empty(s), (use & 1) ^ 1, err, 1)) break;
+        unsigned char* st = smem + s * Smem<NP>::STAGE;
+        mbar_arrive_tx(full(s), Smem<NP>::STAGE);
+        tma_load_2d(smem_u32(st), &mapA, full(s), (kt0 + kt) * BK, m0);
+        tma_load_2d(smem_u32(st + Smem<NP>::A_BYTES), &mapB, full(s), (kt0 + kt) * BK, 0);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && KT > 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, NP);
+      bool ok = true;
+      for (int kt = 0; kt < KT && ok; ++kt) {
+        const int s = kt % NSTAGE;
+        const uint32_t use = (uint32_t)(kt / NSTAGE);
+        const int c = kt / CHUNK, buf = c & 1;
+        const bool first = (kt % CHUNK) == 0;
+        const bool last = ((kt % CHUNK) == CHUNK - 1) || (kt == KT - 1);
+        if (first && c >= 2) ok = mbar_wait(acce(buf), (uint32_t)((c / 2 - 1) & 1), err, 2);
+        if (ok) ok = mbar_wait(full(s), use & 1, err, 3);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a_base = smem_u32(smem + s * Smem<NP>::STAGE);
+        const uint32_t b_base = a_base + Smem<NP>::A_BYTES;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          umma_bf16(tmem + (uint32_t)(buf * NP), sw128_desc(a_base + k * 32), sw128_desc(b_base + k * 32), idesc,
+                    (first && k == 0) ? 0u : 1u);
+        }
+        umma_commit(empty(s));
+        if (last) umma_commit(accf(buf));
+      }
+    }
+  } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    double acc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc[j] = 0.0;
+    bool ok = true;
+    for (int c = 0; c < NC && ok; ++c) {
+      const int buf = c & 1;
+      ok = mbar_wait(accf(buf), (uint32_t)((c / 2) & 1), err, 4);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int g = 0; g < NP / 16; ++g) {
+        float r[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NP + g * 16), r);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) acc[g * 16 + i] += (double)r[i];
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acce(buf));
+    }
+    double* out = partials + ((size_t)split * rows_pad + m0 + row) * NP;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) out[j] = acc[j];
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ operand preparation
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  a = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(a);
+  b = __double2bfloat16(r1);
+  const double r2 = r1 - (double)__bfloat162float(b);
+  c = __double2bfloat16(r2);
+}
+
+// A'[k][i*Mp + n] = i-th bf16 piece of g_n (2 - delta_n0) T_n(E~_k); zero for n >= M, k >= nE or
+// |E~_k| >= 1.  One thread per (row, 16 consecutive orders); T_n from the three-term recurrence
+// anchored by cos(n theta) at the start of each group.
+__global__ void k_build_A(const double* energies, int64_t nE, double H0, double half, int M, int Mp,
+                          const double* g, int rows_pad, __nv_bfloat16* A) {
+  const int groups = Mp / 16;
+  const int64_t total = (int64_t)rows_pad * groups;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / groups;
+    const int n0 = (int)(e - k * groups) * 16;
+    double x = 2.0;
+    if (k < nE) x = (energies[k] - H0) / half;
+    const bool inside = fabs(x) < 1.0;
+    const double th = inside ? acos(x) : 0.0;
+    double tm = inside ? cos(n0 * th) : 0.0, tc = inside ? cos((n0 + 1) * th) : 0.0;
+    __nv_bfloat16* row = A + (size_t)k * 3 * Mp;
+    for (int i = 0; i < 16; ++i) {
+      const int n = n0 + i;
+      double Tn;
+      if (i == 0) {
+        Tn = tm;
+      } else if (i == 1) {
+        Tn = tc;
+      } else {
+        const double t2 = 2.0 * x * tc - tm;
+        tm = tc;
+        tc = t2;
+        Tn = t2;
+      }
+      const double w = (inside && n < M) ? g[n] * Tn * (n == 0 ? 1.0 : 2.0) : 0.0;
+      __nv_bfloat16 a, b, c;
+      split3(w, a, b, c);
+      row[n] = a;
+      row[Mp + n] = b;
+      row[2 * Mp + n] = c;
+    }
+  }
+}
+
+// B'[col][i*Mp + n], col = c*S + s: c-th piece of Re m_n^s when i + c <= 2 (0-based), else 0.
+__global__ void k_build_B(const double* mu, int S, int M, int Mp, int NP, __nv_bfloat16* B) {
+  const int64_t total = (int64_t)NP * 3 * Mp;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(e / (3 * Mp));
+    const int r = (int)(e - (int64_t)col * 3 * Mp);
+    const int i = r / Mp, n = r - i * Mp;
+    const int c = col / S, s = col - c * S;
+    float v = 0.f;
+    if (col < 3 * S && n < M && i + c <= 2) {
+      __nv_bfloat16 p[3];
+      split3(mu[((size_t)s * M + n) * 2], p[0], p[1], p[2]);
+      v = __bfloat162float(p[c]);
+    }
+    B[e] = __float2bfloat16(v);
+  }
+}
+
+// D[s][k] = w_k * sum_split sum_c partials[split][k][c*S + s]
+__global__ void k_finalize(const double* partials, int splits, int rows_pad, int NP, int S, const double* energies,
+                           int64_t nE, double H0, double half, double* D) {
+  const int64_t total = nE * S;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / nE);
+    const int64_t k = e - (int64_t)s * nE;
+    const double x = (energies[k] - H0) / half;
+    double sum = 0.0;
+    for (int sp = 0; sp < splits; ++sp)
+      for (int c = 0; c < 3; ++c) sum += partials[((size_t)sp * rows_pad + k) * NP + c * S + s];
+    D[(size_t)s * nE + k] = fabs(x) < 1.0 ? sum / (M_PI * half * sqrt(1.0 - x * x)) : 0.0;
+  }
+}
+
+__global__ void k_jackson_g(int M, double* g) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= M) return;
+  const double q = M_PI / (M + 1.0);
+  double sn, cs;
+  sincos(q * n, &sn, &cs);
+  g[n] = ((M - n + 1.0) * cs + sn * (cos(q) / sin(q))) / (M + 1.0);
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encode_fn() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  });
+  return fn;
+}
+
+static int make_map(CUtensorMap* map, void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                    uint32_t box_outer) {
+  EncodeTiled enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return TBPM_ECUDA;
+  }
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return TBPM_ECUDA;
+  }
+  return TBPM_OK;
+}
+
+template <int NP>
+static int run_gemm(tbpm_ctx* ctx, const CUtensorMap& mA, const CUtensorMap& mB, int m_tiles, int splits,
+                    int kt_per_split, int kt_total, int rows_pad, double* partials, int* err) {
+  const int smem = Smem<NP>::TOTAL;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [&] {
+    attr_err = cudaFuncSetAttribute(k_gemm_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  TBPM_CK(attr_err);
+  k_gemm_tc<NP><<<dim3(m_tiles, splits), kThreadsTC, smem, ctx->stream>>>(mA, mB, kt_per_split, kt_total, rows_pad,
+                                                                         partials, err);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
+}  // namespace tc
+
+int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies, int64_t nE,
+                              double H0, double half, double* D) {
+  using namespace tc;
+  if (S > 16) {
+    // two passes over state groups keep the epilogue's FP64 sums in registers
+    const int S1 = 16;
+    TBPM_TRY(launch_dos_jackson_tensor(ctx, mu, S1, M, energies, nE, H0, half, D));
+    return launch_dos_jackson_tensor(ctx, mu + (size_t)S1 * M * 2, S - S1, M, energies, nE, H0, half,
+                                     D + (size_t)S1 * nE);
+  }
+  if (nE > (1 << 24) || M < 1) {
+    set_error("tensor reconstruction: n_energies or n_moments out of range");
+    return TBPM_EINVAL;
+  }
+  const int NP = (3 * S <= 16) ? 16 : (3 * S <= 32) ? 32 : 48;
+  const int Mp = (M + BK - 1) / BK * BK;
+  const int rows_pad = (int)((nE + BM - 1) / BM * BM);
+  const int m_tiles = rows_pad / BM;
+  const int kt_total = 3 * Mp / BK;
+  int splits = (2 * ctx->num_sms + m_tiles - 1) / m_tiles;
+  splits = std::max(1, std::min(splits, kt_total / CHUNK));
+  const int kt_per_split = (kt_total + splits - 1) / splits;
+  splits = (kt_total + kt_per_split - 1) / kt_per_split;
+
+  const size_t a_bytes = (size_t)rows_pad * 3 * Mp * 2;
+  const size_t b_bytes = (size_t)NP * 3 * Mp * 2;
+  const size_t p_bytes = (size_t)splits * rows_pad * NP * sizeof(double);
+  const size_t g_bytes = (size_t)M * sizeof(double);
+  TBPM_TRY(ensure(ctx, ctx->ws_recon, a_bytes + b_bytes + p_bytes + g_bytes + 4096));
+  unsigned char* base = (unsigned char*)ctx->ws_recon.p;
+  __nv_bfloat16* A = (__nv_bfloat16*)base;
+  __nv_bfloat16* B = (__nv_bfloat16*)(base + a_bytes);
+  double* partials = (double*)(base + ((a_bytes + b_bytes + 255) & ~(size_t)255));
+  double* g = (double*)((unsigned char*)partials + p_bytes);
+  int* err = (int*)((unsigned char*)g + g_bytes + 64);
+
+  TBPM_CK(cudaMemsetAsync(err, 0, sizeof(int), ctx->stream));
+  k_jackson_g<<<(M + 255) / 256, 256, 0, ctx->stream>>>(M, g);
+  TBPM_CK_LAUNCH(ctx);
+  const int64_t ga = (int64_t)rows_pad * (Mp / 16);
+  k_build_A<<<(int)std::min<int64_t>((ga + 255) / 256, (int64_t)ctx->num_sms * 32), 256, 0, ctx->stream>>>(
+      energies, nE, H0, half, M, Mp, g, rows_pad, A);
+  TBPM_CK_LAUNCH(ctx);
+  const int64_t gb = (int64_t)NP * 3 * Mp;
+  k_build_B<<<(int)std::min<int64_t>((gb + 255) / 256, (int64_t)ctx->num_sms * 32), 256, 0, ctx->stream>>>(
+      mu, S, M, Mp, NP, B);
+  TBPM_CK_LAUNCH(ctx);
+
+  CUtensorMap mA, mB;
+  TBPM_TRY(make_map(&mA, A, (uint64_t)3 * Mp, (uint64_t)rows_pad, BK, BM));
+  TBPM_TRY(make_map(&mB, B, (uint64_t)3 * Mp, (uint64_t)NP, BK, NP));
+  int r;
+  if (NP == 16) r = run_gemm<16>(ctx, mA, mB, m_tiles, splits, kt_per_split, kt_total, rows_pad, partials, err);
+  else if (NP == 32) r = run_gemm<32>(ctx, mA, mB, m_tiles, splits, kt_per_split, kt_total, rows_pad, partials, err);
+  else r = run_gemm<48>(ctx, mA, mB, m_tiles, splits, kt_per_split, kt_total, rows_pad, partials, err);
+  TBPM_TRY(r);
+  const int64_t gf = nE * S;
+  k_finalize<<<(int)std::min<int64_t>((gf + 255) / 256, (int64_t)ctx->num_sms * 16), 256, 0, ctx->stream>>>(
+      partials, splits, rows_pad, NP, S, energies, nE, H0, half, D);
+  TBPM_CK_LAUNCH(ctx);
+  // a timed-out wait inside the GEMM is reported, never hidden
+  int h_err = 0;
+  TBPM_CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  if (h_err) {
+    set_error("tensor-core reconstruction: bounded wait expired (code %d)", h_err);
+    return TBPM_ETIMEOUT;
+  }
+  return TBPM_OK;
+}
+
 }  // namespace tbpm

@@ -1,0 +1,60 @@
+"""Tensor-core (tcgen05, bf16 x3 split, FP32 MMA, FP64 chunk sums) Jackson-DOS reconstruction
+against the FP64 CUDA-core reconstruction of the same moments and against the oracle.
+
+Bar: max_E |D_tensor - D_ref| / max_E D_ref <= 1e-5 (the complex64 tolerance of the path).
+"""
+import numpy as np
+import pytest
+
+from oracle import lattice as olat, propagate as oprop, spectra as ospec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_17432_gb300 import capi as c
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(capi):
+    h = capi.tbpm_create(0)
+    yield h
+    capi.tbpm_destroy(h)
+
+
+def dos(capi, ctx, lat, S, M, E, recon, prec=0):
+    req = capi.request(n_states=S, precision=prec, n_moments=M, dos_method=capi.DOS_JACKSON, recon=recon,
+                       state_seed=9)
+    D = np.zeros((S, E.size))
+    capi.tbpm_dos(ctx, lat, req, E, D)
+    return D
+
+
+@pytest.mark.parametrize("S,M,nE", [(1, 64, 128), (3, 256, 300), (8, 1000, 1000), (16, 512, 257), (20, 192, 129)])
+def test_tensor_matches_fp64_reconstruction(capi, ctx, S, M, nE):
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(1, (64, 48), t=-2.7, W=1.0, seed=5))
+    info = capi.tbpm_lattice_info(lat)
+    E = np.linspace(info.H0 - 1.01 * info.half_width, info.H0 + 1.01 * info.half_width, nE)
+    Dt = dos(capi, ctx, lat, S, M, E, capi.RECON_TENSOR)
+    Df = dos(capi, ctx, lat, S, M, E, capi.RECON_FP64)
+    for s in range(S):
+        assert np.max(np.abs(Dt[s] - Df[s])) / np.max(np.abs(Df[s])) <= 1e-5, s
+    capi.tbpm_lattice_destroy(lat)
+
+
+def test_tensor_reconstruction_matches_oracle(capi, ctx):
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(0, (40, 40), t=1.0, W=1.0, seed=0x7B1A5))
+    ol = olat.build_lattice(0, (40, 40, 1), t=1.0, W=1.0, seed=0x7B1A5)
+    S, M, nE = 2, 512, 400
+    E = np.linspace(ol.H0 - ol.half_width, ol.H0 + ol.half_width, nE)
+    Dt = dos(capi, ctx, lat, S, M, E, capi.RECON_TENSOR)
+    psi = oprop.random_phase_states(ol, 9, S)
+    for s in range(S):
+        mu = oprop.moments(ol, psi[s], psi[s], M)
+        ref = ospec.dos_jackson(mu, E, ol.H0, ol.half_width)
+        assert np.max(np.abs(Dt[s] - ref)) / np.max(ref) <= 1e-5
+    capi.tbpm_lattice_destroy(lat)
