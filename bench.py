@@ -35,10 +35,13 @@ WORKLOADS = {
     "graphene2048": wl.GRAPHENE_2048,
     "graphene1024": wl.Workload("honeycomb1024x1024_S8_M256", wl.honeycomb(1024, 1024, t=-2.7), n_states=8,
                                 n_moments=256, precision=wl.C64, n_steps=70, n_energies=1024),
+    "recon_probe": wl.Workload("honeycomb256x256_S8_M4096_E8192", wl.honeycomb(256, 256, t=-2.7), n_states=8,
+                               n_moments=4096, precision=wl.C64, n_steps=0, n_energies=8192),
     "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
                                n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
 }
-CHEB_SRC = os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", "cheb.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", f)
+               for f in ("cheb.cu", "fused.cu", "stencil.cuh", "tbpm_internal.cuh")]
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -51,10 +54,14 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="tbpm", choices=["tbpm", "reference"])
     p.add_argument("--workload", default="graphene2048", choices=sorted(WORKLOADS))
-    p.add_argument("--recon", default="fp64", choices=["fp64", "tensor"])
+    p.add_argument("--recon", default="tensor", choices=["fp64", "tensor"])
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
+    p.add_argument("--requests", type=int, default=512)
+    p.add_argument("--log2-max-sites", type=int, default=20)
+    p.add_argument("--load", type=float, default=0.8, help="arrival rate as a fraction of measured capacity")
     return p.parse_args()
 
 
@@ -168,12 +175,20 @@ def measured_hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def kernel_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     try:
         with open(TRAFFIC) as f:
             rec = json.load(f)
-        sha = hashlib.sha256(open(CHEB_SRC, "rb").read()).hexdigest()
+        sha = kernel_source_hash()
         ent = rec.get(kernel_key)
         if ent and ent.get("source_sha256") == sha:
             return float(ent["dram_bytes_per_launch"])
@@ -303,19 +318,41 @@ def run_gpu(args, work):
     e2e = {"value": world * site_updates / e2e_s, "unit": "site-updates/s",
            "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
 
-    # ---- roofline of the dominant kernel (the recurrence pass), from the live events
-    per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
-    bytes_per_launch = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
+    # ---- roofline of the dominant kernel, from the live events.  Algorithmic bytes: 24 B per
+    # site-update (read phi_n, read phi_{n-1}, write phi_{n+1}, complex64) + 4 B per site with disorder.
+    per_site_step = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
+    total_alg = per_site_step * (M // 2) * args.steps
+    if prof["fused_launches"] > 0:
+        steps_per_launch = 4
+        kname = "k_fused_honeycomb (4 Chebyshev steps per pass, complex64 state pairs)"
+        per_launch_ms = prof["fused_ms"] / prof["fused_launches"]
+        traffic_key = f"k_fused_honeycomb/{work.name}"
+    else:
+        steps_per_launch = 1
+        kname = "k_moment_stencil<honeycomb, complex64 x2 per thread>"
+        per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
+        traffic_key = f"k_moment_stencil/{work.name}"
+    bytes_per_launch = per_site_step * steps_per_launch
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_hbm_peak()
-    traffic = kernel_traffic(f"k_moment_stencil/{work.name}")
+    traffic = kernel_traffic(traffic_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_kind,
-                "kernel": "k_moment_stencil<honeycomb, complex64 x2 per thread>",
-                "algorithmic_bytes_per_launch": bytes_per_launch,
-                "avg_launch_us": per_launch_ms * 1e3,
+                "traffic": traffic, "peak_source": peak_kind, "kernel": kname,
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
+                "recurrence_algorithmic_gbs": total_alg / (prof["recurrence_ms"] / 1e3) / 1e9,
                 "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+    if traffic:
+        roofline["dram_gbs"] = traffic / (per_launch_ms / 1e3) / 1e9
+        roofline["dram_frac"] = roofline["dram_gbs"] / peak
 
+    recon_ms = prof["recon_ms"] / args.steps
+    Mp = (M + 63) // 64 * 64
+    rows_pad = (nE + 127) // 128 * 128
+    NP = 16 if 3 * S <= 16 else (32 if 3 * S <= 32 else 48)
+    mma_flops = 2.0 * rows_pad * 3 * Mp * NP * (1 if S <= 16 else 2)
+    recon = {"ms_per_step": recon_ms, "launches_per_step": prof["recon_launches"] / args.steps,
+             "path": args.recon,
+             "mma_tflops": (mma_flops / (recon_ms / 1e3) / 1e12) if args.recon == "tensor" and recon_ms > 0 else None}
     out = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -327,6 +364,7 @@ def run_gpu(args, work):
                    "reconstruction": args.recon, "l2": "inputs larger than L2 (2 state blocks of "
                    f"{info.n_sites * S * 8 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
         "roofline": roofline,
+        "reconstruction": recon,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
@@ -380,9 +418,88 @@ def run_gpu(args, work):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving stream
+def request_work(r):
+    n = r.lattice.n_full
+    return (r.n_moments // 2) * n * r.n_states
+
+
+def run_serving(args):
+    import threading
+    from paper_2510_17432_gb300 import capi
+
+    rank, world, local = dist_env()
+    ctx = capi.tbpm_create(local)
+    E = wl.uniform_energy_grid(1024, -8.2, 8.2)
+    recon = capi.RECON_TENSOR if args.recon == "tensor" else capi.RECON_FP64
+
+    def submit(srv, r):
+        sp = r.lattice
+        desc = capi.lattice_desc(sp.kind, sp.L, t=sp.t, W=sp.W, seed=sp.seed)
+        if r.quantity == "ldos":
+            req = capi.request(sites=r.sites, precision=capi.C64, n_moments=r.n_moments)
+        else:
+            req = capi.request(n_states=r.n_states, precision=capi.C64, n_moments=r.n_moments, state_seed=sp.seed)
+        return capi.tbpm_submit(srv, desc, req, E)
+
+    # capacity probe: a closed-loop burst of requests from the same distribution
+    probe = wl.serving_stream(24, 1.0, seed=wl.REQUEST_SEED + 1, log2_max=args.log2_max_sites)
+    srv = capi.tbpm_server_create(ctx, recon=recon)
+    t0 = time.perf_counter()
+    ts = [submit(srv, r) for r in probe]
+    for t, r in zip(ts, probe):
+        capi.tbpm_wait(srv, t, np.zeros((r.n_states, E.size)))
+    cap_su = sum(request_work(r) for r in probe) / (time.perf_counter() - t0)
+    capi.tbpm_server_destroy(srv)
+
+    base = wl.serving_stream(args.requests, 1.0, log2_max=args.log2_max_sites)
+    mean_work = sum(request_work(r) for r in base) / len(base)
+    rate = args.load * cap_su / mean_work
+    stream = wl.serving_stream(args.requests, rate, log2_max=args.log2_max_sites)
+    srv = capi.tbpm_server_create(ctx, recon=recon)
+    tickets = [None] * len(stream)
+    start = time.perf_counter()
+
+    def submitter():
+        for i, r in enumerate(stream):
+            delay = start + r.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = submit(srv, r)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    for i, r in enumerate(stream):
+        while tickets[i] is None:
+            time.sleep(0.0005)
+        q, run, tot = capi.tbpm_wait(srv, tickets[i], np.zeros((r.n_states, E.size)))
+        lat.append(tot / 1e3)
+    th.join()
+    makespan = time.perf_counter() - start
+    stats = capi.tbpm_server_stats(srv)
+    capi.tbpm_server_destroy(srv)
+    capi.tbpm_destroy(ctx)
+    lat = np.array(lat)
+    total_su = sum(request_work(r) for r in stream)
+    print(json.dumps({
+        "metric": "serving latency (submit to DOS on host) and throughput", "requests": len(stream),
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "throughput_site_updates_per_s": total_su / makespan, "makespan_s": makespan,
+        "arrival_rate_per_s": rate, "load": args.load, "capacity_site_updates_per_s": cap_su,
+        "kernel_launches": stats["launches"], "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving stream: {len(stream)} Poisson arrivals, square/honeycomb/cubic, "
+                               f"2^12..2^{args.log2_max_sites} sites, W~U[0,2]t, M~U{{256..8192}}, "
+                               "S~U{1..16} or LDOS at 32 sites", "reconstruction": args.recon}}))
+
+
 def main():
     args = parse()
     work = WORKLOADS[args.workload]
+    if args.serving:
+        run_serving(args)
+        return
     if args.impl == "reference":
         run_reference(args, work)
     else:

@@ -144,14 +144,20 @@ void* tbpm_stream(tbpm_ctx* ctx);
 int tbpm_sync(tbpm_ctx* ctx);
 /* Number of kernels the library has launched on this context since creation. */
 int64_t tbpm_launch_count(const tbpm_ctx* ctx);
+/* Temporal fusion of the moment pass (several Chebyshev steps per pass in shared memory, so
+ * each state vector crosses HBM twice per pass instead of three times per step), used where a
+ * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least one tile wide).
+ * On by default; 0 forces one step per pass.  Results agree within the complex64 tolerance. */
+int tbpm_set_fusion(tbpm_ctx* ctx, int enable);
 /* Phase timing.  tbpm_profile(ctx, 1) clears the record and starts recording CUDA events
- * on the context stream around every recurrence loop (kind 0: the Chebyshev passes of a
- * moment request) and every DOS reconstruction (kind 1); tbpm_profile(ctx, 0) stops.
- * tbpm_profile_read() synchronises and returns out[0] = recurrence milliseconds,
- * out[1] = recurrence kernel launches, out[2] = reconstruction milliseconds,
- * out[3] = reconstruction kernel launches, summed over the recorded phases. */
+ * on the context stream around every recurrence loop of a moment request (kind 0: all its
+ * passes), around its fused multi-step passes (kind 2, a sub-interval of kind 0) and around
+ * every DOS reconstruction (kind 1); tbpm_profile(ctx, 0) stops.  tbpm_profile_read()
+ * synchronises and returns, summed over the recorded phases: out[0] = recurrence ms,
+ * out[1] = recurrence kernel launches, out[2] = reconstruction ms, out[3] = reconstruction
+ * launches, out[4] = fused-pass ms, out[5] = fused-pass launches. */
 int tbpm_profile(tbpm_ctx* ctx, int enable);
-int tbpm_profile_read(tbpm_ctx* ctx, double out[4]);
+int tbpm_profile_read(tbpm_ctx* ctx, double out[6]);
 
 /* ---------------------------------------------------------------- lattice */
 
@@ -212,6 +218,41 @@ int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
 int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
                     const double* d_energies, int64_t n_energies, double* d_D);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous batching of DOS / LDOS requests (moment-based form, Jackson reconstruction).
+ * A scheduler thread admits queued requests in arrival order while their HBM footprint fits
+ * the budget, keeps their states resident, and advances every admitted request by one
+ * Chebyshev step per launch of one batched kernel -- requests of any lattice kind, size,
+ * state count and moment count share each launch; requests that arrive while others run join
+ * at the next launch.  Each request's tiling and reduction order depend only on its own
+ * geometry, so its moments and DOS are bit-identical alone and in any mix. */
+typedef struct tbpm_server tbpm_server;
+typedef struct {
+  size_t hbm_budget_bytes; /* device memory for resident requests; 0 = 70% of free memory */
+  int32_t max_active;      /* requests advanced together; 0 = 64 */
+  int32_t max_queue;       /* queued requests before tbpm_submit returns TBPM_EBUSY; 0 = 4096 */
+  int32_t recon;           /* TBPM_RECON_FP64 or TBPM_RECON_TENSOR for the DOS */
+  int32_t reserved;
+} tbpm_server_config;
+
+/* Start a server on ctx's device (it creates its own streams; ctx only names the device). */
+int tbpm_server_create(tbpm_ctx* ctx, const tbpm_server_config* cfg, tbpm_server** out);
+/* Stop the scheduler; queued and running requests end with TBPM_ECANCELLED. */
+int tbpm_server_destroy(tbpm_server* srv);
+/* Queue one request: lattice, request (form ignored: moment-based; n_moments even >= 2;
+ * random states or site states) and the energies [n_energies].  Everything is copied.
+ * *ticket identifies the request.  TBPM_EBUSY when the queue is full. */
+int tbpm_submit(tbpm_server* srv, const tbpm_lattice_desc* lat, const tbpm_request* req,
+                const double* energies, int64_t n_energies, uint64_t* ticket);
+/* Wait up to timeout_us (< 0: forever) for a request; on success copies its DOS, [S][n_energies]
+ * (D_len values available), and latency_us[3] = {queued, admitted-to-done, submit-to-done}.
+ * Returns the request's status (TBPM_ETIMEOUT if not finished in time; the ticket stays valid). */
+int tbpm_wait(tbpm_server* srv, uint64_t ticket, int64_t timeout_us, double* D, size_t D_len,
+              double* latency_us);
+/* out = {queued, active, completed, kernel launches, bytes reserved, byte budget}. */
+int tbpm_server_stats(tbpm_server* srv, int64_t out[6]);
+
 /* ---------------------------------------------------------------- allocation-free step */
 
 /* One pass of the moment kernel with no device allocation at all.  The paper has no
@@ -254,6 +295,14 @@ int64_t tbpm_truncation_order(double tau);
 int tbpm_block_counts(int64_t n_steps, int64_t b, double tau, int64_t out[3]);
 /* b_opt = argmin_b N_amxsy(b) t_amxsy + N_axpy(b) t_axpy over 1 <= b <= b_max (Sec. II.B). */
 int64_t tbpm_block_opt(int64_t n_steps, double tau, double t_amxsy, double t_axpy, int64_t b_max);
+/* Autotuner of the state-based form (Sec. II.B: the per-operation costs are "obtained via
+ * benchmarking prior to the main calculation"): times recurrence passes with no and with
+ * several open accumulators on this lattice and request (precision, S), then returns
+ * *b_opt = tbpm_block_opt(...) with b capped by the free device memory (and by 256).
+ * times_ms (optional) receives t_amxsy and t_axpy in milliseconds.  CONCURRENT_S requests
+ * with time_block = 0 use it. */
+int tbpm_block_autotune(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int64_t n_steps,
+                        int64_t* b_opt, double times_ms[2]);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,11 @@ class LatticeProps(C.Structure):
                 ("E_max", C.c_double), ("H0", C.c_double), ("half_width", C.c_double)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_active", C.c_int32), ("max_queue", C.c_int32),
+                ("recon", C.c_int32), ("reserved", C.c_int32)]
+
+
 class Request(C.Structure):
     _fields_ = [("precision", C.c_int32), ("states", C.c_int32), ("n_states", C.c_int32),
                 ("form", C.c_int32), ("state_seed", C.c_uint64), ("sites", C.POINTER(C.c_int64)),
@@ -74,6 +79,7 @@ def load():
         "tbpm_sync": (C.c_int, [_P]),
         "tbpm_launch_count": (C.c_int64, [_P]),
         "tbpm_profile": (C.c_int, [_P, C.c_int]),
+        "tbpm_set_fusion": (C.c_int, [_P, C.c_int]),
         "tbpm_profile_read": (C.c_int, [_P, C.POINTER(C.c_double)]),
         "tbpm_lattice_create": (C.c_int, [_P, C.POINTER(LatticeDesc), C.POINTER(_P)]),
         "tbpm_lattice_destroy": (C.c_int, [_P]),
@@ -90,9 +96,17 @@ def load():
         "tbpm_moment_step_noalloc": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_double,
                                                 C.c_double, _P, C.c_int, C.c_int, _P, _P, _P, C.c_int64,
                                                 C.c_int64, _P]),
+        "tbpm_server_create": (C.c_int, [_P, C.POINTER(ServerConfig), C.POINTER(_P)]),
+        "tbpm_server_destroy": (C.c_int, [_P]),
+        "tbpm_submit": (C.c_int, [_P, C.POINTER(LatticeDesc), C.POINTER(Request), _P, C.c_int64,
+                                  C.POINTER(C.c_uint64)]),
+        "tbpm_wait": (C.c_int, [_P, C.c_uint64, C.c_int64, _P, C.c_size_t, C.POINTER(C.c_double)]),
+        "tbpm_server_stats": (C.c_int, [_P, C.POINTER(C.c_int64)]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
+        "tbpm_block_autotune": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int64, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -105,10 +119,12 @@ def load():
 def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
-            "tbpm_launch_count", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
+            "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
-            "tbpm_dos_device", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt"]
+            "tbpm_dos_device", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
+            "tbpm_server_stats"]
 
 
 def _check(status: int):
@@ -159,15 +175,20 @@ def tbpm_launch_count(ctx) -> int:
     return int(load().tbpm_launch_count(ctx))
 
 
+def tbpm_set_fusion(ctx, enable: bool):
+    _check(load().tbpm_set_fusion(ctx, int(bool(enable))))
+
+
 def tbpm_profile(ctx, enable: bool):
     _check(load().tbpm_profile(ctx, int(bool(enable))))
 
 
 def tbpm_profile_read(ctx) -> dict:
-    out = (C.c_double * 4)()
+    out = (C.c_double * 6)()
     _check(load().tbpm_profile_read(ctx, out))
     return {"recurrence_ms": out[0], "recurrence_launches": int(out[1]),
-            "recon_ms": out[2], "recon_launches": int(out[3])}
+            "recon_ms": out[2], "recon_launches": int(out[3]),
+            "fused_ms": out[4], "fused_launches": int(out[5])}
 
 
 # ---------------------------------------------------------------- lattice
@@ -270,6 +291,39 @@ def tbpm_moment_step_noalloc(kind, L, pbc, t_scaled, diag_const, d_diag, precisi
                                            int(step), C.c_void_p(int(stream)) if stream else None))
 
 
+# ---------------------------------------------------------------- serving
+def tbpm_server_create(ctx, hbm_budget_bytes=0, max_active=0, max_queue=0, recon=RECON_FP64):
+    h = _P()
+    cfg = ServerConfig(int(hbm_budget_bytes), int(max_active), int(max_queue), int(recon), 0)
+    _check(load().tbpm_server_create(ctx, C.byref(cfg), C.byref(h)))
+    return h
+
+
+def tbpm_server_destroy(srv):
+    _check(load().tbpm_server_destroy(srv))
+
+
+def tbpm_submit(srv, desc: LatticeDesc, req: Request, energies: np.ndarray) -> int:
+    t = C.c_uint64()
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    _check(load().tbpm_submit(srv, C.byref(desc), C.byref(req), _host_ptr(e), int(e.size), C.byref(t)))
+    return int(t.value)
+
+
+def tbpm_wait(srv, ticket: int, D: np.ndarray, timeout_us: int = -1):
+    """Fills D ([S][n_energies]) and returns (queued_us, run_us, total_us)."""
+    lat = (C.c_double * 3)()
+    _check(load().tbpm_wait(srv, C.c_uint64(ticket), int(timeout_us), _host_ptr(D), int(D.size), lat))
+    return float(lat[0]), float(lat[1]), float(lat[2])
+
+
+def tbpm_server_stats(srv) -> dict:
+    out = (C.c_int64 * 6)()
+    _check(load().tbpm_server_stats(srv, out))
+    return dict(zip(("queued", "active", "completed", "launches", "reserved_bytes", "budget_bytes"),
+                    (int(v) for v in out)))
+
+
 # ---------------------------------------------------------------- cost model
 def tbpm_truncation_order(tau: float) -> int:
     return int(load().tbpm_truncation_order(float(tau)))
@@ -283,3 +337,11 @@ def tbpm_block_counts(n_steps: int, b: int, tau: float) -> tuple:
 
 def tbpm_block_opt(n_steps: int, tau: float, t_amxsy: float, t_axpy: float, b_max: int) -> int:
     return int(load().tbpm_block_opt(int(n_steps), float(tau), float(t_amxsy), float(t_axpy), int(b_max)))
+
+
+def tbpm_block_autotune(ctx, lat, req: Request, n_steps: int):
+    """Returns (b_opt, t_amxsy_ms, t_axpy_ms) measured on the device."""
+    b = C.c_int64()
+    t = (C.c_double * 2)()
+    _check(load().tbpm_block_autotune(ctx, lat, C.byref(req), int(n_steps), C.byref(b), t))
+    return int(b.value), float(t[0]), float(t[1])

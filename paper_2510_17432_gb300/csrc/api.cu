@@ -362,7 +362,8 @@ int tbpm_destroy(tbpm_ctx* ctx) {
   cudaSetDevice(ctx->device);
   DevBuf* bufs[] = {&ctx->ws_phi[0], &ctx->ws_phi[1], &ctx->ws_psi, &ctx->ws_acc, &ctx->ws_partials,
                     &ctx->ws_counter, &ctx->ws_mu, &ctx->ws_table, &ctx->ws_aux, &ctx->ws_out,
-                    &ctx->ws_energies, &ctx->ws_recon};
+                    &ctx->ws_energies, &ctx->ws_recon, &ctx->ws_phi2[0], &ctx->ws_phi2[1],
+                    &ctx->ws_fused_partials};
   for (DevBuf* b : bufs) release(ctx, *b);
   cudaStreamSynchronize(ctx->stream);
   for (auto& ph : ctx->phases) {
@@ -390,6 +391,16 @@ int tbpm_sync(tbpm_ctx* ctx) {
 
 int64_t tbpm_launch_count(const tbpm_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_set_fusion: ctx is NULL");
+    return TBPM_EINVAL;
+  }
+  ctx->fusion = enable != 0;
+  return TBPM_OK;
+}
+
 int tbpm_profile(tbpm_ctx* ctx, int enable) {
   clear_error();
   if (!ctx) {
@@ -406,14 +417,14 @@ int tbpm_profile(tbpm_ctx* ctx, int enable) {
   return TBPM_OK;
 }
 
-int tbpm_profile_read(tbpm_ctx* ctx, double out[4]) {
+int tbpm_profile_read(tbpm_ctx* ctx, double out[6]) {
   clear_error();
   if (!ctx || !out) {
     set_error("tbpm_profile_read: NULL argument");
     return TBPM_EINVAL;
   }
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  for (int k = 0; k < 4; ++k) out[k] = 0.0;
+  for (int k = 0; k < 6; ++k) out[k] = 0.0;
   for (auto& ph : ctx->phases) {
     float ms = 0.f;
     TBPM_CK(cudaEventElapsedTime(&ms, ph.a, ph.b));
@@ -761,6 +772,7 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
   }
   a->diag_const = (0.0 - lat->H0) / lat->half;
   a->thop = lat->desc.t / lat->half;
+  set_float_coefficients(a);
   a->n_sites = lat->n_sites;
   a->S = pl.Spad;
   a->P = pl.P;
@@ -792,12 +804,42 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
   a.mu = d_mu;
   a.M = (int)M;
   const int tok = phase_begin(ctx, 0);
-  for (int64_t n = 0; n < M / 2; ++n) {
-    a.cur = ctx->ws_phi[n & 1].p;
-    a.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+  // step n reads cur = phi_n, overwrites prev (phi_{n-1}) with phi_{n+1}; then the roles swap
+  void* cur = ctx->ws_phi[0].p;
+  void* prev = ctx->ws_phi[1].p;
+  int64_t n = 0;
+  const int K = fused_steps();
+  const bool fuse = ctx->fusion && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= K;
+  if (fuse) {
+    TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pl.state_bytes));
+  }
+  auto unfused = [&]() -> int {
+    a.cur = cur;
+    a.prev_out = prev;
     a.step = (int)n;
     TBPM_TRY(launch_moment_step(ctx, a, pl.precision, n == 0));
+    std::swap(cur, prev);
+    ++n;
+    return TBPM_OK;
+  };
+  TBPM_TRY(unfused());  // phi_1 = H~ phi_0, m_0, m_1
+  if (fuse) {
+    const int ftok = phase_begin(ctx, 2);
+    void* pair_out[2] = {ctx->ws_phi2[0].p, ctx->ws_phi2[1].p};
+    while (n + K <= M / 2) {
+      TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n));
+      void* old_prev = prev;
+      void* old_cur = cur;
+      prev = pair_out[0];
+      cur = pair_out[1];
+      pair_out[0] = old_prev;
+      pair_out[1] = old_cur;
+      n += K;
+    }
+    phase_end(ctx, ftok);
   }
+  while (n < M / 2) TBPM_TRY(unfused());
   phase_end(ctx, tok);
   return TBPM_OK;
 }
@@ -830,15 +872,74 @@ void block_coefficients(double tau, double shift, int bb, std::vector<double>* c
   }
 }
 
-// b from the Tab. I cost model with per-site costs from the bytes each pass moves:
-// one term of the recurrence reads phi_n, phi_{n-1} and writes phi_{n+1} (24 B per complex64
-// site-state), one axpy reads and writes an accumulator (16 B).  Capped by free memory.
-int64_t choose_block(const tbpm_lattice* lat, const Plan& pl, int64_t n_steps) {
+// Largest b whose accumulators fit in 80% of the free device memory (and <= 256, <= n_steps).
+int64_t block_cap(const Plan& pl, int64_t n_steps) {
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const int64_t by_mem = (int64_t)std::max<double>(1.0, 0.8 * (double)free_b / (double)pl.state_bytes - 4.0);
-  const int64_t cap = std::min<int64_t>(std::min<int64_t>(by_mem, 256), n_steps);
-  return tbpm_block_opt(n_steps, pl.tau, 3.0, 2.0, cap);
+  return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(by_mem, 256), n_steps));
+}
+
+// Measured per-pass costs of the state-based form (Sec. II.B: "obtained via benchmarking prior
+// to the main calculation"): t_amxsy = one recurrence pass with no accumulator open,
+// t_axpy = the extra time per open accumulator.  Times in milliseconds.
+int measure_pass_costs(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int k_acc,
+                       double* t_amxsy, double* t_axpy) {
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_acc, pl.state_bytes * (size_t)k_acc));
+  TBPM_TRY(ensure(ctx, ctx->ws_table, sizeof(double) * 2 * (size_t)k_acc));
+  TBPM_CK(cudaMemsetAsync(ctx->ws_table.p, 0, sizeof(double) * 2 * (size_t)k_acc, ctx->stream));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[1].p, nullptr));
+  TBPM_CK(cudaMemsetAsync(ctx->ws_acc.p, 0, pl.state_bytes * (size_t)k_acc, ctx->stream));
+  AccumArgs g;
+  memset(&g, 0, sizeof(g));
+  TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
+  g.acc = ctx->ws_acc.p;
+  g.acc_stride = lat->n_sites * (int64_t)pl.Spad;
+  g.coef = (const double*)ctx->ws_table.p;
+  g.psi = ctx->ws_psi.p;
+  g.j_done = -1;
+  g.r.cur = ctx->ws_phi[0].p;
+  g.r.prev_out = ctx->ws_phi[1].p;
+  cudaEvent_t e[3];
+  for (auto& x : e) TBPM_CK(cudaEventCreate(&x));
+  const int reps = 3;
+  float ms0 = 0.f, ms1 = 0.f;
+  int r = TBPM_OK;
+  for (int pass = 0; pass < 2 && r == TBPM_OK; ++pass) {   // pass 0 warms up
+    g.b = 0;
+    g.j_lo = 0;
+    cudaEventRecord(e[0], ctx->stream);
+    for (int i = 0; i < reps && r == TBPM_OK; ++i) r = launch_accum_step(ctx, g, pl.precision, ACC_REGULAR);
+    cudaEventRecord(e[1], ctx->stream);
+    g.b = k_acc;
+    for (int i = 0; i < reps && r == TBPM_OK; ++i) r = launch_accum_step(ctx, g, pl.precision, ACC_REGULAR);
+    cudaEventRecord(e[2], ctx->stream);
+  }
+  if (r == TBPM_OK && cudaEventSynchronize(e[2]) == cudaSuccess) {
+    cudaEventElapsedTime(&ms0, e[0], e[1]);
+    cudaEventElapsedTime(&ms1, e[1], e[2]);
+  }
+  for (auto& x : e) cudaEventDestroy(x);
+  TBPM_TRY(r);
+  *t_amxsy = ms0 / reps;
+  *t_axpy = std::max(1e-6, (double)(ms1 - ms0) / reps / k_acc);
+  return TBPM_OK;
+}
+
+// b_opt = argmin_b C(b) with measured costs (Sec. II.B), capped by memory.
+int choose_block(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t n_steps,
+                 int64_t* b, double* t_amxsy, double* t_axpy) {
+  const int64_t cap = block_cap(pl, n_steps);
+  double ta = 0, tx = 0;
+  TBPM_TRY(measure_pass_costs(ctx, lat, req, pl, (int)std::min<int64_t>(cap, 8), &ta, &tx));
+  if (t_amxsy) *t_amxsy = ta;
+  if (t_axpy) *t_axpy = tx;
+  *b = tbpm_block_opt(n_steps, pl.tau, ta, tx, cap);
+  return TBPM_OK;
 }
 
 // State-based propagation in blocks of b steps; b = 1 is the sequential form.
@@ -948,7 +1049,8 @@ int run_correlation(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, c
   }
   if (req->form == TBPM_SEQUENTIAL) return run_blocks(ctx, lat, req, pl, n_steps, 1, d_C);
   if (req->form == TBPM_CONCURRENT_S) {
-    const int64_t b = req->time_block > 0 ? req->time_block : choose_block(lat, pl, n_steps);
+    int64_t b = req->time_block;
+    if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, &b, nullptr, nullptr));
     return run_blocks(ctx, lat, req, pl, n_steps, b, d_C);
   }
   set_error("unknown form %d", req->form);
@@ -989,6 +1091,20 @@ int run_dos(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Pla
 }
 
 }  // namespace
+
+namespace tbpm {
+int lattice_ensure_d64(tbpm_lattice* lat) {
+  TBPM_TRY(ensure_d64(lat));
+  TBPM_CK(cudaStreamSynchronize(lat->ctx->stream));
+  return TBPM_OK;
+}
+
+int init_request_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, void* dst) {
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  return init_states(ctx, lat, req, pl, dst, nullptr);
+}
+}  // namespace tbpm
 
 // ====================================================================== C ABI: hot path
 extern "C" {
@@ -1167,6 +1283,7 @@ int tbpm_apply_hopping(tbpm_ctx* ctx, const tbpm_lattice* lat_c, int precision, 
   a.diag = nullptr;
   a.diag_const = 0.0;
   a.thop = 1.0;
+  set_float_coefficients(&a);
   a.mu = (double*)ctx->ws_mu.p;
   a.M = 2;
   a.cur = ctx->ws_phi[0].p;
@@ -1174,6 +1291,28 @@ int tbpm_apply_hopping(tbpm_ctx* ctx, const tbpm_lattice* lat_c, int precision, 
   TBPM_TRY(launch_moment_step(ctx, a, pl.precision, true));
   TBPM_CK(cudaMemcpyAsync(y, ctx->ws_phi[1].p, pl.state_bytes, cudaMemcpyDeviceToHost, ctx->stream));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+// Block-size autotuner: measures t_amxsy and t_axpy on this lattice and request, then minimises
+// the Tab. I cost model (Sec. II.B) under the memory cap.
+int tbpm_block_autotune(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int64_t n_steps,
+                        int64_t* b_opt, double times_ms[2]) {
+  clear_error();
+  if (!ctx || !lat_c || !req || !b_opt || n_steps < 1) {
+    set_error("tbpm_block_autotune: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  double ta = 0, tx = 0;
+  TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, b_opt, &ta, &tx));
+  if (times_ms) {
+    times_ms[0] = ta;
+    times_ms[1] = tx;
+  }
   return TBPM_OK;
 }
 

@@ -21,146 +21,9 @@
 #include <unordered_map>
 
 #include "tbpm_internal.cuh"
+#include "stencil.cuh"
 
 namespace tbpm {
-
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-
-// ------------------------------------------------------------------ 16-byte state packs
-template <typename R, int SPT>
-struct Pack {
-  R v[2 * SPT];
-};
-
-template <typename R, int SPT>
-__device__ __forceinline__ Pack<R, SPT> ld(const Pack<R, SPT>* p) {
-  Pack<R, SPT> r;
-  if constexpr (sizeof(Pack<R, SPT>) == 16) {
-    if constexpr (sizeof(R) == 4) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
-    } else {
-      const double2 q = __ldg(reinterpret_cast<const double2*>(p));
-      r.v[0] = q.x; r.v[1] = q.y;
-    }
-  } else {
-    const float2 q = __ldg(reinterpret_cast<const float2*>(p));
-    r.v[0] = q.x; r.v[1] = q.y;
-  }
-  return r;
-}
-
-template <typename R, int SPT>
-__device__ __forceinline__ Pack<R, SPT> ld_stream(const Pack<R, SPT>* p) {
-  Pack<R, SPT> r;
-  if constexpr (sizeof(Pack<R, SPT>) == 16) {
-    if constexpr (sizeof(R) == 4) {
-      const float4 q = __ldcs(reinterpret_cast<const float4*>(p));
-      r.v[0] = q.x; r.v[1] = q.y; r.v[2] = q.z; r.v[3] = q.w;
-    } else {
-      const double2 q = __ldcs(reinterpret_cast<const double2*>(p));
-      r.v[0] = q.x; r.v[1] = q.y;
-    }
-  } else {
-    const float2 q = __ldcs(reinterpret_cast<const float2*>(p));
-    r.v[0] = q.x; r.v[1] = q.y;
-  }
-  return r;
-}
-
-template <typename R, int SPT>
-__device__ __forceinline__ void st(Pack<R, SPT>* p, const Pack<R, SPT>& r) {
-  if constexpr (sizeof(Pack<R, SPT>) == 16) {
-    if constexpr (sizeof(R) == 4) {
-      *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-    } else {
-      *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
-    }
-  } else {
-    *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
-  }
-}
-
-template <typename R, int SPT>
-__device__ __forceinline__ void st_stream(Pack<R, SPT>* p, const Pack<R, SPT>& r) {
-  if constexpr (sizeof(Pack<R, SPT>) == 16) {
-    if constexpr (sizeof(R) == 4) {
-      __stcs(reinterpret_cast<float4*>(p), make_float4(r.v[0], r.v[1], r.v[2], r.v[3]));
-    } else {
-      __stcs(reinterpret_cast<double2*>(p), make_double2(r.v[0], r.v[1]));
-    }
-  } else {
-    __stcs(reinterpret_cast<float2*>(p), make_float2(r.v[0], r.v[1]));
-  }
-}
-
-// ------------------------------------------------------------------ accumulators
-// Neumaier-compensated FP32 sum (complex64 path) or plain FP64 sum (complex128 path).
-template <typename R>
-struct Acc;
-
-template <>
-struct Acc<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    c += (fabsf(s) >= fabsf(x)) ? ((s - t) + x) : ((x - t) + s);
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
-template <>
-struct Acc<double> {
-  double s = 0.0;
-  __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ double value() const { return s; }
-};
-
-// ------------------------------------------------------------------ grid reduction
-// Every thread holds NV values for its states (states p*SPT .. p*SPT+SPT-1, C values each,
-// p = threadIdx.x % P).  Sums them over the grid and calls fin(q, total) for q = s*C + c in
-// the last block.  Deterministic: fixed trees and a fixed block order.
-template <int NV, int SPT, int C, typename Fin>
-__device__ __forceinline__ void grid_reduce(double (&v)[NV], int P, int S, double* partials,
-                                            unsigned* counter, int nblocks, Fin fin) {
-  static_assert(NV == SPT * C, "values per thread");
-  __shared__ double red[kWarps][32][NV];
-  __shared__ unsigned ticket;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    for (int off = 16; off >= P; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-  }
-  if (lane < P) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red[warp][lane][k] = v[k];
-  }
-  __syncthreads();
-  const int SC = S * C;
-  if (threadIdx.x < SC) {
-    const int q = threadIdx.x, s = q / C, c = q - s * C;
-    const int p = s / SPT, k = (s - p * SPT) * C + c;
-    double acc = 0.0;
-    for (int w = 0; w < kWarps; ++w) acc += red[w][p][k];
-    partials[(size_t)blockIdx.x * SC + q] = acc;
-    __threadfence();
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) ticket = atomicAdd(counter, 1u);
-  __syncthreads();
-  if (ticket != (unsigned)(nblocks - 1)) return;
-  // last block: sum the partials in block order, one warp per output value
-  __threadfence();
-  for (int q = warp; q < SC; q += kWarps) {
-    double acc = 0.0;
-    for (int b = lane; b < nblocks; b += 32) acc += __ldcg(partials + (size_t)b * SC + q);
-    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) fin(q, acc);
-  }
-  if (threadIdx.x == 0) *counter = 0u;
-}
 
 // ------------------------------------------------------------------ H~ phi for one unit
 // Computes hphi = sum over neighbours of phi_j and the per-site diagonal term.
@@ -275,7 +138,7 @@ __device__ __forceinline__ void for_each_unit(const RecurrenceArgs& a, F f) {
 
 template <typename R>
 __device__ __forceinline__ R site_diag(const RecurrenceArgs& a, int64_t site) {
-  if (a.diag == nullptr) return (R)a.diag_const;
+  if (a.diag == nullptr) return coef_dc<R>(a, true);
   return __ldg(reinterpret_cast<const R*>(a.diag) + site);
 }
 
@@ -286,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_moment_step(RecurrenceArgs a) {
   const PK* cur = reinterpret_cast<const PK*>(a.cur);
   PK* po = reinterpret_cast<PK*>(a.prev_out);
   const int p = threadIdx.x & (a.P - 1);
-  const R th = FIRST ? (R)a.thop : (R)(2.0 * a.thop);
+  const R th = coef_th<R>(a, FIRST);
   Acc<R> A[SPT], Br[SPT], Bi[SPT];
 
   for_each_unit<KIND, CSR, R, SPT>(a, [&](int64_t site, int64_t x, int64_t sir,
@@ -347,85 +210,6 @@ __global__ void __launch_bounds__(kThreads) k_moment_step(RecurrenceArgs a) {
 // line are 32-bit.  The inner products are summed in FP32 over at most 32 units per thread
 // and then folded into FP64 (GB300 issues only 2 FP64 operations per clock per SM, so FP64
 // work per unit is kept to a fraction of an operation).
-template <typename R>
-struct Partial;
-template <>
-struct Partial<float> {
-  float f = 0.f;
-  double d = 0.0;
-  __device__ __forceinline__ void add(float x) { f += x; }
-  __device__ __forceinline__ void fold() { d += (double)f; f = 0.f; }
-  __device__ __forceinline__ double value() const { return d + (double)f; }
-};
-template <>
-struct Partial<double> {
-  double d = 0.0;
-  __device__ __forceinline__ void add(double x) { d += x; }
-  __device__ __forceinline__ void fold() {}
-  __device__ __forceinline__ double value() const { return d; }
-};
-
-// Unit bases of the line and of its neighbouring lines (-1 when an open boundary drops them).
-struct LineBases {
-  int64_t own, up, dn, zup, zdn;
-};
-
-template <int KIND>
-__device__ __forceinline__ LineBases line_bases(const Geom& g, int64_t row, int64_t upr) {
-  LineBases b;
-  int64_t y = row, zc = 0;
-  if constexpr (KIND == TBPM_CUBIC) {
-    y = row % g.Ly;
-    zc = row / g.Ly;
-  }
-  b.own = row * upr;
-  int64_t r;
-  r = (y + 1 < g.Ly) ? row + 1 : (g.pbc_y ? row + 1 - g.Ly : -1);
-  b.up = r >= 0 ? r * upr : -1;
-  r = (y > 0) ? row - 1 : (g.pbc_y ? row - 1 + g.Ly : -1);
-  b.dn = r >= 0 ? r * upr : -1;
-  b.zup = b.zdn = -1;
-  if constexpr (KIND == TBPM_CUBIC) {
-    const int64_t plane = g.Ly, vol = g.Ly * g.Lz;
-    r = (zc + 1 < g.Lz) ? row + plane : (g.pbc_z ? row + plane - vol : -1);
-    b.zup = r >= 0 ? r * upr : -1;
-    r = (zc > 0) ? row - plane : (g.pbc_z ? row - plane + vol : -1);
-    b.zdn = r >= 0 ? r * upr : -1;
-  }
-  return b;
-}
-
-// Neighbour unit offsets of in-line unit u (absolute, -1 = none); returns the count.
-template <int KIND>
-__device__ __forceinline__ int stencil_neighbours(const Geom& g, const LineBases& b, int u, int P, int logP,
-                                                  int p, int upr, int64_t (&nb)[6]) {
-  const int64_t Lx = g.Lx;
-  if constexpr (KIND == TBPM_HONEYCOMB) {
-    const int sir = u >> logP, s = sir & 1, xc = sir >> 1;
-    nb[0] = b.own + (u ^ P);
-    if (s) {
-      nb[1] = (xc < Lx - 1) ? b.own + u + P : (g.pbc_x ? b.own + p : -1);
-      nb[2] = b.up >= 0 ? b.up + u - P : -1;
-    } else {
-      nb[1] = (xc > 0) ? b.own + u - P : (g.pbc_x ? b.own + u - P + upr : -1);
-      nb[2] = b.dn >= 0 ? b.dn + u + P : -1;
-    }
-    return 3;
-  } else {
-    const int xc = u >> logP;
-    nb[0] = (xc < Lx - 1) ? b.own + u + P : (g.pbc_x ? b.own + p : -1);
-    nb[1] = (xc > 0) ? b.own + u - P : (g.pbc_x ? b.own + u - P + upr : -1);
-    nb[2] = b.up >= 0 ? b.up + u : -1;
-    nb[3] = b.dn >= 0 ? b.dn + u : -1;
-    if constexpr (KIND == TBPM_CUBIC) {
-      nb[4] = b.zup >= 0 ? b.zup + u : -1;
-      nb[5] = b.zdn >= 0 ? b.zdn + u : -1;
-      return 6;
-    }
-    return 4;
-  }
-}
-
 template <int KIND, typename R, int SPT, bool FIRST>
 __global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a) {
   using PK = Pack<R, SPT>;
@@ -438,8 +222,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a
   const int P = a.P, logP = a.logP, p = threadIdx.x & (P - 1);
   const int upr = (int)(g.row_sites * P);
   const int stpr = (upr + TU - 1) / TU;
-  const R th = FIRST ? (R)a.thop : (R)(2.0 * a.thop);
-  const R dc = FIRST ? (R)a.diag_const : (R)(2.0 * a.diag_const);
+  const R th = coef_th<R>(a, FIRST);
+  const R dc = coef_dc<R>(a, FIRST);
   Partial<R> A[SPT], Br[SPT], Bi[SPT];
 
   int64_t row = blockIdx.x / stpr;
@@ -560,8 +344,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_accum_stencil(AccumArgs gargs) 
   const int P = a.P, logP = a.logP, p = threadIdx.x & (P - 1);
   const int upr = (int)(g.row_sites * P);
   const int tpr = (upr + kThreads - 1) / kThreads;
-  const R th = (MODE == ACC_FIRST) ? (R)a.thop : (R)(2.0 * a.thop);
-  const R dc = (MODE == ACC_FIRST) ? (R)a.diag_const : (R)(2.0 * a.diag_const);
+  const R th = coef_th<R>(a, MODE == ACC_FIRST);
+  const R dc = coef_dc<R>(a, MODE == ACC_FIRST);
   const int64_t astr = gargs.acc_stride / SPT;
   const int jlo = gargs.j_lo, jb = gargs.b, jdone = gargs.j_done;
   const bool first_term = gargs.first_term != 0;
@@ -683,7 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_accum_step(AccumArgs g) {
   PK* acc = reinterpret_cast<PK*>(g.acc);
   const PK* psi = reinterpret_cast<const PK*>(g.psi);
   const int p = threadIdx.x & (a.P - 1);
-  const R th = (MODE == ACC_FIRST) ? (R)a.thop : (R)(2.0 * a.thop);
+  const R th = coef_th<R>(a, MODE == ACC_FIRST);
   const int64_t astr = g.acc_stride / SPT;  // in packs
   Acc<R> Cr[SPT], Ci[SPT];
 
@@ -1002,6 +786,7 @@ extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int3
   a.diag = d_diag;
   a.diag_const = diag_const;
   a.thop = t_scaled;
+  set_float_coefficients(&a);
   a.n_sites = g.n_full;
   const int spt = (precision == TBPM_C64 && n_states >= 2) ? 2 : 1;
   a.S = n_states;

@@ -403,15 +403,15 @@ static int run_gemm(tbpm_ctx* ctx, const CUtensorMap& mA, const CUtensorMap& mB,
 
 }  // namespace tc
 
-int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies, int64_t nE,
-                              double H0, double half, double* D) {
+int launch_dos_jackson_tensor_async(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
+                                    int64_t nE, double H0, double half, double* D, int* h_err) {
   using namespace tc;
   if (S > 16) {
     // two passes over state groups keep the epilogue's FP64 sums in registers
     const int S1 = 16;
-    TBPM_TRY(launch_dos_jackson_tensor(ctx, mu, S1, M, energies, nE, H0, half, D));
-    return launch_dos_jackson_tensor(ctx, mu + (size_t)S1 * M * 2, S - S1, M, energies, nE, H0, half,
-                                     D + (size_t)S1 * nE);
+    TBPM_TRY(launch_dos_jackson_tensor_async(ctx, mu, S1, M, energies, nE, H0, half, D, h_err));
+    return launch_dos_jackson_tensor_async(ctx, mu + (size_t)S1 * M * 2, S - S1, M, energies, nE, H0, half,
+                                           D + (size_t)S1 * nE, h_err);
   }
   if (nE > (1 << 24) || M < 1) {
     set_error("tensor reconstruction: n_energies or n_moments out of range");
@@ -422,7 +422,7 @@ int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, con
   const int rows_pad = (int)((nE + BM - 1) / BM * BM);
   const int m_tiles = rows_pad / BM;
   const int kt_total = 3 * Mp / BK;
-  int splits = (2 * ctx->num_sms + m_tiles - 1) / m_tiles;
+  int splits = (2 * ctx->num_sms) / m_tiles;  // one wave at 2 resident CTAs per SM
   splits = std::max(1, std::min(splits, kt_total / CHUNK));
   const int kt_per_split = (kt_total + splits - 1) / splits;
   splits = (kt_total + kt_per_split - 1) / kt_per_split;
@@ -463,12 +463,23 @@ int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, con
   k_finalize<<<(int)std::min<int64_t>((gf + 255) / 256, (int64_t)ctx->num_sms * 16), 256, 0, ctx->stream>>>(
       partials, splits, rows_pad, NP, S, energies, nE, H0, half, D);
   TBPM_CK_LAUNCH(ctx);
-  // a timed-out wait inside the GEMM is reported, never hidden
-  int h_err = 0;
-  TBPM_CK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  // a timed-out wait inside the GEMM is reported, never hidden: OR the flag into *h_err
+  if (h_err) TBPM_CK(cudaMemcpyAsync(h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  return TBPM_OK;
+}
+
+int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies, int64_t nE,
+                              double H0, double half, double* D) {
+  if (ctx->pinned_cap < 16) {
+    set_error("context has no pinned status word");
+    return TBPM_ECUDA;
+  }
+  int* h_err = reinterpret_cast<int*>(ctx->pinned + 1);
+  *h_err = 0;
+  TBPM_TRY(launch_dos_jackson_tensor_async(ctx, mu, S, M, energies, nE, H0, half, D, h_err));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  if (h_err) {
-    set_error("tensor-core reconstruction: bounded wait expired (code %d)", h_err);
+  if (*h_err) {
+    set_error("tensor-core reconstruction: bounded wait expired (code %d)", *h_err);
     return TBPM_ETIMEOUT;
   }
   return TBPM_OK;

@@ -152,7 +152,8 @@ struct tbpm_ctx {
   int64_t launches = 0;
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
-      ws_energies, ws_recon;
+      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials;
+  bool fusion = true;  // temporal fusion of the moment pass where a fused kernel applies
   double* pinned = nullptr;
   size_t pinned_cap = 0;
   // phase timing with CUDA events on the context stream (tbpm_profile)
@@ -206,6 +207,9 @@ struct RecurrenceArgs {
   const void* diag;    // per-site D_i (float* or double*), or null when the lattice is clean
   double diag_const;   // D when diag == null
   double thop;         // t / |H|
+  // the same coefficients pre-rounded for the FP32 kernels: first term (x1) and regular
+  // terms (x2); kept in the argument block so no kernel recomputes them in FP64
+  float th1f, th2f, dc1f, dc2f;
   int64_t n_sites;
   // states-per-thread layout: P = S / spt thread units per site
   int S, P, logP;
@@ -235,11 +239,25 @@ struct AccumArgs {
   int j_global;         // time index of accumulator j_done
 };
 
+// fills th1f/th2f/dc1f/dc2f from thop and diag_const
+inline void set_float_coefficients(RecurrenceArgs* a) {
+  a->th1f = (float)a->thop;
+  a->th2f = (float)(2.0 * a->thop);
+  a->dc1f = (float)a->diag_const;
+  a->dc2f = (float)(2.0 * a->diag_const);
+}
+
 int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first);
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
+
+// temporal fusion (csrc/fused.cu)
+bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad);
+int fused_steps();
+int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                      const void* cur_in, void* prev_out, void* cur_out, int step0);
 
 enum { ACC_FIRST = 0, ACC_REGULAR = 1, ACC_NOSPMV = 2 };
 
@@ -253,6 +271,12 @@ int launch_dos_jackson_fp64(tbpm_ctx* ctx, const double* mu, int S, int M, const
                             int64_t nE, double H0, double half, double* D);
 int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
                               int64_t nE, double H0, double half, double* D);
+// same, without synchronising: the GEMM's bounded-wait status is copied to pinned *h_err
+int launch_dos_jackson_tensor_async(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
+                                    int64_t nE, double H0, double half, double* D, int* h_err);
+// FP64 D_i of a lattice (made on first use), and a request's initial state block
+int lattice_ensure_d64(tbpm_lattice* lat);
+int init_request_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, void* dst);
 int launch_dos_fourier(tbpm_ctx* ctx, const double* C, int S, int n_steps, const double* energies,
                        int64_t nE, double tau_phys, int window, double* D);
 

@@ -298,3 +298,30 @@ def test_full_size_graphene_sampled(capi, ctx):
     ref = oprop.moments(ol, psi, psi, 32)
     assert np.max(np.abs(mu[0, :32] - ref)) <= 1e-5
     capi.tbpm_lattice_destroy(lat)
+
+
+# ---------------------------------------------------------------- temporal fusion (4 steps per pass)
+
+FUSED_CASES = [
+    ("honey48x36_exact_tile", dict(kind=1, L=(48, 36), t=-2.7, W=0.0), 2, 64),
+    ("honey101x77_ragged_W1", dict(kind=1, L=(101, 77), t=-2.7, W=1.0), 8, 202),
+    ("honey90x70_open_x", dict(kind=1, L=(90, 70), t=-2.7, W=0.5, pbc=(0, 1, 1)), 4, 130),
+    ("honey60x100_open_y", dict(kind=1, L=(60, 100), t=1.0, W=2.0, pbc=(1, 0, 1)), 16, 96),
+    ("honey50x40_open_xy_S32", dict(kind=1, L=(50, 40), t=-2.7, W=1.0, pbc=(0, 0, 1)), 32, 38),
+]
+
+
+@pytest.mark.parametrize("name,spec,S,M", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
+def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M):
+    lat, ol = make(capi, ctx, **spec)
+    capi.tbpm_set_fusion(ctx, True)
+    mf = gpu_moments(capi, ctx, lat, S, M, 0)
+    capi.tbpm_set_fusion(ctx, False)
+    mu = gpu_moments(capi, ctx, lat, S, M, 0)
+    capi.tbpm_set_fusion(ctx, True)
+    assert np.max(np.abs(mf - mu)) <= 1e-6
+    psi = oprop.random_phase_states(ol, 3, S)
+    for s in (0, S - 1):
+        ref = oprop.moments(ol, psi[s], psi[s], M)
+        assert np.max(np.abs(mf[s] - ref)) <= 1e-5
+    capi.tbpm_lattice_destroy(lat)
