@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--fusion", type=int, default=0,
+                   help="moment-pass fusion mode: 0 = one step per pass, 1..3 = fused variants")
     p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
     p.add_argument("--requests", type=int, default=512)
     p.add_argument("--log2-max-sites", type=int, default=20)
@@ -239,6 +241,7 @@ def run_gpu(args, work):
         pg = dist
 
     ctx = capi.tbpm_create(local)
+    capi.tbpm_set_fusion(ctx, args.fusion)
     spec = work.lattice
     desc = capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, vacancy_frac=spec.vacancy_frac,
                              seed=spec.seed, pbc=spec.pbc, path=spec.path)
@@ -323,10 +326,10 @@ def run_gpu(args, work):
     per_site_step = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
     total_alg = per_site_step * (M // 2) * args.steps
     if prof["fused_launches"] > 0:
-        steps_per_launch = 4
-        kname = "k_fused_honeycomb (4 Chebyshev steps per pass, complex64 state pairs)"
+        steps_per_launch = {1: 4, 2: 2}[args.fusion]
+        kname = f"k_fused_cols ({steps_per_launch} Chebyshev steps per pass, complex64 state pairs)"
         per_launch_ms = prof["fused_ms"] / prof["fused_launches"]
-        traffic_key = f"k_fused_honeycomb/{work.name}"
+        traffic_key = f"k_fused_cols{steps_per_launch}/{work.name}"
     else:
         steps_per_launch = 1
         kname = "k_moment_stencil<honeycomb, complex64 x2 per thread>"
@@ -361,7 +364,7 @@ def run_gpu(args, work):
         "config": {"workload": work.name, "sites": info.n_sites, "states": S, "moments": M, "energies": nE,
                    "form": "concurrent moment-based, cost-halving (M/2 matrix applications)",
                    "precision": "complex64 states, FP64 reductions",
-                   "reconstruction": args.recon, "l2": "inputs larger than L2 (2 state blocks of "
+                   "reconstruction": args.recon, "fusion_mode": args.fusion, "l2": "inputs larger than L2 (2 state blocks of "
                    f"{info.n_sites * S * 8 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "reconstruction": recon,
@@ -488,7 +491,7 @@ def run_serving(args):
         "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
         "throughput_site_updates_per_s": total_su / makespan, "makespan_s": makespan,
         "arrival_rate_per_s": rate, "load": args.load, "capacity_site_updates_per_s": cap_su,
-        "kernel_launches": stats["launches"], "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+        "kernel_launches": stats["launches"], "batched_kernel_gpu_s": stats["gpu_us"] / 1e6, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serving stream: {len(stream)} Poisson arrivals, square/honeycomb/cubic, "
                                f"2^12..2^{args.log2_max_sites} sites, W~U[0,2]t, M~U{{256..8192}}, "
                                "S~U{1..16} or LDOS at 32 sites", "reconstruction": args.recon}}))

@@ -147,8 +147,10 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
 /* Temporal fusion of the moment pass (several Chebyshev steps per pass in shared memory, so
  * each state vector crosses HBM twice per pass instead of three times per step), used where a
  * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least one tile wide).
- * On by default; 0 forces one step per pass.  Results agree within the complex64 tolerance. */
-int tbpm_set_fusion(tbpm_ctx* ctx, int enable);
+ * mode: 0 = one step per pass (default: on GB300 the one-step pass reaches ~82% of HBM
+ * bandwidth while the shared-memory passes are limited by shared-memory instruction issue);
+ * 1 = 4 steps per pass; 2 = 2 steps per pass.  Results agree within the complex64 tolerance. */
+int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
 /* Phase timing.  tbpm_profile(ctx, 1) clears the record and starts recording CUDA events
  * on the context stream around every recurrence loop of a moment request (kind 0: all its
  * passes), around its fused multi-step passes (kind 2, a sub-interval of kind 0) and around
@@ -250,8 +252,9 @@ int tbpm_submit(tbpm_server* srv, const tbpm_lattice_desc* lat, const tbpm_reque
  * Returns the request's status (TBPM_ETIMEOUT if not finished in time; the ticket stays valid). */
 int tbpm_wait(tbpm_server* srv, uint64_t ticket, int64_t timeout_us, double* D, size_t D_len,
               double* latency_us);
-/* out = {queued, active, completed, kernel launches, bytes reserved, byte budget}. */
-int tbpm_server_stats(tbpm_server* srv, int64_t out[6]);
+/* out = {queued, active, completed, batched kernel launches, bytes reserved, byte budget,
+ * device microseconds spent in the batched launches (summed over launches known complete)}. */
+int tbpm_server_stats(tbpm_server* srv, int64_t out[7]);
 
 /* ---------------------------------------------------------------- allocation-free step */
 

@@ -175,8 +175,9 @@ def tbpm_launch_count(ctx) -> int:
     return int(load().tbpm_launch_count(ctx))
 
 
-def tbpm_set_fusion(ctx, enable: bool):
-    _check(load().tbpm_set_fusion(ctx, int(bool(enable))))
+def tbpm_set_fusion(ctx, mode: int):
+    """0 = one step per pass, 1..3 = fused variants (see include/tbpm.h)."""
+    _check(load().tbpm_set_fusion(ctx, int(mode)))
 
 
 def tbpm_profile(ctx, enable: bool):
@@ -318,9 +319,9 @@ def tbpm_wait(srv, ticket: int, D: np.ndarray, timeout_us: int = -1):
 
 
 def tbpm_server_stats(srv) -> dict:
-    out = (C.c_int64 * 6)()
+    out = (C.c_int64 * 7)()
     _check(load().tbpm_server_stats(srv, out))
-    return dict(zip(("queued", "active", "completed", "launches", "reserved_bytes", "budget_bytes"),
+    return dict(zip(("queued", "active", "completed", "launches", "reserved_bytes", "budget_bytes", "gpu_us"),
                     (int(v) for v in out)))
 
 

@@ -346,6 +346,16 @@ int tbpm_create(tbpm_ctx** out, int device) {
   cudaError_t e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->pinned, 4096);
+  if (e == cudaSuccess) {
+    // keep memory freed by stream-ordered frees in the pool instead of returning it to the
+    // system at every synchronisation (re-mapping it made later allocations expensive)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   if (e != cudaSuccess) {
     set_error("tbpm_create: %s", cudaGetErrorString(e));
     delete ctx;
@@ -397,7 +407,11 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     set_error("tbpm_set_fusion: ctx is NULL");
     return TBPM_EINVAL;
   }
-  ctx->fusion = enable != 0;
+  if (enable < 0 || enable > 2) {
+    set_error("tbpm_set_fusion: mode %d unknown (0..2)", enable);
+    return TBPM_EINVAL;
+  }
+  ctx->fusion = enable;
   return TBPM_OK;
 }
 
@@ -578,6 +592,10 @@ int tbpm_lattice_create(tbpm_ctx* ctx, const tbpm_lattice_desc* desc, tbpm_latti
   }
   if (d.path < TBPM_PATH_AUTO || d.path > TBPM_PATH_CSR) {
     set_error("unknown path %d", d.path);
+    return TBPM_EINVAL;
+  }
+  if (d.kind == TBPM_CUBIC && (double)d.L[1] * (double)d.L[2] >= 2147483648.0) {
+    set_error("cubic lattice: Ly*Lz must be below 2^31");
     return TBPM_EINVAL;
   }
   double nf = (double)d.L[0] * (double)d.L[1] * (d.kind == TBPM_CUBIC ? (double)d.L[2] : 1.0) *
@@ -808,8 +826,8 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
   void* cur = ctx->ws_phi[0].p;
   void* prev = ctx->ws_phi[1].p;
   int64_t n = 0;
-  const int K = fused_steps();
-  const bool fuse = ctx->fusion && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= K;
+  const int K = fused_steps(ctx->fusion);
+  const bool fuse = ctx->fusion > 0 && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= K;
   if (fuse) {
     TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
     TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pl.state_bytes));
@@ -828,7 +846,7 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
     const int ftok = phase_begin(ctx, 2);
     void* pair_out[2] = {ctx->ws_phi2[0].p, ctx->ws_phi2[1].p};
     while (n + K <= M / 2) {
-      TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n));
+      TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n, ctx->fusion));
       void* old_prev = prev;
       void* old_cur = cur;
       prev = pair_out[0];

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <unordered_map>
 
@@ -566,6 +567,30 @@ __global__ void __launch_bounds__(kThreads) k_dot(RecurrenceArgs a, const void* 
   });
 }
 
+// ------------------------------------------------------------------ quasi-eigenstate accumulation
+// qe[k] += w[k] * x for k < nE (complex weights), every unit of a state block: the N_E axpy of
+// the sequential and state-based quasi-eigenstate forms (Tab. I, QE rows).
+template <typename R, int SPT>
+__global__ void __launch_bounds__(kThreads) k_qe_axpy(const void* xv, void* qev, int64_t stride_packs, int64_t n_units,
+                                                      const double* w, int nE) {
+  using PK = Pack<R, SPT>;
+  const PK* X = reinterpret_cast<const PK*>(xv);
+  PK* Q = reinterpret_cast<PK*>(qev);
+  for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.x * kThreads) {
+    const PK x = ld(X + u);
+    for (int k = 0; k < nE; ++k) {
+      const R wr = (R)__ldg(w + 2 * k), wi = (R)__ldg(w + 2 * k + 1);
+      PK q = ld_stream(Q + k * stride_packs + u);
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        q.v[2 * s] += wr * x.v[2 * s] - wi * x.v[2 * s + 1];
+        q.v[2 * s + 1] += wr * x.v[2 * s + 1] + wi * x.v[2 * s];
+      }
+      st_stream(Q + k * stride_packs + u, q);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename R, int SPT>
 static void* moment_kernel(int kind, bool csr, bool first) {
@@ -674,6 +699,21 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode
   return launch(ctx, fn, gg.r.nblocks, args);
 }
 
+int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe, const double* w,
+                   int nE) {
+  const int spt = spt_of(precision, a.S);
+  const int64_t n_units = a.n_sites * a.P;
+  const int grid = (int)std::min<int64_t>((n_units + kThreads - 1) / kThreads, (int64_t)ctx->num_sms * 8);
+  void* fn;
+  if (precision == TBPM_C128) fn = (void*)k_qe_axpy<double, 1>;
+  else if (spt == 2) fn = (void*)k_qe_axpy<float, 2>;
+  else fn = (void*)k_qe_axpy<float, 1>;
+  int64_t stride = n_units;
+  int64_t nu = n_units;
+  void* args[] = {(void*)&x, &qe, &stride, &nu, (void*)&w, &nE};
+  return launch(ctx, fn, grid, args);
+}
+
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out, int out_stride) {
   const int spt = spt_of(precision, a.S);
@@ -755,8 +795,8 @@ extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int3
   g.Lx = L[0];
   g.Ly = L[1];
   g.Lz = kind == TBPM_CUBIC ? L[2] : 1;
-  if (g.Lx < 1 || g.Ly < 1 || g.Lz < 1) {
-    set_error("tbpm_moment_step_noalloc: lattice sizes must be >= 1");
+  if (g.Lx < 1 || g.Ly < 1 || g.Lz < 1 || (double)g.Ly * (double)g.Lz >= 2147483648.0) {
+    set_error("tbpm_moment_step_noalloc: lattice sizes must be >= 1 with Ly*Lz below 2^31");
     return TBPM_EINVAL;
   }
   g.pbc_x = pbc[0] != 0;

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "tbpm_internal.cuh"
 
 namespace tbpm {
@@ -276,6 +278,71 @@ __global__ void __launch_bounds__(256) k_dos_fourier(const double* C, int S, int
 int launch_dos_fourier(tbpm_ctx* ctx, const double* C, int S, int n_steps, const double* energies,
                        int64_t nE, double tau_phys, int window, double* D) {
   k_dos_fourier<<<(unsigned)nE, 256, 0, ctx->stream>>>(C, S, n_steps, energies, nE, tau_phys, window, D);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
+// ------------------------------------------------------------------ quasi-eigenstate coefficients
+// Energy-based form of Sec. IV (Eqs. form2_concurrent, QE_coeff with a(E,t) = e^{iEt}/2pi):
+//   C_0(E) = (tau/2pi) sum_j w_j 2 J_0(j tau~) cos(eps t_j),
+//   C_n(E) = (tau/2pi) sum_j w_j 4 J_n(j tau~) Re[(-i)^n e^{i eps t_j}],  n >= 1,
+// eps = E - H0, w_j = (2 - delta_j0)/2.  phase[k][j] = (cos, sin)(eps_k t_j).
+__global__ void k_qe_phase(const double* energies, int nE, double H0, double tphys, int n_steps, double* phase) {
+  const int64_t total = (int64_t)nE * (n_steps + 1);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / (n_steps + 1));
+    const int j = (int)(e - (int64_t)k * (n_steps + 1));
+    double sn, cs;
+    sincos((energies[k] - H0) * (double)j * tphys, &sn, &cs);
+    phase[2 * e] = cs;
+    phase[2 * e + 1] = sn;
+  }
+}
+
+// One block per (n, group of 8 energies); threads over j.  coef[(n*nE + k)*2] = C_n(E_k), imag 0.
+__global__ void __launch_bounds__(256) k_qe_coeffs(const double* table, int n_steps, const double* phase, int nE,
+                                                   double scale, double* coef) {
+  __shared__ double sh[8];
+  const int n = blockIdx.x;
+  const int k0 = blockIdx.y * 8;
+  const int64_t width = n_steps + 1;
+  double acc[8];
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+  for (int j = threadIdx.x; j <= n_steps; j += blockDim.x) {
+    const double Jn = table[(int64_t)n * width + j];
+    const double w = j == 0 ? 0.5 : 1.0;
+    for (int q = 0; q < 8 && k0 + q < nE; ++q) {
+      const double* ph = phase + ((int64_t)(k0 + q) * width + j) * 2;
+      double f;
+      if (n == 0) f = 2.0 * ph[0];
+      else {
+        switch (n & 3) {  // 4 Re[(-i)^n (cos + i sin)]
+          case 0: f = 4.0 * ph[0]; break;
+          case 1: f = 4.0 * ph[1]; break;
+          case 2: f = -4.0 * ph[0]; break;
+          default: f = -4.0 * ph[1]; break;
+        }
+      }
+      acc[q] += w * Jn * f;
+    }
+  }
+  for (int q = 0; q < 8 && k0 + q < nE; ++q) {
+    const double tot = block_sum<256>(acc[q], sh);
+    if (threadIdx.x == 0) {
+      coef[((int64_t)n * nE + k0 + q) * 2] = scale * tot;
+      coef[((int64_t)n * nE + k0 + q) * 2 + 1] = 0.0;
+    }
+  }
+}
+
+int launch_qe_coefficients(tbpm_ctx* ctx, const double* table, int n_steps, int n_terms, const double* energies,
+                           int nE, double H0, double tphys, double* phase, double* coef) {
+  const int64_t tot = (int64_t)nE * (n_steps + 1);
+  k_qe_phase<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, ctx->stream>>>(energies, nE, H0, tphys,
+                                                                                      n_steps, phase);
+  TBPM_CK_LAUNCH(ctx);
+  k_qe_coeffs<<<dim3(n_terms, (nE + 7) / 8), 256, 0, ctx->stream>>>(table, n_steps, phase, nE,
+                                                                     tphys / (2.0 * M_PI), coef);
   TBPM_CK_LAUNCH(ctx);
   return TBPM_OK;
 }

@@ -111,8 +111,10 @@ __device__ __forceinline__ void serve_unit(const ServeItem& it, const Pack<R, SP
 }
 
 // One tile of one request; the last tile of the request finishes its step.
+// `it` is the block's shared-memory copy; `git` the item in global memory, whose step field the
+// last tile advances for the next launch.
 template <int KIND, bool CSR, typename R, int SPT>
-__device__ void serve_tile(ServeItem* itp, int64_t lt, double (*red)[32][6], unsigned& ticket) {
+__device__ void serve_tile(const ServeItem* itp, ServeItem* git, int64_t lt, double (*red)[32][6], unsigned& ticket) {
   using PK = Pack<R, SPT>;
   const ServeItem& it = *itp;
   const int step = it.step;
@@ -210,23 +212,27 @@ __device__ void serve_tile(ServeItem* itp, int64_t lt, double (*red)[32][6], uns
     __syncthreads();
     if (threadIdx.x == 0) {
       *it.counter = 0u;
-      itp->step = step + 1;
+      git->step = step + 1;
     }
   }
   __syncthreads();
 }
 
 template <int KIND, bool CSR>
-__device__ __forceinline__ void serve_dispatch_prec(ServeItem* it, int64_t lt, double (*red)[32][6],
-                                                    unsigned& ticket) {
-  if (it->precision == TBPM_C128) serve_tile<KIND, CSR, double, 1>(it, lt, red, ticket);
-  else if (it->spt == 2) serve_tile<KIND, CSR, float, 2>(it, lt, red, ticket);
-  else serve_tile<KIND, CSR, float, 1>(it, lt, red, ticket);
+__device__ __forceinline__ void serve_dispatch_prec(const ServeItem* it, ServeItem* git, int64_t lt,
+                                                    double (*red)[32][6], unsigned& ticket) {
+  if (it->precision == TBPM_C128) serve_tile<KIND, CSR, double, 1>(it, git, lt, red, ticket);
+  else if (it->spt == 2) serve_tile<KIND, CSR, float, 2>(it, git, lt, red, ticket);
+  else serve_tile<KIND, CSR, float, 1>(it, git, lt, red, ticket);
 }
 
 __global__ void __launch_bounds__(kThreads) k_serve_step(ServeItem* items, int n_items, int64_t total_tiles) {
   __shared__ double red[kWarps][32][6];
   __shared__ unsigned ticket;
+  __shared__ ServeItem sit;  // the tile's work item, staged once per tile
+  __shared__ int sit_index;
+  if (threadIdx.x == 0) sit_index = -1;
+  __syncthreads();
   for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
     int lo = 0, hi = n_items - 1;
     while (lo < hi) {  // last item with tile_begin <= t
@@ -234,12 +240,20 @@ __global__ void __launch_bounds__(kThreads) k_serve_step(ServeItem* items, int n
       if (items[mid].tile_begin <= t) lo = mid;
       else hi = mid - 1;
     }
-    ServeItem* it = items + lo;
-    const int64_t lt = t - it->tile_begin;
-    if (it->path == TBPM_PATH_CSR) serve_dispatch_prec<0, true>(it, lt, red, ticket);
-    else if (it->geom.kind == TBPM_HONEYCOMB) serve_dispatch_prec<TBPM_HONEYCOMB, false>(it, lt, red, ticket);
-    else if (it->geom.kind == TBPM_SQUARE) serve_dispatch_prec<TBPM_SQUARE, false>(it, lt, red, ticket);
-    else serve_dispatch_prec<TBPM_CUBIC, false>(it, lt, red, ticket);
+    if (lo != sit_index) {
+      __syncthreads();
+      constexpr int W = sizeof(ServeItem) / sizeof(int);
+      static_assert(sizeof(ServeItem) % sizeof(int) == 0, "item size");
+      for (int w = threadIdx.x; w < W; w += blockDim.x)
+        reinterpret_cast<int*>(&sit)[w] = reinterpret_cast<const int*>(items + lo)[w];
+      if (threadIdx.x == 0) sit_index = lo;
+      __syncthreads();
+    }
+    const int64_t lt = t - sit.tile_begin;
+    if (sit.path == TBPM_PATH_CSR) serve_dispatch_prec<0, true>(&sit, items + lo, lt, red, ticket);
+    else if (sit.geom.kind == TBPM_HONEYCOMB) serve_dispatch_prec<TBPM_HONEYCOMB, false>(&sit, items + lo, lt, red, ticket);
+    else if (sit.geom.kind == TBPM_SQUARE) serve_dispatch_prec<TBPM_SQUARE, false>(&sit, items + lo, lt, red, ticket);
+    else serve_dispatch_prec<TBPM_CUBIC, false>(&sit, items + lo, lt, red, ticket);
   }
 }
 
@@ -306,9 +320,12 @@ struct tbpm_server {
   ServeItem* h_items[2] = {nullptr, nullptr};
   cudaEvent_t items_ev[2] = {nullptr, nullptr};
   int items_cap = 0, items_slot = 0;
-  std::vector<cudaEvent_t> inflight;
+  std::vector<cudaEvent_t> inflight;      // end of each in-flight launch (timed)
+  std::vector<cudaEvent_t> inflight_beg;  // start of each in-flight launch
+  std::vector<char> inflight_live;
   size_t inflight_head = 0;
   int64_t launches = 0, completed = 0;
+  double gpu_ms = 0.0;  // summed device time of the batched launches
 };
 
 static size_t job_footprint(const ServeJob* j, int64_t n_sites, int64_t n_full, int z) {
@@ -536,20 +553,28 @@ static void scheduler(tbpm_server* srv) {
       int64_t total = 0;
       for (ServeJob* j : srv->active) total += j->n_tiles;
       // bound the queue depth so completion times and admission follow the device
-      if (srv->inflight.size() >= depth) {
-        cudaEventSynchronize(srv->inflight[srv->inflight_head]);
+      const size_t h = srv->inflight_head;
+      if (srv->inflight.size() < depth) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        srv->inflight_beg.push_back(e0);
+        srv->inflight.push_back(e1);
+        srv->inflight_live.push_back(0);
+      } else if (srv->inflight_live[h]) {
+        cudaEventSynchronize(srv->inflight[h]);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, srv->inflight_beg[h], srv->inflight[h]) == cudaSuccess) srv->gpu_ms += ms;
+        srv->inflight_live[h] = 0;
       }
       const int grid = (int)std::min<int64_t>(total, (int64_t)srv->ctx->num_sms * 4);
+      cudaEventRecord(srv->inflight_beg[h], srv->ctx->stream);
       k_serve_step<<<grid, kThreads, 0, srv->ctx->stream>>>(srv->d_items, (int)srv->active.size(), total);
+      cudaEventRecord(srv->inflight[h], srv->ctx->stream);
+      srv->inflight_live[h] = 1;
       srv->ctx->launches++;
       srv->launches++;
-      if (srv->inflight.size() < depth) {
-        cudaEvent_t e;
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-        srv->inflight.push_back(e);
-      }
-      cudaEventRecord(srv->inflight[srv->inflight_head], srv->ctx->stream);
-      srv->inflight_head = (srv->inflight_head + 1) % depth;
+      srv->inflight_head = (h + 1) % depth;
       std::vector<ServeJob*> still;
       for (ServeJob* j : srv->active) {
         j->steps_done++;
@@ -666,6 +691,7 @@ int tbpm_server_destroy(tbpm_server* srv) {
     if (srv->items_ev[k]) cudaEventDestroy(srv->items_ev[k]);
   }
   for (cudaEvent_t e : srv->inflight) cudaEventDestroy(e);
+  for (cudaEvent_t e : srv->inflight_beg) cudaEventDestroy(e);
   if (srv->d_items) cudaFreeAsync(srv->d_items, srv->ctx->stream);
   tbpm_destroy(srv->builder);
   tbpm_destroy(srv->ctx);
@@ -783,7 +809,7 @@ int tbpm_wait(tbpm_server* srv, uint64_t ticket, int64_t timeout_us, double* D, 
   return result;
 }
 
-int tbpm_server_stats(tbpm_server* srv, int64_t out[6]) {
+int tbpm_server_stats(tbpm_server* srv, int64_t out[7]) {
   clear_error();
   if (!srv || !out) {
     set_error("tbpm_server_stats: NULL argument");
@@ -796,6 +822,7 @@ int tbpm_server_stats(tbpm_server* srv, int64_t out[6]) {
   out[3] = srv->launches;
   out[4] = (int64_t)srv->used;
   out[5] = (int64_t)srv->budget;
+  out[6] = (int64_t)(srv->gpu_ms * 1000.0);
   return TBPM_OK;
 }
 

@@ -200,8 +200,11 @@ __device__ __forceinline__ LineBases line_bases(const Geom& g, int64_t row, int6
   LineBases b;
   int64_t y = row, zc = 0;
   if constexpr (KIND == TBPM_CUBIC) {
-    y = row % g.Ly;
-    zc = row / g.Ly;
+    // rows = Ly*Lz < 2^31 on any lattice that fits the device: 32-bit division
+    const uint32_t r32 = (uint32_t)row, ly = (uint32_t)g.Ly;
+    const uint32_t z32 = r32 / ly;
+    zc = z32;
+    y = r32 - z32 * ly;
   }
   b.own = row * upr;
   int64_t r;

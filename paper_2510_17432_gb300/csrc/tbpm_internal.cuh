@@ -152,8 +152,8 @@ struct tbpm_ctx {
   int64_t launches = 0;
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
-      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials;
-  bool fusion = true;  // temporal fusion of the moment pass where a fused kernel applies
+      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef;
+  int fusion = 0;  // temporal-fusion mode of the moment pass (0 = one step per pass, the default)
   double* pinned = nullptr;
   size_t pinned_cap = 0;
   // phase timing with CUDA events on the context stream (tbpm_profile)
@@ -252,12 +252,16 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
+int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe, const double* w,
+                   int nE);
+int launch_qe_coefficients(tbpm_ctx* ctx, const double* table, int n_steps, int n_terms, const double* energies,
+                           int nE, double H0, double tphys, double* phase, double* coef);
 
 // temporal fusion (csrc/fused.cu)
 bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad);
-int fused_steps();
+int fused_steps(int variant);
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
-                      const void* cur_in, void* prev_out, void* cur_out, int step0);
+                      const void* cur_in, void* prev_out, void* cur_out, int step0, int variant);
 
 enum { ACC_FIRST = 0, ACC_REGULAR = 1, ACC_NOSPMV = 2 };
 

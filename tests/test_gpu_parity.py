@@ -303,7 +303,8 @@ def test_full_size_graphene_sampled(capi, ctx):
 # ---------------------------------------------------------------- temporal fusion (4 steps per pass)
 
 FUSED_CASES = [
-    ("honey48x36_exact_tile", dict(kind=1, L=(48, 36), t=-2.7, W=0.0), 2, 64),
+    ("honey48x32_exact_tile", dict(kind=1, L=(48, 32), t=-2.7, W=0.0), 2, 64),
+    ("honey88x56_two_tiles", dict(kind=1, L=(88, 56), t=-2.7, W=0.0), 2, 66),
     ("honey101x77_ragged_W1", dict(kind=1, L=(101, 77), t=-2.7, W=1.0), 8, 202),
     ("honey90x70_open_x", dict(kind=1, L=(90, 70), t=-2.7, W=0.5, pbc=(0, 1, 1)), 4, 130),
     ("honey60x100_open_y", dict(kind=1, L=(60, 100), t=1.0, W=2.0, pbc=(1, 0, 1)), 16, 96),
@@ -311,14 +312,15 @@ FUSED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name,spec,S,M", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
-def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M):
+def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode):
     lat, ol = make(capi, ctx, **spec)
-    capi.tbpm_set_fusion(ctx, True)
+    capi.tbpm_set_fusion(ctx, mode)
     mf = gpu_moments(capi, ctx, lat, S, M, 0)
-    capi.tbpm_set_fusion(ctx, False)
+    capi.tbpm_set_fusion(ctx, 0)
     mu = gpu_moments(capi, ctx, lat, S, M, 0)
-    capi.tbpm_set_fusion(ctx, True)
+    capi.tbpm_set_fusion(ctx, 1)
     assert np.max(np.abs(mf - mu)) <= 1e-6
     psi = oprop.random_phase_states(ol, 3, S)
     for s in (0, S - 1):
