@@ -61,8 +61,8 @@ enum { TBPM_PATH_AUTO = 0, TBPM_PATH_STENCIL = 1, TBPM_PATH_CSR = 2 };
 enum { TBPM_C64 = 0, TBPM_C128 = 1 };
 /* initial states: random phases (Sec. II.A) or site states |r> (LDOS, Sec. III) */
 enum { TBPM_STATES_RANDOM = 0, TBPM_STATES_SITES = 1 };
-/* propagation form (Sec. II.A): sequential, moment-based concurrent, state-based concurrent */
-enum { TBPM_SEQUENTIAL = 0, TBPM_CONCURRENT_M = 1, TBPM_CONCURRENT_S = 2 };
+/* propagation form (Sec. II.A): sequential, moment-based, state-based, energy-based concurrent */
+enum { TBPM_SEQUENTIAL = 0, TBPM_CONCURRENT_M = 1, TBPM_CONCURRENT_S = 2, TBPM_CONCURRENT_E = 3 };
 /* DOS reconstruction: Jackson-damped Chebyshev series, or windowed Fourier transform of C(t) */
 enum { TBPM_DOS_JACKSON = 0, TBPM_DOS_FOURIER = 1 };
 enum { TBPM_WINDOW_NONE = 0, TBPM_WINDOW_HANN = 1 };
@@ -288,6 +288,41 @@ int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int32_t pbc[3],
                              double diag_const, const void* d_diag, int precision, int n_states,
                              const void* d_cur, void* d_prev_out, double* d_mu, int64_t n_moments,
                              int64_t step, void* stream);
+
+/* Quasi-eigenstates (Sec. IV, Eq. QE): |Psi(E)> = (1/2pi) int e^{iEt}|psi(t)> dt, sampled at
+ * t_j = j tau~/|H|, j = -N_t..N_t, for every state and energy, by the request's form:
+ *   SEQUENTIAL    forward and backward step-by-step propagation (Eq. form1_sequential),
+ *   CONCURRENT_S  the same states from time blocks of b steps (Eq. TE; b = 0: autotuned),
+ *   CONCURRENT_E  one recurrence, |Psi(E)> = sum_n C_n(E) T_n(H~)|psi> (Eqs. form2_concurrent,
+ *                 QE_coeff; C_n carries the 1/2pi of Eq. QE and exp(+-i H0 t)).
+ * out = host [n_energies][S][n_sites] complex (FP32 pairs for C64, FP64 for C128).
+ * Device memory: n_energies accumulating state blocks. */
+int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
+                           const double* energies, int64_t n_energies, void* out);
+
+/* DC (electronic) conductivity (Sec. V, Eqs. DC, dc_corr, dc_mom) along `direction`
+ * (0 = x, 1 = y, 2 = z for the cubic lattice), hbar = e = 1:
+ *   J_a = i[H, P_a], (J_a)_ij = -i t (r_j - r_i)_a on every bond (nearest image across periodic
+ *     boundaries).  Bond vectors: unit square / cubic lattices; graphene with C-C distance 1,
+ *     A -> B bonds (1,0), (-1/2,-sqrt3/2), (-1/2,sqrt3/2) in the neighbour order of
+ *     tbpm_lattice_export, B -> A their negatives.
+ *   C(t_j, E) = <psi| J e^{iHt_j} J |Psi(E)> / |<psi|Psi(E)>|, t_j = j tau~/|H|, j = 0..N_t, with
+ *     |Psi(E)> the quasi-eigenstates of tbpm_quasi_eigenstates (energy-based form for
+ *     n_energies <= 200, state-based otherwise), by the request's form:
+ *       SEQUENTIAL    e^{-iHt} J|psi> step by step, one inner product per step and energy,
+ *       CONCURRENT_S  the same states from time blocks of b steps (b = 0: autotuned); each
+ *                     block's b states meet all energies in one pass,
+ *       CONCURRENT_M  moments m_n(E) = <J psi|T_n(H~)|J Psi(E)>, n < N(N_t tau~), then
+ *                     C = e^{i H0 t} sum_n c_n^*(t~) m_n / |<psi|Psi(E)>|.
+ *   sigma(E) = D(E)/A int_0^{N_t tau} Re[e^{-iEt} C(t,E)] dt, trapezoid weights on t_j,
+ *     D(E) = N Re<psi|Psi(E)>, A = N x area per site (1; 3 sqrt3/4 for graphene).
+ * C (optional, may be NULL) = host [S][n_energies][N_t+1][2]; sigma = host [S][n_energies].
+ * A state whose <psi|Psi(E)> is exactly 0 gets C = 0 and sigma = 0 at that energy.
+ * Errors: TBPM_EINVAL for a direction outside the lattice's dimensions, another form,
+ * n_steps outside [1, 2^20], n_energies outside [1, 4096] or n_energies x S > 65536.
+ * Device memory: n_energies + 4 state blocks (+ b for CONCURRENT_S). */
+int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int direction,
+                      const double* energies, int64_t n_energies, double* C, double* sigma);
 
 /* ---------------------------------------------------------------- cost model */
 

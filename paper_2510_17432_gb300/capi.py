@@ -18,7 +18,7 @@ SQUARE, HONEYCOMB, CUBIC = 0, 1, 2
 PATH_AUTO, PATH_STENCIL, PATH_CSR = 0, 1, 2
 C64, C128 = 0, 1
 STATES_RANDOM, STATES_SITES = 0, 1
-SEQUENTIAL, CONCURRENT_M, CONCURRENT_S = 0, 1, 2
+SEQUENTIAL, CONCURRENT_M, CONCURRENT_S, CONCURRENT_E = 0, 1, 2, 3
 DOS_JACKSON, DOS_FOURIER = 0, 1
 WINDOW_NONE, WINDOW_HANN = 0, 1
 RECON_FP64, RECON_TENSOR = 0, 1
@@ -102,6 +102,8 @@ def load():
                                   C.POINTER(C.c_uint64)]),
         "tbpm_wait": (C.c_int, [_P, C.c_uint64, C.c_int64, _P, C.c_size_t, C.POINTER(C.c_double)]),
         "tbpm_server_stats": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+        "tbpm_quasi_eigenstates": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
+        "tbpm_conductivity": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, _P, C.c_int64, _P, _P]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -122,7 +124,7 @@ def exported_symbols():
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
-            "tbpm_dos_device", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
 
@@ -279,6 +281,20 @@ def tbpm_dos(ctx, lat, req: Request, energies: np.ndarray, D: np.ndarray):
 
 def tbpm_dos_device(ctx, lat, req: Request, d_energies, n_energies: int, d_D):
     _check(load().tbpm_dos_device(ctx, lat, C.byref(req), _dev_ptr(d_energies), int(n_energies), _dev_ptr(d_D)))
+
+
+def tbpm_quasi_eigenstates(ctx, lat, req: Request, energies: np.ndarray, out: np.ndarray):
+    """out: [n_energies][S][n_sites] complex64 (C64) or complex128 (C128)."""
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    _check(load().tbpm_quasi_eigenstates(ctx, lat, C.byref(req), _host_ptr(e), int(e.size), _host_ptr(out)))
+
+
+def tbpm_conductivity(ctx, lat, req: Request, direction: int, energies: np.ndarray, C_out: np.ndarray | None,
+                      sigma: np.ndarray):
+    """C_out: [S][n_energies][n_steps+1] complex128 or None; sigma: [S][n_energies] float64."""
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    _check(load().tbpm_conductivity(ctx, lat, C.byref(req), int(direction), _host_ptr(e), int(e.size),
+                                    _host_ptr(C_out), _host_ptr(sigma)))
 
 
 def tbpm_moment_step_noalloc(kind, L, pbc, t_scaled, diag_const, d_diag, precision, n_states, d_cur,

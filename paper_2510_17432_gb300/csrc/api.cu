@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "tbpm_internal.cuh"
@@ -373,7 +374,8 @@ int tbpm_destroy(tbpm_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->ws_phi[0], &ctx->ws_phi[1], &ctx->ws_psi, &ctx->ws_acc, &ctx->ws_partials,
                     &ctx->ws_counter, &ctx->ws_mu, &ctx->ws_table, &ctx->ws_aux, &ctx->ws_out,
                     &ctx->ws_energies, &ctx->ws_recon, &ctx->ws_phi2[0], &ctx->ws_phi2[1],
-                    &ctx->ws_fused_partials};
+                    &ctx->ws_fused_partials, &ctx->ws_qe, &ctx->ws_qe_coef, &ctx->ws_xdot,
+                    &ctx->ws_jpsi, &ctx->ws_ec};
   for (DevBuf* b : bufs) release(ctx, *b);
   cudaStreamSynchronize(ctx->stream);
   for (auto& ph : ctx->phases) {
@@ -961,9 +963,15 @@ int choose_block(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, cons
 }
 
 // State-based propagation in blocks of b steps; b = 1 is the sequential form.
-// d_C [Spad][n_steps+1][2].
+// d_C [Spad][n_steps+1][2].  The hook sees each finished time block: psi(t_{start+1}) ..
+// psi(t_{start+bb}) as bb consecutive state blocks.  init (device, optional) replaces the
+// request's initial states.
+using BlockHook = std::function<int(int64_t /*start*/, int /*bb*/, const void* /*first state block*/)>;
+
 int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t n_steps,
-               int64_t b, double* d_C) {
+               int64_t b, double* d_C, double tau_signed = 0.0, const BlockHook& hook = nullptr,
+               const void* init = nullptr) {
+  const double tau = tau_signed != 0.0 ? tau_signed : pl.tau;
   if (n_steps < 1) {
     set_error("n_steps must be >= 1");
     return TBPM_EINVAL;
@@ -973,7 +981,10 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
   TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
   TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
   TBPM_TRY(ensure(ctx, ctx->ws_acc, pl.state_bytes * (size_t)b));
-  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  if (init)
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_psi.p, init, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  else
+    TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
   TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, ctx->ws_psi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
 
   AccumArgs g;
@@ -986,9 +997,9 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
   const double shift = lat->H0 / lat->half;
   std::vector<double> coef_full, coef_last;
   std::vector<int> nper_full, nper_last;
-  block_coefficients(pl.tau, shift, (int)b, &coef_full, &nper_full);
+  block_coefficients(tau, shift, (int)b, &coef_full, &nper_full);
   const int64_t last_len = n_steps % b;
-  if (last_len) block_coefficients(pl.tau, shift, (int)last_len, &coef_last, &nper_last);
+  if (last_len) block_coefficients(tau, shift, (int)last_len, &coef_last, &nper_last);
   const size_t tab_bytes = (coef_full.size() + coef_last.size()) * sizeof(double);
   TBPM_TRY(ensure(ctx, ctx->ws_table, tab_bytes));
   double* tab_full = (double*)ctx->ws_table.p;
@@ -1033,6 +1044,7 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
         TBPM_TRY(launch_dot(ctx, g.r, pl.precision, ctx->ws_psi.p, accj, d_C + (start + j + 1) * 2, C_len));
       }
     }
+    if (hook) TBPM_TRY(hook(start, bb, ctx->ws_acc.p));
     // the block's last state starts the next block
     const char* last = (const char*)ctx->ws_acc.p + (size_t)(bb - 1) * pl.state_bytes;
     TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, last, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1073,6 +1085,183 @@ int run_correlation(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, c
   }
   set_error("unknown form %d", req->form);
   return TBPM_EINVAL;
+}
+
+// Quasi-eigenstates (Sec. IV) of all Spad states into ws_qe: [nE][n_sites][Spad].
+int run_qe(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, const double* d_E, int nE) {
+  const int64_t n_steps = req->n_steps;
+  if (n_steps < 1 || n_steps > (1 << 22) || nE < 1 || nE > 4096) {
+    set_error("quasi-eigenstates need 1 <= n_steps and 1 <= n_energies <= 4096");
+    return TBPM_EINVAL;
+  }
+  const double tphys = pl.tau / lat->half;
+  TBPM_TRY(ensure(ctx, ctx->ws_qe, pl.state_bytes * (size_t)nE));
+  const size_t phase_bytes = sizeof(double) * 2 * (size_t)nE * (n_steps + 1);
+  if (req->form == TBPM_CONCURRENT_E) {
+    const int64_t need = truncation_order_host(n_steps * pl.tau);
+    const int n_table = (int)need + 8;
+    const size_t tab = sizeof(double) * (size_t)n_table * (n_steps + 1);
+    TBPM_TRY(ensure(ctx, ctx->ws_table, tab + sizeof(int) * (n_steps + 1)));
+    TBPM_TRY(ensure(ctx, ctx->ws_qe_coef, phase_bytes + sizeof(double) * 2 * (size_t)need * nE));
+    double* table = (double*)ctx->ws_table.p;
+    int* nper = (int*)((char*)ctx->ws_table.p + tab);
+    double* phase = (double*)ctx->ws_qe_coef.p;
+    double* coef = phase + 2 * (size_t)nE * (n_steps + 1);
+    TBPM_TRY(launch_bessel_table(ctx, pl.tau, (int)n_steps, n_table, table, nper));
+    TBPM_TRY(launch_qe_coefficients(ctx, table, (int)n_steps, (int)need, d_E, nE, lat->H0, tphys, phase, coef));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+    TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+    AccumArgs g;
+    memset(&g, 0, sizeof(g));
+    TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
+    g.acc = ctx->ws_qe.p;
+    g.acc_stride = lat->n_sites * (int64_t)pl.Spad;
+    g.b = nE;
+    g.j_lo = 0;
+    g.j_done = -1;
+    const int tok = phase_begin(ctx, 0);
+    for (int64_t n = 0; n < need; ++n) {
+      const int mode = (n == need - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
+      g.r.cur = ctx->ws_phi[n & 1].p;
+      g.r.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+      g.coef = coef + (size_t)n * nE * 2;
+      g.first_term = n == 0;
+      TBPM_TRY(launch_accum_step(ctx, g, pl.precision, mode));
+    }
+    phase_end(ctx, tok);
+    return TBPM_OK;
+  }
+  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
+    set_error("quasi-eigenstates: form must be SEQUENTIAL, CONCURRENT_S or CONCURRENT_E");
+    return TBPM_EINVAL;
+  }
+  // explicit states psi(+-t_j), each folded into the N_E accumulators with (tau/2pi) e^{+-i E t_j}
+  TBPM_TRY(ensure(ctx, ctx->ws_qe_coef, phase_bytes));
+  double* phase = (double*)ctx->ws_qe_coef.p;
+  {
+    const int64_t tot = (int64_t)nE * (n_steps + 1);
+    (void)tot;
+    TBPM_TRY(launch_qe_coefficients_phase_only(ctx, d_E, nE, tphys, (int)n_steps, phase));
+  }
+  TBPM_CK(cudaMemsetAsync(ctx->ws_qe.p, 0, pl.state_bytes * (size_t)nE, ctx->stream));
+  RecurrenceArgs ra;
+  TBPM_TRY(base_args(ctx, lat, pl, &ra, 3));
+  const int width = (int)(n_steps + 1);
+  const double scale = tphys / (2.0 * M_PI);
+  int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
+  if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, &b, nullptr, nullptr));
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)(n_steps + 1) * pl.Spad));
+  double* dC = (double*)ctx->ws_out.p;
+  for (int dir = 0; dir < 2; ++dir) {
+    const double sgn = dir == 0 ? 1.0 : -1.0;
+    BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
+      for (int j = 0; j < bb; ++j)
+        TBPM_TRY(launch_qe_axpy(ctx, ra, pl.precision, (const char*)first + (size_t)j * pl.state_bytes,
+                                ctx->ws_qe.p, phase, width, (int)(start + j + 1), sgn, scale, nE));
+      return TBPM_OK;
+    };
+    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, dC, sgn * pl.tau, hook));
+    if (dir == 0)  // j = 0 term, tau a(E,0) psi, once; run_blocks left psi in ws_psi
+      TBPM_TRY(launch_qe_axpy(ctx, ra, pl.precision, ctx->ws_psi.p, ctx->ws_qe.p, phase, width, 0, 1.0, scale, nE));
+  }
+  return TBPM_OK;
+}
+
+// Electronic conductivity (Sec. V) along `direction` for all Spad states and nE energies.
+// Leaves C(t_j, E_k) in ws_out as [Spad][nE][n_steps+1][2] and sigma in ws_ec (after the
+// 2*Spad*nE norms) as [Spad][nE].  Returns the sigma pointer through *d_sigma.
+int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, const double* d_E, int nE,
+           int direction, double** d_C_out, double** d_sigma) {
+  const int64_t n_steps = req->n_steps;
+  const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
+  if (direction < 0 || direction >= dims) {
+    set_error("direction %d out of range for a %d-dimensional lattice", direction, dims);
+    return TBPM_EINVAL;
+  }
+  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S && req->form != TBPM_CONCURRENT_M) {
+    set_error("conductivity: form must be SEQUENTIAL, CONCURRENT_S or CONCURRENT_M");
+    return TBPM_EINVAL;
+  }
+  if (n_steps < 1 || n_steps > (1 << 20) || nE < 1 || nE > 4096 || (int64_t)nE * pl.Spad > 65536) {
+    set_error("conductivity needs 1 <= n_steps <= 2^20, 1 <= n_energies <= 4096 and n_energies * states <= 65536");
+    return TBPM_EINVAL;
+  }
+  // quasi-eigenstates: energy-based form for few energies, state-based otherwise (Sec. IV)
+  tbpm_request qreq = *req;
+  qreq.form = nE <= 200 ? TBPM_CONCURRENT_E : TBPM_CONCURRENT_S;
+  qreq.time_block = 0;
+  TBPM_TRY(run_qe(ctx, lat, &qreq, pl, d_E, nE));
+  const int rows = pl.Spad * nE;
+  const int64_t W = n_steps + 1;
+  TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double) * 3 * (size_t)rows));
+  double* nrm = (double*)ctx->ws_ec.p;
+  double* sigma = nrm + 2 * (size_t)rows;
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_jpsi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  const int64_t n = lat->n_sites;
+  // <psi|Psi(E)> before the kets are overwritten
+  TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_psi.p, 1, ctx->ws_qe.p, nE, nrm, nE, 0, 1, 0));
+  // |psi_2(E)> = J |Psi(E)> in place (through one scratch block), |psi_1> = J |psi>
+  for (int k = 0; k < nE; ++k) {
+    char* qk = (char*)ctx->ws_qe.p + (size_t)k * pl.state_bytes;
+    TBPM_TRY(launch_current(ctx, lat, pl.precision, pl.Spad, direction, qk, ctx->ws_phi[0].p));
+    TBPM_CK(cudaMemcpyAsync(qk, ctx->ws_phi[0].p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  TBPM_TRY(launch_current(ctx, lat, pl.precision, pl.Spad, direction, ctx->ws_psi.p, ctx->ws_jpsi.p));
+  const void* kets = ctx->ws_qe.p;
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)rows * W));
+  double* C = (double*)ctx->ws_out.p;
+  const int tok = phase_begin(ctx, 0);
+  if (req->form == TBPM_CONCURRENT_M) {
+    // m_n(E) = <J psi|T_n(H~)|J Psi(E)> (Eq. dc_mom), n < N(t~_tot)
+    const int64_t Nn = truncation_order_host(n_steps * pl.tau);
+    TBPM_TRY(ensure(ctx, ctx->ws_mu, sizeof(double) * 2 * (size_t)rows * Nn));
+    double* m = (double*)ctx->ws_mu.p;
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, ctx->ws_jpsi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    AccumArgs g;
+    memset(&g, 0, sizeof(g));
+    TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
+    g.b = 0;
+    g.j_done = -1;
+    TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_phi[0].p, 1, kets, nE, m, (int64_t)nE * Nn, 0, Nn, 0));
+    for (int64_t k = 0; k + 1 < Nn; ++k) {
+      g.r.cur = ctx->ws_phi[k & 1].p;
+      g.r.prev_out = ctx->ws_phi[(k + 1) & 1].p;
+      TBPM_TRY(launch_accum_step(ctx, g, pl.precision, k == 0 ? ACC_FIRST : ACC_REGULAR));
+      TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_phi[(k + 1) & 1].p, 1, kets, nE, m,
+                           (int64_t)nE * Nn, 0, Nn, k + 1));
+    }
+    phase_end(ctx, tok);
+    const int n_table = (int)Nn + 8;
+    const size_t tab = sizeof(double) * (size_t)n_table * W;
+    TBPM_TRY(ensure(ctx, ctx->ws_table, tab + sizeof(int) * (size_t)W));
+    double* table = (double*)ctx->ws_table.p;
+    int* nper = (int*)((char*)ctx->ws_table.p + tab);
+    TBPM_TRY(launch_bessel_table(ctx, pl.tau, (int)n_steps, n_table, table, nper));
+    TBPM_TRY(launch_ec_corr_from_moments(ctx, table, nper, (int)n_steps, m, rows, (int)Nn, lat->H0 / lat->half,
+                                         pl.tau, C));
+  } else {
+    // psi_1(t_j) = e^{-iHt_j} J psi in time blocks; each block's b states meet all N_E kets at once
+    int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
+    if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, &b, nullptr, nullptr));
+    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)W * pl.Spad));
+    double* dC = (double*)ctx->ws_recon.p;  // <J psi|psi_1(t)>, unused
+    BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
+      return launch_xdot(ctx, pl.precision, pl.Spad, n, first, bb, kets, nE, C, (int64_t)nE * W, 1, W, start + 1);
+    };
+    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, dC, 0.0, hook, ctx->ws_jpsi.p));
+    TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_jpsi.p, 1, kets, nE, C, (int64_t)nE * W, 0, W, 0));
+    phase_end(ctx, tok);
+  }
+  const double area = lat->desc.kind == TBPM_HONEYCOMB ? 3.0 * sqrt(3.0) / 4.0 : 1.0;
+  TBPM_TRY(launch_ec_finish(ctx, C, nrm, d_E, nE, rows, (int)n_steps, pl.tau / lat->half, area, sigma));
+  *d_C_out = C;
+  *d_sigma = sigma;
+  return TBPM_OK;
 }
 
 int copy_rows(tbpm_ctx* ctx, double* dst, const double* src, int S, size_t row_doubles, cudaMemcpyKind kind) {
@@ -1331,6 +1520,55 @@ int tbpm_block_autotune(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_req
     times_ms[0] = ta;
     times_ms[1] = tx;
   }
+  return TBPM_OK;
+}
+
+int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* energies,
+                           int64_t nE, void* out) {
+  clear_error();
+  if (!ctx || !energies || !out || nE < 1) {
+    set_error("tbpm_quasi_eigenstates: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)nE));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_energies.p, energies, sizeof(double) * nE, cudaMemcpyHostToDevice, ctx->stream));
+  TBPM_TRY(run_qe(ctx, lat, req, pl, (const double*)ctx->ws_energies.p, (int)nE));
+  const int64_t n = lat->n_sites;
+  for (int64_t k = 0; k < nE; ++k)
+    for (int s = 0; s < pl.S; ++s)
+      TBPM_CK(cudaMemcpy2DAsync((char*)out + ((size_t)k * pl.S + s) * n * pl.elem, pl.elem,
+                                (const char*)ctx->ws_qe.p + (size_t)k * pl.state_bytes + s * pl.elem,
+                                pl.Spad * pl.elem, pl.elem, n, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int direction,
+                      const double* energies, int64_t nE, double* C, double* sigma) {
+  clear_error();
+  if (!ctx || !energies || !sigma || nE < 1 || nE > 4096) {
+    set_error("tbpm_conductivity: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)nE));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_energies.p, energies, sizeof(double) * nE, cudaMemcpyHostToDevice, ctx->stream));
+  double *d_C = nullptr, *d_sigma = nullptr;
+  TBPM_TRY(run_ec(ctx, lat, req, pl, (const double*)ctx->ws_energies.p, (int)nE, direction, &d_C, &d_sigma));
+  // rows s*nE + k of the first S states are contiguous
+  const size_t rows = (size_t)pl.S * nE;
+  if (C)
+    TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * rows * (req->n_steps + 1), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  TBPM_CK(cudaMemcpyAsync(sigma, d_sigma, sizeof(double) * rows, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
   return TBPM_OK;
 }
 

@@ -568,18 +568,20 @@ __global__ void __launch_bounds__(kThreads) k_dot(RecurrenceArgs a, const void* 
 }
 
 // ------------------------------------------------------------------ quasi-eigenstate accumulation
-// qe[k] += w[k] * x for k < nE (complex weights), every unit of a state block: the N_E axpy of
-// the sequential and state-based quasi-eigenstate forms (Tab. I, QE rows).
+// qe[k] += w_k x for k < nE with w_k = scale (cos, sgn sin)(theta_kj) from phase[k][j] = (cos, sin):
+// the N_E axpy of the sequential and state-based quasi-eigenstate forms (Tab. I, QE rows).
 template <typename R, int SPT>
 __global__ void __launch_bounds__(kThreads) k_qe_axpy(const void* xv, void* qev, int64_t stride_packs, int64_t n_units,
-                                                      const double* w, int nE) {
+                                                      const double* phase, int width, int j, double sgn, double scale,
+                                                      int nE) {
   using PK = Pack<R, SPT>;
   const PK* X = reinterpret_cast<const PK*>(xv);
   PK* Q = reinterpret_cast<PK*>(qev);
   for (int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.x * kThreads) {
     const PK x = ld(X + u);
     for (int k = 0; k < nE; ++k) {
-      const R wr = (R)__ldg(w + 2 * k), wi = (R)__ldg(w + 2 * k + 1);
+      const double* ph = phase + ((int64_t)k * width + j) * 2;
+      const R wr = (R)(scale * __ldg(ph)), wi = (R)(scale * sgn * __ldg(ph + 1));
       PK q = ld_stream(Q + k * stride_packs + u);
 #pragma unroll
       for (int s = 0; s < SPT; ++s) {
@@ -699,8 +701,8 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode
   return launch(ctx, fn, gg.r.nblocks, args);
 }
 
-int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe, const double* w,
-                   int nE) {
+int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe,
+                   const double* phase, int width, int j, double sgn, double scale, int nE) {
   const int spt = spt_of(precision, a.S);
   const int64_t n_units = a.n_sites * a.P;
   const int grid = (int)std::min<int64_t>((n_units + kThreads - 1) / kThreads, (int64_t)ctx->num_sms * 8);
@@ -710,7 +712,7 @@ int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const 
   else fn = (void*)k_qe_axpy<float, 1>;
   int64_t stride = n_units;
   int64_t nu = n_units;
-  void* args[] = {(void*)&x, &qe, &stride, &nu, (void*)&w, &nE};
+  void* args[] = {(void*)&x, &qe, &stride, &nu, (void*)&phase, &width, &j, &sgn, &scale, &nE};
   return launch(ctx, fn, grid, args);
 }
 

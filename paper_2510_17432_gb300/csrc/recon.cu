@@ -335,6 +335,16 @@ __global__ void __launch_bounds__(256) k_qe_coeffs(const double* table, int n_st
   }
 }
 
+// (cos, sin)(E_k t_j) without the H0 shift: the phases of explicitly propagated states.
+int launch_qe_coefficients_phase_only(tbpm_ctx* ctx, const double* energies, int nE, double tphys, int n_steps,
+                                      double* phase) {
+  const int64_t tot = (int64_t)nE * (n_steps + 1);
+  k_qe_phase<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, ctx->stream>>>(energies, nE, 0.0, tphys,
+                                                                                      n_steps, phase);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
 int launch_qe_coefficients(tbpm_ctx* ctx, const double* table, int n_steps, int n_terms, const double* energies,
                            int nE, double H0, double tphys, double* phase, double* coef) {
   const int64_t tot = (int64_t)nE * (n_steps + 1);

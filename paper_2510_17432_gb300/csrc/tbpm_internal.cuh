@@ -152,7 +152,7 @@ struct tbpm_ctx {
   int64_t launches = 0;
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
-      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef;
+      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec;
   int fusion = 0;  // temporal-fusion mode of the moment pass (0 = one step per pass, the default)
   double* pinned = nullptr;
   size_t pinned_cap = 0;
@@ -252,10 +252,12 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
-int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe, const double* w,
-                   int nE);
+int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe,
+                   const double* phase, int width, int j, double sgn, double scale, int nE);
 int launch_qe_coefficients(tbpm_ctx* ctx, const double* table, int n_steps, int n_terms, const double* energies,
                            int nE, double H0, double tphys, double* phase, double* coef);
+int launch_qe_coefficients_phase_only(tbpm_ctx* ctx, const double* energies, int nE, double tphys, int n_steps,
+                                      double* phase);
 
 // temporal fusion (csrc/fused.cu)
 bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad);
@@ -278,6 +280,16 @@ int launch_dos_jackson_tensor(tbpm_ctx* ctx, const double* mu, int S, int M, con
 // same, without synchronising: the GEMM's bounded-wait status is copied to pinned *h_err
 int launch_dos_jackson_tensor_async(tbpm_ctx* ctx, const double* mu, int S, int M, const double* energies,
                                     int64_t nE, double H0, double half, double* D, int* h_err);
+// electronic conductivity (csrc/conduct.cu)
+void current_weights(int kind, int direction, double t, double kw[2][6]);
+int launch_current(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int S, int direction, const void* x,
+                   void* y);
+int launch_xdot(tbpm_ctx* ctx, int precision, int S, int64_t n_sites, const void* A, int nA, const void* B, int nB,
+                double* out, int64_t os, int64_t oa, int64_t ob, int64_t off);
+int launch_ec_corr_from_moments(tbpm_ctx* ctx, const double* table, const int* n_per_step, int n_steps,
+                                const double* m, int rows, int Nn, double shift, double tau, double* C);
+int launch_ec_finish(tbpm_ctx* ctx, double* C, const double* nrm, const double* energies, int nE, int rows,
+                     int n_steps, double tphys, double area, double* sigma);
 // FP64 D_i of a lattice (made on first use), and a request's initial state block
 int lattice_ensure_d64(tbpm_lattice* lat);
 int init_request_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, void* dst);

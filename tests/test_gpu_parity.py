@@ -320,7 +320,6 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
     mf = gpu_moments(capi, ctx, lat, S, M, 0)
     capi.tbpm_set_fusion(ctx, 0)
     mu = gpu_moments(capi, ctx, lat, S, M, 0)
-    capi.tbpm_set_fusion(ctx, 1)
     assert np.max(np.abs(mf - mu)) <= 1e-6
     psi = oprop.random_phase_states(ol, 3, S)
     for s in (0, S - 1):
