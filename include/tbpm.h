@@ -324,6 +324,44 @@ int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_re
 int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int direction,
                       const double* energies, int64_t n_energies, double* C, double* sigma);
 
+/* Fermi-Dirac operator (the operators f(H), f^{1/2}(H) of the OC, DP and CD sections), hbar = k_B = 1:
+ *   f(E) = 1/(1 + e^{(E - mu)/kT}); out = f(H) psi (sqrt_f = 0) or f(H)^{1/2} psi (sqrt_f != 0) for
+ *   the request's states, as the Chebyshev series sum_n a_n T_n(H~) psi with
+ *   a_n = ((2 - delta_n0)/K) sum_k f(H0 + |H| cos th_k) cos(n th_k), th_k = pi (k + 1/2)/K
+ *   (Chebyshev-Gauss quadrature), truncated at 1 + max{n : |a_n| > 1e-14} within
+ *   min(2^14, 12 |H|/kT + 64) orders (kT well below |H|/1300 is therefore not resolved).
+ * out = host [S][n_sites] complex (FP32 pairs for C64, FP64 for C128).
+ * Errors: TBPM_EINVAL for kT <= 0 or a non-finite mu. */
+int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, double mu, double kT,
+                     int sqrt_f, void* out);
+
+/* Optical conductivity (OC section, Eq. oc_corr and the Kubo and Kramers-Kronig relations there):
+ *   C(t_j) = <psi_1(t_j)| J_alpha |psi_2(t_j)>, psi_1(t) = e^{-iHt} f(H) psi,
+ *   psi_2(t) = e^{-iHt} [1 - f(H)] J_beta psi, t_j = j tau~/|H| (tau~ = pi/2 when req->tau = 0),
+ *   j = 0..N_t; both states advance in one state block of 2 x pow2(S) states, by the request's
+ *   form SEQUENTIAL (b = 1) or CONCURRENT_S (time blocks of b = time_block steps, 0 = autotuned).
+ *   Re sigma(w_k) = 2 (e^{-w_k/kT} - 1)/(w_k a) tau sum_j w_j sin(w_k t_j) Im C(t_j), w_k = k w_max/(n_omega-1),
+ *   w_j = window_j (2 - delta_j0)/2, a = area per site (1; 3 sqrt3/4 for graphene; the sample's
+ *   trace N C over its area N a); Re sigma(0) = 0 (no Drude term).
+ *   Im sigma(w_k) = -(2 w_k/pi) sum_{j: j-k odd} Re sigma(w_j) c_j/(w_j^2 - w_k^2), c_0 = dw, c_j = 2 dw
+ *   (Kramers-Kronig, principal value by Maclaurin's rule).
+ * C (optional, may be NULL) = host [S][N_t+1][2]; sigma = host [S][n_omega][2] (Re, Im).
+ * Errors: TBPM_EINVAL for S > 16, directions outside the lattice's dimensions, kT <= 0,
+ * another form, n_omega outside [2, 2^20] or w_max <= 0. */
+int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int alpha,
+                              int beta, double mu, double kT, double omega_max, int64_t n_omega, double* C,
+                              double* sigma);
+
+/* Dynamical polarization (DP section): C(t_j, q) = <psi_1(t_j)| rho(q) |psi_2(q, t_j)>,
+ *   rho(q) = sum_i e^{i q.r_i}|i><i|, psi_1 as for the OC, psi_2(q, t) = e^{-iHt} [1 - f(H)] rho(-q) psi;
+ *   Pi(q, w) = -(2/a) tau sum_j w_j e^{i w t_j} Im C(t_j, q) for each caller-given w.
+ *   Site positions r_i: unit square / cubic lattices at (x, y, z); graphene A(x,y) = x a1 + y a2,
+ *   B(x,y) = A(x,y) + (1, 0), a1 = (3/2, sqrt3/2), a2 = (3/2, -sqrt3/2).
+ * q = host [3]; C (optional) = host [S][N_t+1][2]; Pi = host [S][n_omega][2] (Re, Im).
+ * Errors as for tbpm_optical_conductivity (n_omega in [1, 2^20]). */
+int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, const double q[3],
+                      double mu, double kT, const double* omegas, int64_t n_omega, double* C, double* Pi);
+
 /* ---------------------------------------------------------------- cost model */
 
 /* Truncation order N(tau~) = 1 + max{n : |c_n(tau~)| > 1e-14} (Sec. II.A), FP64 host. */

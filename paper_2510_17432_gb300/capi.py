@@ -104,6 +104,11 @@ def load():
         "tbpm_server_stats": (C.c_int, [_P, C.POINTER(C.c_int64)]),
         "tbpm_quasi_eigenstates": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
         "tbpm_conductivity": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, _P, C.c_int64, _P, _P]),
+        "tbpm_fermi_apply": (C.c_int, [_P, _P, C.POINTER(Request), C.c_double, C.c_double, C.c_int, _P]),
+        "tbpm_optical_conductivity": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, C.c_int, C.c_double,
+                                                C.c_double, C.c_double, C.c_int64, _P, _P]),
+        "tbpm_polarization": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_double, C.c_double, _P, C.c_int64,
+                                        _P, _P]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -124,7 +129,8 @@ def exported_symbols():
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
-            "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
+            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
 
@@ -295,6 +301,27 @@ def tbpm_conductivity(ctx, lat, req: Request, direction: int, energies: np.ndarr
     e = np.ascontiguousarray(energies, dtype=np.float64)
     _check(load().tbpm_conductivity(ctx, lat, C.byref(req), int(direction), _host_ptr(e), int(e.size),
                                     _host_ptr(C_out), _host_ptr(sigma)))
+
+
+def tbpm_fermi_apply(ctx, lat, req: Request, mu: float, kT: float, sqrt_f: bool, out: np.ndarray):
+    """out: [S][n_sites] complex64 (C64) or complex128 (C128)."""
+    _check(load().tbpm_fermi_apply(ctx, lat, C.byref(req), float(mu), float(kT), int(bool(sqrt_f)), _host_ptr(out)))
+
+
+def tbpm_optical_conductivity(ctx, lat, req: Request, alpha: int, beta: int, mu: float, kT: float,
+                              omega_max: float, n_omega: int, C_out: np.ndarray | None, sigma: np.ndarray):
+    """C_out: [S][n_steps+1] complex128 or None; sigma: [S][n_omega] complex128 (Re + i Im)."""
+    _check(load().tbpm_optical_conductivity(ctx, lat, C.byref(req), int(alpha), int(beta), float(mu), float(kT),
+                                            float(omega_max), int(n_omega), _host_ptr(C_out), _host_ptr(sigma)))
+
+
+def tbpm_polarization(ctx, lat, req: Request, q, mu: float, kT: float, omegas: np.ndarray,
+                      C_out: np.ndarray | None, Pi: np.ndarray):
+    """q: 3 floats; C_out: [S][n_steps+1] complex128 or None; Pi: [S][n_omega] complex128."""
+    qa = np.ascontiguousarray(np.asarray(q, dtype=np.float64).reshape(3))
+    w = np.ascontiguousarray(omegas, dtype=np.float64)
+    _check(load().tbpm_polarization(ctx, lat, C.byref(req), _host_ptr(qa), float(mu), float(kT), _host_ptr(w),
+                                    int(w.size), _host_ptr(C_out), _host_ptr(Pi)))
 
 
 def tbpm_moment_step_noalloc(kind, L, pbc, t_scaled, diag_const, d_diag, precision, n_states, d_cur,

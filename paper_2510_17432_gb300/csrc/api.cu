@@ -375,7 +375,7 @@ int tbpm_destroy(tbpm_ctx* ctx) {
                     &ctx->ws_counter, &ctx->ws_mu, &ctx->ws_table, &ctx->ws_aux, &ctx->ws_out,
                     &ctx->ws_energies, &ctx->ws_recon, &ctx->ws_phi2[0], &ctx->ws_phi2[1],
                     &ctx->ws_fused_partials, &ctx->ws_qe, &ctx->ws_qe_coef, &ctx->ws_xdot,
-                    &ctx->ws_jpsi, &ctx->ws_ec};
+                    &ctx->ws_jpsi, &ctx->ws_ec, &ctx->ws_fermi};
   for (DevBuf* b : bufs) release(ctx, *b);
   cudaStreamSynchronize(ctx->stream);
   for (auto& ph : ctx->phases) {
@@ -1264,6 +1264,134 @@ int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
   return TBPM_OK;
 }
 
+// Chebyshev coefficients of the Fermi-Dirac function (or its square root) on the lattice's
+// spectral window into ws_fermi; *coef = device complex table [n_terms][2], truncated at
+// 1 + max{n : |a_n| > 1e-14} within n_cap = min(2^14, 12|H|/kT + 64) orders.
+int fermi_series(tbpm_ctx* ctx, const tbpm_lattice* lat, double mu, double kT, int sqrt_f, const double** coef,
+                 int* n_terms) {
+  if (!(kT > 0.0) || !isfinite(kT) || !isfinite(mu)) {
+    set_error("Fermi-Dirac operator needs kT > 0 and a finite mu");
+    return TBPM_EINVAL;
+  }
+  const double want = 12.0 * lat->half / kT + 64.0;
+  const int n_cap = (int)std::min<double>(16384.0, std::max<double>(64.0, ceil(want)));
+  const int K = std::max(2 * n_cap, 1024);
+  TBPM_TRY(ensure(ctx, ctx->ws_fermi, sizeof(double) * ((size_t)K + 2 * (size_t)n_cap)));
+  double* scratch = (double*)ctx->ws_fermi.p;
+  double* table = scratch + K;
+  TBPM_TRY(launch_fermi_coefficients(ctx, mu, kT, lat->H0, lat->half, sqrt_f, n_cap, K, scratch, table));
+  std::vector<double> h(2 * (size_t)n_cap);
+  TBPM_CK(cudaMemcpyAsync(h.data(), table, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  int last = 0;
+  for (int n = n_cap - 1; n >= 0; --n)
+    if (fabs(h[2 * (size_t)n]) > 1e-14) {
+      last = n;
+      break;
+    }
+  *coef = table;
+  *n_terms = last + 1;
+  return TBPM_OK;
+}
+
+// out = sum_{n < n_terms} coef_n T_n(H~) X for one state block of plan pc (X and out distinct
+// from ws_phi).
+int apply_series(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, const void* X, void* out, const double* coef,
+                 int n_terms) {
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pc.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pc.state_bytes));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, X, pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  AccumArgs g;
+  memset(&g, 0, sizeof(g));
+  TBPM_TRY(base_args(ctx, lat, pc, &g.r, 3));
+  g.acc = out;
+  g.acc_stride = lat->n_sites * (int64_t)pc.Spad;
+  g.b = 1;
+  g.j_lo = 0;
+  g.j_done = -1;
+  for (int n = 0; n < n_terms; ++n) {
+    const int mode = (n == n_terms - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
+    g.r.cur = ctx->ws_phi[n & 1].p;
+    g.r.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+    g.coef = coef + 2 * (size_t)n;
+    g.first_term = n == 0;
+    TBPM_TRY(launch_accum_step(ctx, g, pc.precision, mode));
+  }
+  return TBPM_OK;
+}
+
+// Optical conductivity (op 0: X = J_alpha, O = J_beta) or dynamical polarization (op 1:
+// X = rho(q), O = rho(-q)) correlation C(t_j) = <psi_1(t_j)|X|psi_2(t_j)> of all Sh states into
+// ws_out [Sh][n_steps+1][2]; the pair plan's time step is returned in *tphys.
+int run_response(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int op, int alpha,
+                 int beta, const double q[3], double mu, double kT, double** d_C, double* tphys) {
+  const int64_t n_steps = req->n_steps;
+  if (n_steps < 1 || n_steps > (1 << 22)) {
+    set_error("n_steps must lie in [1, 2^22]");
+    return TBPM_EINVAL;
+  }
+  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
+    set_error("optical conductivity and polarization take the SEQUENTIAL or CONCURRENT_S form");
+    return TBPM_EINVAL;
+  }
+  const int Sh = pl.Spad;
+  if (2 * Sh > 32) {
+    set_error("optical conductivity and polarization support at most 16 states per call");
+    return TBPM_EINVAL;
+  }
+  if (op == 0) {
+    const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
+    if (alpha < 0 || alpha >= dims || beta < 0 || beta >= dims) {
+      set_error("directions must lie in [0, %d)", dims);
+      return TBPM_EINVAL;
+    }
+  }
+  tbpm_request rc = *req;
+  rc.n_states = 2 * Sh;
+  rc.states = TBPM_STATES_RANDOM;
+  Plan pc;
+  TBPM_TRY(make_plan(lat, &rc, &pc));
+  pc.tau = req->tau == 0.0 ? M_PI / 2 : req->tau;
+  *tphys = pc.tau / lat->half;
+  const int64_t n = lat->n_sites;
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  const double2* phase = nullptr;
+  if (op == 1) {
+    TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double2) * (size_t)n));
+    phase = (const double2*)ctx->ws_ec.p;
+    TBPM_TRY(launch_density_phases(ctx, lat, q, (double2*)ctx->ws_ec.p));
+  } else {
+    TBPM_TRY(ensure(ctx, ctx->ws_jpsi, pl.state_bytes));
+    TBPM_TRY(launch_current(ctx, lat, pl.precision, Sh, beta, ctx->ws_psi.p, ctx->ws_jpsi.p));
+  }
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pc.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pc.state_bytes));
+  TBPM_TRY(launch_pair_init(ctx, pl.precision, n, Sh, ctx->ws_psi.p, op == 0 ? ctx->ws_jpsi.p : nullptr, phase,
+                            ctx->ws_phi2[0].p));
+  const double* coef = nullptr;
+  int nf = 0;
+  TBPM_TRY(fermi_series(ctx, lat, mu, kT, 0, &coef, &nf));
+  TBPM_TRY(apply_series(ctx, lat, pc, ctx->ws_phi2[0].p, ctx->ws_phi2[1].p, coef, nf));
+  TBPM_TRY(launch_pair_split(ctx, pl.precision, n, Sh, ctx->ws_phi2[0].p, ctx->ws_phi2[1].p));
+  const void* Y0 = ctx->ws_phi2[1].p;
+  const int64_t W = n_steps + 1;
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)W * Sh));
+  double* C = (double*)ctx->ws_out.p;
+  const int tok = phase_begin(ctx, 0);
+  TBPM_TRY(launch_xmy(ctx, lat, pl.precision, Sh, alpha, phase, Y0, 1, pc.state_bytes, C, W, 0));
+  int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
+  if (b <= 0) TBPM_TRY(choose_block(ctx, lat, &rc, pc, n_steps, &b, nullptr, nullptr));
+  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)W * pc.Spad));
+  BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
+    return launch_xmy(ctx, lat, pl.precision, Sh, alpha, phase, first, bb, pc.state_bytes, C, W, start + 1);
+  };
+  TBPM_TRY(run_blocks(ctx, lat, &rc, pc, n_steps, b, (double*)ctx->ws_recon.p, 0.0, hook, Y0));
+  phase_end(ctx, tok);
+  *d_C = C;
+  return TBPM_OK;
+}
+
 int copy_rows(tbpm_ctx* ctx, double* dst, const double* src, int S, size_t row_doubles, cudaMemcpyKind kind) {
   TBPM_CK(cudaMemcpyAsync(dst, src, sizeof(double) * row_doubles * S, kind, ctx->stream));
   return TBPM_OK;
@@ -1568,6 +1696,92 @@ int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
     TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * rows * (req->n_steps + 1), cudaMemcpyDeviceToHost,
                             ctx->stream));
   TBPM_CK(cudaMemcpyAsync(sigma, d_sigma, sizeof(double) * rows, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double mu, double kT,
+                     int sqrt_f, void* out) {
+  clear_error();
+  if (!ctx || !out) {
+    set_error("tbpm_fermi_apply: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  const double* coef = nullptr;
+  int nf = 0;
+  TBPM_TRY(fermi_series(ctx, lat, mu, kT, sqrt_f ? 1 : 0, &coef, &nf));
+  TBPM_TRY(apply_series(ctx, lat, pl, ctx->ws_psi.p, ctx->ws_phi2[0].p, coef, nf));
+  const int64_t n = lat->n_sites;
+  for (int s = 0; s < pl.S; ++s)
+    TBPM_CK(cudaMemcpy2DAsync((char*)out + (size_t)s * n * pl.elem, pl.elem,
+                              (const char*)ctx->ws_phi2[0].p + s * pl.elem, pl.Spad * pl.elem, pl.elem, n,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int alpha,
+                              int beta, double mu, double kT, double omega_max, int64_t n_omega, double* C,
+                              double* sigma) {
+  clear_error();
+  if (!ctx || !sigma || n_omega < 2 || n_omega > (1 << 20) || !(omega_max > 0.0)) {
+    set_error("tbpm_optical_conductivity: invalid argument (n_omega in [2, 2^20], omega_max > 0)");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  double* d_C = nullptr;
+  double tphys = 0.0;
+  const double q0[3] = {0, 0, 0};
+  TBPM_TRY(run_response(ctx, lat, req, pl, 0, alpha, beta, q0, mu, kT, &d_C, &tphys));
+  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pl.S));
+  double* d_sig = (double*)ctx->ws_recon.p;
+  const double area = lat->desc.kind == TBPM_HONEYCOMB ? 3.0 * sqrt(3.0) / 4.0 : 1.0;
+  TBPM_TRY(launch_oc_spectrum(ctx, d_C, pl.S, (int)req->n_steps, omega_max / (double)(n_omega - 1), (int)n_omega,
+                              kT, tphys, area, req->window, d_sig));
+  if (C)
+    TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * (size_t)pl.S * (req->n_steps + 1), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  TBPM_CK(cudaMemcpyAsync(sigma, d_sig, sizeof(double) * 2 * (size_t)pl.S * n_omega, cudaMemcpyDeviceToHost,
+                          ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double q[3], double mu,
+                      double kT, const double* omegas, int64_t n_omega, double* C, double* Pi) {
+  clear_error();
+  if (!ctx || !q || !omegas || !Pi || n_omega < 1 || n_omega > (1 << 20)) {
+    set_error("tbpm_polarization: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  double* d_C = nullptr;
+  double tphys = 0.0;
+  TBPM_TRY(run_response(ctx, lat, req, pl, 1, 0, 0, q, mu, kT, &d_C, &tphys));
+  TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)n_omega));
+  TBPM_CK(cudaMemcpyAsync(ctx->ws_energies.p, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
+  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pl.S));
+  double* d_pi = (double*)ctx->ws_recon.p;
+  const double area = lat->desc.kind == TBPM_HONEYCOMB ? 3.0 * sqrt(3.0) / 4.0 : 1.0;
+  TBPM_TRY(launch_dp_spectrum(ctx, d_C, pl.S, (int)req->n_steps, (const double*)ctx->ws_energies.p, (int)n_omega,
+                              tphys, area, req->window, d_pi));
+  if (C)
+    TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * (size_t)pl.S * (req->n_steps + 1), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+  TBPM_CK(cudaMemcpyAsync(Pi, d_pi, sizeof(double) * 2 * (size_t)pl.S * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
   return TBPM_OK;
 }

@@ -359,8 +359,14 @@ int launch_xdot(tbpm_ctx* ctx, int precision, int S, int64_t n_sites, const void
   else
     r = single ? xdot_launch<float, 1, 1, 8>(ctx, xa, (int)G) : xdot_launch<float, 1, 4, 4>(ctx, xa, (int)G);
   TBPM_TRY(r);
+  return launch_partial_reduce(ctx, xa.partials, (int)G, nA, nB, S, out, os, oa, ob, off);
+}
+
+int launch_partial_reduce(tbpm_ctx* ctx, const double* partials, int G, int nA, int nB, int S, double* out,
+                          int64_t os, int64_t oa, int64_t ob, int64_t off) {
+  const int64_t per = (int64_t)nA * nB * S * 2;
   const int rgrid = (int)std::max<int64_t>(1, std::min<int64_t>((per + 255) / 256, (int64_t)ctx->num_sms * 16));
-  k_xdot_reduce<<<rgrid, 256, 0, ctx->stream>>>(xa.partials, (int)G, nA, nB, S, out, os, oa, ob, off);
+  k_xdot_reduce<<<rgrid, 256, 0, ctx->stream>>>(partials, G, nA, nB, S, out, os, oa, ob, off);
   TBPM_CK_LAUNCH(ctx);
   return TBPM_OK;
 }

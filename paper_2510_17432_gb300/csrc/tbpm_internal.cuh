@@ -152,7 +152,7 @@ struct tbpm_ctx {
   int64_t launches = 0;
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
-      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec;
+      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi;
   int fusion = 0;  // temporal-fusion mode of the moment pass (0 = one step per pass, the default)
   double* pinned = nullptr;
   size_t pinned_cap = 0;
@@ -286,10 +286,25 @@ int launch_current(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int S,
                    void* y);
 int launch_xdot(tbpm_ctx* ctx, int precision, int S, int64_t n_sites, const void* A, int nA, const void* B, int nB,
                 double* out, int64_t os, int64_t oa, int64_t ob, int64_t off);
+int launch_partial_reduce(tbpm_ctx* ctx, const double* partials, int G, int nA, int nB, int S, double* out,
+                          int64_t os, int64_t oa, int64_t ob, int64_t off);
 int launch_ec_corr_from_moments(tbpm_ctx* ctx, const double* table, const int* n_per_step, int n_steps,
                                 const double* m, int rows, int Nn, double shift, double tau, double* C);
 int launch_ec_finish(tbpm_ctx* ctx, double* C, const double* nrm, const double* energies, int nE, int rows,
                      int n_steps, double tphys, double area, double* sigma);
+// Fermi-Dirac filtered responses (csrc/response.cu)
+int launch_fermi_coefficients(tbpm_ctx* ctx, double mu, double kT, double H0, double half, int sqrt_f, int n_cap,
+                              int K, double* scratch, double* coef);
+int launch_density_phases(tbpm_ctx* ctx, const tbpm_lattice* lat, const double q[3], double2* phase);
+int launch_pair_init(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* psi, const void* opsi,
+                     const double2* phase, void* xc);
+int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* xc, void* f);
+int launch_xmy(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int Sh, int alpha, const double2* phase,
+               const void* Y, int bb, size_t pair_bytes, double* C, int64_t os, int64_t off);
+int launch_oc_spectrum(tbpm_ctx* ctx, const double* C, int S, int n_steps, double dw, int n_omega, double kT,
+                       double tphys, double area, int window, double* out);
+int launch_dp_spectrum(tbpm_ctx* ctx, const double* C, int S, int n_steps, const double* omegas, int n_omega,
+                       double tphys, double area, int window, double* out);
 // FP64 D_i of a lattice (made on first use), and a request's initial state block
 int lattice_ensure_d64(tbpm_lattice* lat);
 int init_request_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, void* dst);
