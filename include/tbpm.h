@@ -362,6 +362,19 @@ int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm
 int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, const double q[3],
                       double mu, double kT, const double* omegas, int64_t n_omega, double* C, double* Pi);
 
+/* Charge density (CD section, Eq. rho), read as N times the weighted time average of the integrand
+ * over the sampled window (the integrand of a finite sample does not decay):
+ *   rho_i = N sum_{j=0}^{N_t} w_j |psi(t_j)_i|^2 / sum_j w_j,  psi(t) = e^{-iHt} f^{1/2}(H) psi,
+ *   w_j = (2 - delta_j0)/2, t_j = j tau~/|H|; req->tau = 0 selects tau~ = pi |H| / Delta_occ with
+ *   Delta_occ = min(E_max, mu + 20 kT) - E_min (the integrand's band is 2 Delta_occ wide).
+ *   Forms SEQUENTIAL (b = 1) or CONCURRENT_S (b = time_block, 0 = autotuned); abs2py
+ *   (z_i += |x_i|^2) runs once per time block over all of its states.  N_t = 0 gives the plain
+ *   estimate N |<i|f^{1/2}|psi>|^2.
+ * rho = host [S][n_sites] (FP64).  Errors: TBPM_EINVAL for kT <= 0, mu below the spectrum,
+ * n_steps outside [0, 2^22] or another form. */
+int tbpm_charge_density(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, double mu, double kT,
+                        double* rho);
+
 /* ---------------------------------------------------------------- cost model */
 
 /* Truncation order N(tau~) = 1 + max{n : |c_n(tau~)| > 1e-14} (Sec. II.A), FP64 host. */

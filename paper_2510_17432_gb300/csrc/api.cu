@@ -1786,6 +1786,69 @@ int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
   return TBPM_OK;
 }
 
+int tbpm_charge_density(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double mu, double kT,
+                        double* rho) {
+  clear_error();
+  if (!ctx || !rho) {
+    set_error("tbpm_charge_density: invalid argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  TBPM_CK(cudaSetDevice(ctx->device));
+  const int64_t n_steps = req->n_steps;
+  if (n_steps < 0 || n_steps > (1 << 22)) {
+    set_error("n_steps must lie in [0, 2^22]");
+    return TBPM_EINVAL;
+  }
+  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
+    set_error("charge density takes the SEQUENTIAL or CONCURRENT_S form");
+    return TBPM_EINVAL;
+  }
+  double tau = req->tau;
+  if (tau == 0.0) {
+    const double occ = std::min(lat->E_max, mu + 20.0 * kT) - lat->E_min;
+    if (!(occ > 0.0)) {
+      set_error("charge density: no occupied states below mu");
+      return TBPM_EINVAL;
+    }
+    tau = M_PI * lat->half / occ;
+  }
+  Plan pc = pl;
+  pc.tau = tau;
+  const int64_t n = lat->n_sites;
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  const double* coef = nullptr;
+  int nf = 0;
+  TBPM_TRY(fermi_series(ctx, lat, mu, kT, 1, &coef, &nf));
+  TBPM_TRY(apply_series(ctx, lat, pl, ctx->ws_psi.p, ctx->ws_phi2[0].p, coef, nf));
+  const int64_t elems = n * pl.Spad;
+  TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double) * (size_t)elems));
+  double* z = (double*)ctx->ws_ec.p;
+  TBPM_CK(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)elems, ctx->stream));
+  const int tok = phase_begin(ctx, 0);
+  TBPM_TRY(launch_abs2py(ctx, pl.precision, ctx->ws_phi2[0].p, 1, pl.state_bytes, elems, 0.5, z));
+  if (n_steps >= 1) {
+    int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
+    if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pc, n_steps, &b, nullptr, nullptr));
+    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)(n_steps + 1) * pl.Spad));
+    BlockHook hook = [&](int64_t, int bb, const void* first) -> int {
+      return launch_abs2py(ctx, pl.precision, first, bb, pl.state_bytes, elems, 1.0, z);
+    };
+    TBPM_TRY(run_blocks(ctx, lat, req, pc, n_steps, b, (double*)ctx->ws_recon.p, 0.0, hook, ctx->ws_phi2[0].p));
+  }
+  phase_end(ctx, tok);
+  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * (size_t)n * pl.S));
+  const double wsum = 0.5 + (double)n_steps;
+  TBPM_TRY(launch_cd_finish(ctx, z, n, pl.S, pl.Spad, (double)n / wsum, (double*)ctx->ws_out.p));
+  TBPM_CK(cudaMemcpyAsync(rho, ctx->ws_out.p, sizeof(double) * (size_t)n * pl.S, cudaMemcpyDeviceToHost, ctx->stream));
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
 // ---------------------------------------------------------------- cost model (Sec. II.B, Tab. I)
 int tbpm_block_counts(int64_t n_steps, int64_t b, double tau, int64_t out[3]) {
   clear_error();

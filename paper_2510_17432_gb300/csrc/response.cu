@@ -17,6 +17,8 @@
 //    weight 2 dw; w = 0 weight dw), Pi(w) = -(2/a_site) tau sum_j w_j e^{i w t_j} Im C(t_j);
 //    w_j = window_j (2 - delta_j0)/2.  a_site = area (volume) per site; the sample trace N C(t)
 //    over the sample area N a_site.
+//  * Charge density (CD section, Eq. rho): abs2py z_i += |psi(t_j)_i|^2 over the states of each time
+//    block; rho_i = N sum_j w_j |psi(t_j)_i|^2 / sum_j w_j with psi(t) = e^{-iHt} f^{1/2}(H) psi.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -337,6 +339,31 @@ __global__ void __launch_bounds__(256) k_dp_pi(const double* C, int n_steps, con
   }
 }
 
+// abs2py (CD section): z[e] += scale sum_a |Y_a[e]|^2 over bb state blocks, e < n_elems (FP64 z).
+template <typename R>
+__global__ void k_abs2py(const void* yv, int bb, int64_t stride, int64_t n_elems, double scale, double* z) {
+  using T = typename C2<R>::T;
+  const T* Y = reinterpret_cast<const T*>(yv);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elems; e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int a = 0; a < bb; ++a) {
+      const T v = Y[(int64_t)a * stride + e];
+      acc += (double)(v.x * v.x + v.y * v.y);
+    }
+    z[e] += scale * acc;
+  }
+}
+
+// out[s][i] = factor z[i][s] for the first S of Spad states
+__global__ void k_cd_finish(const double* z, int64_t n, int S, int Spad, double factor, double* out) {
+  const int64_t total = n * S;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n);
+    const int64_t i = e - (int64_t)s * n;
+    out[e] = factor * z[i * Spad + s];
+  }
+}
+
 int grid_of(tbpm_ctx* ctx, int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)ctx->num_sms * 8));
 }
@@ -412,6 +439,24 @@ int launch_xmy(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int Sh, in
   }
   TBPM_CK_LAUNCH(ctx);
   return launch_partial_reduce(ctx, a.partials, (int)G, bb, 1, Sh, C, os, 1, 0, off);
+}
+
+int launch_abs2py(tbpm_ctx* ctx, int precision, const void* Y, int bb, size_t block_bytes, int64_t n_elems,
+                  double scale, double* z) {
+  const int64_t stride = (int64_t)(block_bytes / (precision == TBPM_C128 ? 16 : 8));
+  const int g = grid_of(ctx, n_elems);
+  if (precision == TBPM_C128)
+    k_abs2py<double><<<g, 256, 0, ctx->stream>>>(Y, bb, stride, n_elems, scale, z);
+  else
+    k_abs2py<float><<<g, 256, 0, ctx->stream>>>(Y, bb, stride, n_elems, scale, z);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
+int launch_cd_finish(tbpm_ctx* ctx, const double* z, int64_t n, int S, int Spad, double factor, double* out) {
+  k_cd_finish<<<grid_of(ctx, n * S), 256, 0, ctx->stream>>>(z, n, S, Spad, factor, out);
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
 }
 
 int launch_oc_spectrum(tbpm_ctx* ctx, const double* C, int S, int n_steps, double dw, int n_omega, double kT,

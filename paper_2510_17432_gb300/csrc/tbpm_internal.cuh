@@ -301,6 +301,9 @@ int launch_pair_init(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void
 int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* xc, void* f);
 int launch_xmy(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int Sh, int alpha, const double2* phase,
                const void* Y, int bb, size_t pair_bytes, double* C, int64_t os, int64_t off);
+int launch_abs2py(tbpm_ctx* ctx, int precision, const void* Y, int bb, size_t block_bytes, int64_t n_elems,
+                  double scale, double* z);
+int launch_cd_finish(tbpm_ctx* ctx, const double* z, int64_t n, int S, int Spad, double factor, double* out);
 int launch_oc_spectrum(tbpm_ctx* ctx, const double* C, int S, int n_steps, double dw, int n_omega, double kT,
                        double tphys, double area, int window, double* out);
 int launch_dp_spectrum(tbpm_ctx* ctx, const double* C, int S, int n_steps, const double* omegas, int n_omega,

@@ -167,3 +167,24 @@ def test_response_rejects_invalid_requests(capi, ctx):
         capi.tbpm_polarization(ctx, lat, capi.request(n_states=17, n_steps=4, form=0), (0.1, 0, 0), 0.0, 0.1,
                                np.array([1.0]), big, np.zeros((17, 1), np.complex128))
     capi.tbpm_lattice_destroy(lat)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("form,b,Nt", [(0, 0, 9), (2, 4, 9), (2, 0, 11), (0, 0, 0)])
+@pytest.mark.parametrize("name,spec", LATS, ids=[c[0] for c in LATS])
+def test_charge_density_matches_oracle(capi, ctx, name, spec, form, b, Nt, prec):
+    from oracle import charge as ocd
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(**spec))
+    ol = _oracle_lattice(spec)
+    S = 2
+    mu = ol.H0 - 0.25 * (ol.E_max - ol.E_min) / 2
+    kT = 0.06 * (ol.E_max - ol.E_min) / 2
+    rho = np.zeros((S, ol.n))
+    capi.tbpm_charge_density(ctx, lat, capi.request(n_states=S, precision=prec, form=form, n_steps=Nt,
+                                                    time_block=b, state_seed=11), mu, kT, rho)
+    psi = oprop.random_phase_states(ol, 11, S)
+    tau = ocd.cd_default_tau(ol, mu, kT)
+    for s in range(S):
+        ref = ocd.charge_density_sequential(ol, psi[s], mu, kT, Nt, tau)
+        assert _rel(rho[s], ref) <= TOL[prec], (s, _rel(rho[s], ref))
+    capi.tbpm_lattice_destroy(lat)
