@@ -74,6 +74,21 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(pg, x: float, device=None) -> float:
+    """Max of x over the ranks of the default process group (identity without one)."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling: fixed units per rank)."""
+    return world * units_per_rank / max_seconds
+
+
 # ---------------------------------------------------------------- clocks during the timed region
 class Clocks:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -291,12 +306,9 @@ def run_gpu(args, work):
     capi.tbpm_profile(ctx, False)
     launches = capi.tbpm_launch_count(ctx) - launches0
     clk = clocks.stop()
-    if pg is not None:
-        t = torch.tensor([dev_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = reduce_max(pg, dev_ms, dev)
     ms_per_step = dev_ms / args.steps
-    value = world * site_updates / (ms_per_step / 1e3)
+    value = whole_job_rate(site_updates, world, ms_per_step / 1e3)
 
     # parity of this run's output against the oracle is covered by the tests; sanity here
     D = d_D.cpu().numpy()
@@ -314,11 +326,8 @@ def run_gpu(args, work):
         capi.tbpm_lattice_destroy(lat)
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if pg is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * site_updates / e2e_s, "unit": "site-updates/s",
+    e2e_s = reduce_max(pg, e2e_s, dev)
+    e2e = {"value": whole_job_rate(site_updates, world, e2e_s), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
 
     # ---- roofline of the dominant kernel, from the live events.  Algorithmic bytes: 24 B per

@@ -1,0 +1,59 @@
+"""The multi-process path of bench.py on CPU: two gloo ranks agree on the slowest rank's time and
+on the whole-job rate, and the reference arm runs and prints on rank 0 only."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_path):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    local_seconds = [1.5, 2.25][rank]
+    slowest = bench.reduce_max(dist, local_seconds)
+    rate = bench.whole_job_rate(1000.0, world, slowest)
+    dist.barrier()
+    with open(f"{out_path}.{rank}", "w") as f:
+        json.dump({"slowest": slowest, "rate": rate}, f)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_max_and_aggregate(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    out = str(tmp_path / "r")
+    mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    res = [json.load(open(f"{out}.{r}")) for r in range(2)]
+    for r in res:
+        assert r["slowest"] == 2.25
+        assert r["rate"] == pytest.approx(2 * 1000.0 / 2.25)
+
+
+def test_single_process_helpers_need_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(None, 3.0) == 3.0
+    assert bench.whole_job_rate(10.0, 1, 2.0) == 5.0
+
+
+def test_reference_arm_is_silent_on_other_ranks():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1", MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
