@@ -39,6 +39,11 @@ WORKLOADS = {
                                n_moments=4096, precision=wl.C64, n_steps=0, n_energies=8192),
     "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
                                n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
+    "graphene22528": wl.GRAPHENE_22528,
+    "vacancy4096": wl.GRAPHENE_4096_VAC,
+    "vacancy1024": wl.Workload("honeycomb1024x1024_vac1pct_W2_Nt256", wl.honeycomb(1024, 1024, t=-2.7, W=2.0,
+                                                                                 vacancy_frac=0.01, path=wl.PATH_CSR),
+                               n_states=1, n_moments=0, precision=wl.C64, n_steps=256, n_energies=16),
 }
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", f)
                for f in ("cheb.cu", "fused.cu", "stencil.cuh", "tbpm_internal.cuh")]
@@ -146,8 +151,8 @@ import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import lattice as L, propagate as P
-kind, dims, t, W, seed, seconds, reps = {kind}, {dims}, {t}, {W}, {seed}, {seconds}, {reps}
-lat = L.build_lattice(kind, dims, t=t, W=W, seed=seed)
+kind, dims, t, W, vac, seed, seconds, reps = {kind}, {dims}, {t}, {W}, {vac}, {seed}, {seconds}, {reps}
+lat = L.build_lattice(kind, dims, t=t, W=W, vacancy_frac=vac, seed=seed)
 psi = P.random_phase_states(lat, 1, 1)[0]
 t0 = time.perf_counter(); P.moments(lat, psi, psi, 4); one = (time.perf_counter() - t0) / 4
 k = int(max(4, min(4096, seconds / max(one, 1e-6))))
@@ -159,10 +164,25 @@ print(json.dumps(out))
 """
 
 
+ORACLE_MAX_SITES = 1 << 25  # larger lattices are sampled on a 2^24-site lattice of the same kind
+
+
+def oracle_lattice_dims(spec) -> tuple:
+    """The lattice the oracle is timed on: the workload's own, or a 2^24-site one of the same kind
+    when the workload's would not fit the host (the method is O(N), so the rate carries over)."""
+    if spec.n_full <= ORACLE_MAX_SITES:
+        return tuple(spec.L)
+    if spec.kind == wl.HONEYCOMB:
+        return (2896, 2896, 1)
+    if spec.kind == wl.SQUARE:
+        return (4096, 4096, 1)
+    return (256, 256, 256)
+
+
 def oracle_sample(work: wl.Workload, seconds: float, reps: int = 1):
     spec = work.lattice
-    code = ORACLE_SAMPLE.format(root=ROOT, kind=spec.kind, dims=tuple(spec.L), t=spec.t, W=spec.W, seed=spec.seed,
-                                seconds=seconds, reps=reps)
+    code = ORACLE_SAMPLE.format(root=ROOT, kind=spec.kind, dims=oracle_lattice_dims(spec), t=spec.t, W=spec.W,
+                                vac=spec.vacancy_frac, seed=spec.seed, seconds=seconds, reps=reps)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -173,11 +193,14 @@ def oracle_sample(work: wl.Workload, seconds: float, reps: int = 1):
 def cpu_baseline_obj(work: wl.Workload, samples):
     su = sum(s["site_updates"] for s in samples)
     sec = sum(s["seconds"] for s in samples)
+    dims = oracle_lattice_dims(work.lattice)
+    where = (f"the full {wl.KIND_NAMES[work.lattice.kind]} {dims[0]}x{dims[1]} lattice ({work.lattice.n_full} sites)"
+             if dims == tuple(work.lattice.L) else
+             f"a {wl.KIND_NAMES[work.lattice.kind]} {'x'.join(str(d) for d in dims if d > 1)} lattice of the same "
+             f"parameters (the {work.lattice.n_full}-site lattice does not fit the host; O(N) method)")
     return {"value": su / sec, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 oracle (numpy/scipy CSR matvec), 1 state, {samples[0]['steps']} plain Chebyshev "
-                      f"steps per sample on the full {wl.KIND_NAMES[work.lattice.kind]} "
-                      f"{work.lattice.L[0]}x{work.lattice.L[1]} lattice ({work.lattice.n_full} sites), "
-                      f"{len(samples)} sample(s), {sec:.1f} s"}
+                      f"steps per sample on {where}, {len(samples)} sample(s), {sec:.1f} s"}
 
 
 # ---------------------------------------------------------------- roofline inputs
@@ -369,7 +392,8 @@ def run_gpu(args, work):
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded Philox random-phase states on a clean honeycomb lattice)",
+        "data": "synthetic (seeded Philox random-phase states on a "
+                + ("clean " if spec.W == 0 else f"disordered (W={spec.W}) ") + "honeycomb lattice)",
         "config": {"workload": work.name, "sites": info.n_sites, "states": S, "moments": M, "energies": nE,
                    "form": "concurrent moment-based, cost-halving (M/2 matrix applications)",
                    "precision": "complex64 states, FP64 reductions",
@@ -422,6 +446,173 @@ def run_gpu(args, work):
     elif rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = None
 
+    capi.tbpm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- state-based correlation (vacancy lattices)
+def state_based_schedule(n_steps: int, b: int, tau: float, trunc) -> tuple:
+    """Passes of the time-block form in the library's order: for every block of bb <= b steps,
+    Chebyshev terms n = 0..N_b-1 with the accumulators of times j whose N((j+1) tau) > n open.
+    Returns (matrix applications, [(open accumulators, spmv?, first?) per pass], block count)."""
+    passes, apps, blocks = [], 0, 0
+    start = 0
+    while start < n_steps:
+        bb = min(b, n_steps - start)
+        nper = [trunc((j + 1) * tau) for j in range(bb)]
+        Nb = max(nper)
+        for n in range(Nb):
+            opened = sum(1 for j in range(bb) if nper[j] > n)
+            spmv = n < Nb - 1
+            passes.append((opened, spmv, n == 0))
+            apps += spmv
+        blocks += 1
+        start += bb
+    return apps, passes, blocks
+
+
+def state_based_bytes(passes, blocks, n_sites, S, elem, z, diag_bytes, n_steps, corr=True) -> float:
+    """Algorithmic bytes of the time-block passes: per pass read phi_n, and with a matrix
+    application read phi_{n-1} (not on the first term), write phi_{n+1}, the ELL lists (4z B per
+    site) and D_i; per open accumulator write (first term) or read + write; per time step one read
+    of psi for <psi|psi(t)>; per block the copy of its last state."""
+    st = float(n_sites) * S * elem
+    total = 0.0
+    for opened, spmv, first in passes:
+        total += st
+        if spmv:
+            total += st + (0.0 if first else st) + 4.0 * z * n_sites + diag_bytes * n_sites
+        total += opened * st * (1.0 if first else 2.0)
+    total += blocks * 2.0 * st
+    if corr:
+        total += n_steps * st
+    return total
+
+
+def run_state_based(args, work):
+    import torch
+    from paper_2510_17432_gb300 import capi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    dev = torch.device("cuda", local)
+    ctx = capi.tbpm_create(local)
+    spec = work.lattice
+    desc = capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, vacancy_frac=spec.vacancy_frac,
+                             seed=spec.seed, pbc=spec.pbc, path=spec.path)
+    lat = capi.tbpm_lattice_create(ctx, desc)
+    info = capi.tbpm_lattice_info(lat)
+    N, S, Nt = info.n_sites, work.n_states, work.n_steps
+    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
+    tau = math.pi
+    trunc = capi.tbpm_truncation_order
+    z = wl.COORDINATION[spec.kind]
+
+    def timed_corr(prec, form, b, reps):
+        req = capi.request(n_states=S, precision=prec, form=form, n_steps=Nt, time_block=b, state_seed=1 + rank)
+        d_C = torch.empty((max(S, 1), Nt + 1, 2), device=dev, dtype=torch.float64)
+        for _ in range(args.warmup if reps > 1 else 1):
+            capi.tbpm_correlation_device(ctx, lat, req, d_C)
+        capi.tbpm_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = capi.tbpm_launch_count(ctx)
+        e0.record(stream)
+        for _ in range(reps):
+            capi.tbpm_correlation_device(ctx, lat, req, d_C)
+        e1.record(stream)
+        capi.tbpm_sync(ctx)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps, (capi.tbpm_launch_count(ctx) - l0) // reps, d_C.cpu().numpy()
+
+    out_forms = {}
+    peak, peak_kind = measured_hbm_peak()
+    clocks = Clocks(local)
+    clocks.start()
+    for prec, elem, dbytes in ((capi.C64, 8, 4), (capi.C128, 16, 8)):
+        b_opt, t_a, t_x = capi.tbpm_block_autotune(ctx, lat, capi.request(n_states=S, precision=prec, form=2,
+                                                                            n_steps=Nt, state_seed=1), Nt)
+        res = {}
+        for name, form, b in (("concurrent_s", capi.CONCURRENT_S, b_opt), ("sequential", capi.SEQUENTIAL, 1)):
+            reps = args.steps if (prec == capi.C64 and name == "concurrent_s") else 1
+            sec, launches, C = timed_corr(prec, form, b, reps)
+            apps, passes, blocks = state_based_schedule(Nt, b, tau, trunc)
+            alg = state_based_bytes(passes, blocks, N, S, elem, z, dbytes if spec.W != 0 else 0, Nt)
+            res[name] = {"b": b, "seconds": sec, "matrix_applications": apps, "launches": launches,
+                         "site_updates_per_s": apps * N * S / sec, "algorithmic_gbs": alg / sec / 1e9,
+                         "frac_of_hbm": alg / sec / 1e9 / peak, "C": C}
+        diff = float(np.max(np.abs(res["concurrent_s"]["C"] - res["sequential"]["C"])) /
+                     np.max(np.abs(res["sequential"]["C"])))
+        for r in res.values():
+            r.pop("C")
+        out_forms["c64" if prec == capi.C64 else "c128"] = {
+            "t_amxsy_ms": t_a, "t_axpy_ms": t_x, "b_opt": b_opt, **res,
+            "speedup_wall": res["sequential"]["seconds"] / res["concurrent_s"]["seconds"],
+            "max_rel_correlation_difference": diff}
+    clk = clocks.stop()
+
+    # DC conductivity and quasi-eigenstates at the workload's energies (complex64), all three EC forms
+    ec = {}
+    if work.n_energies and not args.no_sequential:
+        E = wl.uniform_energy_grid(work.n_energies, info.H0 - 0.8 * info.half_width, info.H0 + 0.8 * info.half_width)
+        sig = {}
+        for name, form in (("ec_concurrent_m", capi.CONCURRENT_M), ("ec_concurrent_s", capi.CONCURRENT_S),
+                           ("ec_sequential", capi.SEQUENTIAL)):
+            sg = np.zeros((S, E.size))
+            t0 = time.perf_counter()
+            capi.tbpm_conductivity(ctx, lat, capi.request(n_states=S, precision=capi.C64, form=form, n_steps=Nt,
+                                                          state_seed=1), 0, E, None, sg)
+            ec[name + "_wall_s"] = time.perf_counter() - t0
+            sig[name] = sg
+        ref = sig["ec_sequential"]
+        ec["energies"] = int(E.size)
+        ec["quasi_eigenstates"] = "energy-based form inside every EC call (N_E <= 200)"
+        ec["max_rel_sigma_difference_m_vs_seq"] = float(np.max(np.abs(sig["ec_concurrent_m"] - ref)) /
+                                                        np.max(np.abs(ref)))
+        ec["max_rel_sigma_difference_s_vs_seq"] = float(np.max(np.abs(sig["ec_concurrent_s"] - ref)) /
+                                                        np.max(np.abs(ref)))
+    c64 = out_forms["c64"]
+    value = whole_job_rate(c64["concurrent_s"]["site_updates_per_s"], world, 1.0)
+    roofline = {"bound": "hbm", "achieved": c64["concurrent_s"]["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": c64["concurrent_s"]["frac_of_hbm"], "traffic": None, "peak_source": peak_kind,
+                "kernel": "k_accum_step (ELL, complex64, time-block accumulation)",
+                "bytes_model": "per pass: phi_n, phi_{n-1}, phi_{n+1}, 4z B ELL + D_i per site, 8 or 16 B per "
+                               "open accumulator, psi once per time step, one copy per block"}
+    out = {"metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * c64["concurrent_s"]["seconds"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded Philox random-phase state, vacancies and disorder)",
+           "config": {"workload": work.name, "sites": N, "states": S, "n_steps": Nt, "tau": "pi",
+                      "form": "state-based time blocks (b autotuned from measured pass costs)",
+                      "path": "ELL (vacancies)", "l2": f"inputs larger than L2 ({N * S * 8 / 1e6:.0f} MB per state block)",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "forms": out_forms, "conductivity": ec or None,
+           "e2e": None, "gpu_launches": c64["concurrent_s"]["launches"], "clocks": clk}
+    # end to end through tbpm_correlation (host buffer)
+    Ch = np.zeros((S, Nt + 1), np.complex128)
+    req = capi.request(n_states=S, precision=capi.C64, form=capi.CONCURRENT_S, n_steps=Nt,
+                       time_block=c64["concurrent_s"]["b"], state_seed=1)
+    t0 = time.perf_counter()
+    capi.tbpm_correlation(ctx, lat, req, Ch)
+    e2e_s = reduce_max(pg, time.perf_counter() - t0, dev)
+    out["e2e"] = {"value": whole_job_rate(c64["concurrent_s"]["matrix_applications"] * N * S, world, e2e_s),
+                  "unit": "site-updates/s", "h2d_bytes_per_step": 72, "d2h_bytes_per_step": int(Ch.nbytes)}
+    if rank == 0 and not args.no_cpu and world == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline_obj(work, oracle_sample(work, args.cpu_seconds))
+        except Exception as exc:
+            out["cpu_baseline"] = {"value": None, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"failed: {exc!r}"[:300]}
+    capi.tbpm_lattice_destroy(lat)
     capi.tbpm_destroy(ctx)
     if rank == 0:
         print(json.dumps(out))
@@ -514,6 +705,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, work)
+    elif work.n_moments == 0:
+        run_state_based(args, work)
     else:
         run_gpu(args, work)
 

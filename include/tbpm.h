@@ -151,6 +151,13 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
  * bandwidth while the shared-memory passes are limited by shared-memory instruction issue);
  * 1 = 4 steps per pass; 2 = 2 steps per pass.  Results agree within the complex64 tolerance. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
+/* Memory control of the Fermi-Dirac filtered quantities (tbpm_optical_conductivity,
+ * tbpm_polarization, tbpm_charge_density): their states are processed in passes of at most
+ * max_states states (rounded down to a power of two; 0 = as many as fit in 85% of the free device
+ * memory, at most 16).  A pass holds at most three pair blocks (2 x its states) during the
+ * Fermi-Dirac series and 2 + b during the propagation; results do not depend on the pass width.
+ * No counterpart in the paper (its states fit in host memory). */
+int tbpm_set_pass_states(tbpm_ctx* ctx, int max_states);
 /* Phase timing.  tbpm_profile(ctx, 1) clears the record and starts recording CUDA events
  * on the context stream around every recurrence loop of a moment request (kind 0: all its
  * passes), around its fused multi-step passes (kind 2, a sub-interval of kind 0) and around
@@ -346,8 +353,11 @@ int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request*
  *   Im sigma(w_k) = -(2 w_k/pi) sum_{j: j-k odd} Re sigma(w_j) c_j/(w_j^2 - w_k^2), c_0 = dw, c_j = 2 dw
  *   (Kramers-Kronig, principal value by Maclaurin's rule).
  * C (optional, may be NULL) = host [S][N_t+1][2]; sigma = host [S][n_omega][2] (Re, Im).
- * Errors: TBPM_EINVAL for S > 16, directions outside the lattice's dimensions, kT <= 0,
- * another form, n_omega outside [2, 2^20] or w_max <= 0. */
+ * Any S <= 32: the states run in passes of at most 16 (fewer when memory is short, see
+ * tbpm_set_pass_states).
+ * Errors: TBPM_EINVAL for directions outside the lattice's dimensions, kT <= 0, another form,
+ * n_steps outside [1, 2^22], n_omega outside [2, 2^20] or w_max <= 0; TBPM_ENOMEM when not even
+ * one state's pass fits. */
 int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int alpha,
                               int beta, double mu, double kT, double omega_max, int64_t n_omega, double* C,
                               double* sigma);

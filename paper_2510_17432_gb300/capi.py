@@ -110,6 +110,7 @@ def load():
         "tbpm_polarization": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_double, C.c_double, _P, C.c_int64,
                                         _P, _P]),
         "tbpm_charge_density": (C.c_int, [_P, _P, C.POINTER(Request), C.c_double, C.c_double, _P]),
+        "tbpm_set_pass_states": (C.c_int, [_P, C.c_int]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -131,7 +132,7 @@ def exported_symbols():
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
-            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
 
@@ -323,6 +324,10 @@ def tbpm_polarization(ctx, lat, req: Request, q, mu: float, kT: float, omegas: n
     w = np.ascontiguousarray(omegas, dtype=np.float64)
     _check(load().tbpm_polarization(ctx, lat, C.byref(req), _host_ptr(qa), float(mu), float(kT), _host_ptr(w),
                                     int(w.size), _host_ptr(C_out), _host_ptr(Pi)))
+
+
+def tbpm_set_pass_states(ctx, max_states: int):
+    _check(load().tbpm_set_pass_states(ctx, int(max_states)))
 
 
 def tbpm_charge_density(ctx, lat, req: Request, mu: float, kT: float, rho: np.ndarray):

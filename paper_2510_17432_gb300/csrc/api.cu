@@ -290,7 +290,7 @@ __global__ void k_make_diag(int64_t n, const double* v64, double H0, double half
 // ------------------------------------------------------------------ initial states
 // Random phases psi_i = exp(2 pi i u / 2^32) / sqrt(N), u = Philox(state_seed; i, 2, s).
 template <typename R>
-__global__ void k_init_random(int64_t n, int Spad, int logS, int S, uint64_t seed, const int64_t* full_of,
+__global__ void k_init_random(int64_t n, int Spad, int logS, int S, int s0, uint64_t seed, const int64_t* full_of,
                               double inv_sqrt_n, R* out, uint32_t* draws) {
   const int64_t total = n * Spad;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -300,7 +300,7 @@ __global__ void k_init_random(int64_t n, int Spad, int logS, int S, uint64_t see
     R re = R(0), im = R(0);
     if (s < S) {
       const int64_t f = full_of ? full_of[k] : k;
-      const uint32_t u = draw_u32(seed, (uint64_t)f, STREAM_PHASE, (uint32_t)s);
+      const uint32_t u = draw_u32(seed, (uint64_t)f, STREAM_PHASE, (uint32_t)(s0 + s));
       double sn, cs;
       sincospi((double)u * 0x1p-31, &sn, &cs);
       re = (R)(cs * inv_sqrt_n);
@@ -414,6 +414,16 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     return TBPM_EINVAL;
   }
   ctx->fusion = enable;
+  return TBPM_OK;
+}
+
+int tbpm_set_pass_states(tbpm_ctx* ctx, int max_states) {
+  clear_error();
+  if (!ctx || max_states < 0) {
+    set_error("tbpm_set_pass_states: invalid argument");
+    return TBPM_EINVAL;
+  }
+  ctx->max_pass_states = max_states;
   return TBPM_OK;
 }
 
@@ -696,6 +706,7 @@ struct Plan {
   size_t elem;        // bytes per complex element
   size_t state_bytes; // one block of Spad states
   double tau;
+  int s0;             // index of the block's first state among the request's states (Philox sub-stream)
 };
 
 int ilog2(int v) {
@@ -741,6 +752,7 @@ int make_plan(const tbpm_lattice* lat, const tbpm_request* req, Plan* pl) {
   pl->elem = req->precision == TBPM_C64 ? 8 : 16;
   pl->state_bytes = (size_t)lat->n_sites * pl->Spad * pl->elem;
   pl->tau = req->tau == 0.0 ? M_PI : req->tau;
+  pl->s0 = 0;
   if (!(pl->tau > 0.0) || !isfinite(pl->tau)) {
     set_error("tau must be positive");
     return TBPM_EINVAL;
@@ -755,10 +767,10 @@ int init_states(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req,
     const double inv = 1.0 / sqrt((double)n);
     const int nb = grid_for(ctx, n * pl.Spad, kT, 32);
     if (pl.precision == TBPM_C64)
-      k_init_random<float><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, req->state_seed, lat->full_of,
+      k_init_random<float><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, pl.s0, req->state_seed, lat->full_of,
                                                        inv, (float*)dst, draws);
     else
-      k_init_random<double><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, req->state_seed, lat->full_of,
+      k_init_random<double><<<nb, kT, 0, ctx->stream>>>(n, pl.Spad, pl.logS, pl.S, pl.s0, req->state_seed, lat->full_of,
                                                         inv, (double*)dst, draws);
     TBPM_CK_LAUNCH(ctx);
   } else {
@@ -970,29 +982,35 @@ using BlockHook = std::function<int(int64_t /*start*/, int /*bb*/, const void* /
 
 int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t n_steps,
                int64_t b, double* d_C, double tau_signed = 0.0, const BlockHook& hook = nullptr,
-               const void* init = nullptr) {
+               const void* init = nullptr, bool corr = true) {
   const double tau = tau_signed != 0.0 ? tau_signed : pl.tau;
   if (n_steps < 1) {
     set_error("n_steps must be >= 1");
     return TBPM_EINVAL;
   }
   b = std::max<int64_t>(1, std::min<int64_t>(b, n_steps));
-  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  if (corr) TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
   TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
   TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
   TBPM_TRY(ensure(ctx, ctx->ws_acc, pl.state_bytes * (size_t)b));
-  if (init)
-    TBPM_CK(cudaMemcpyAsync(ctx->ws_psi.p, init, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-  else
-    TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
-  TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, ctx->ws_psi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (corr) {
+    if (init)
+      TBPM_CK(cudaMemcpyAsync(ctx->ws_psi.p, init, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    else
+      TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, ctx->ws_psi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else if (!init) {
+    TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+  } else if (init != ctx->ws_phi[0].p) {
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, init, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
 
   AccumArgs g;
   memset(&g, 0, sizeof(g));
   TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
   const int C_len = (int)(n_steps + 1);
   // C(0) = <psi|psi>
-  TBPM_TRY(launch_dot(ctx, g.r, pl.precision, ctx->ws_psi.p, ctx->ws_psi.p, d_C, C_len));
+  if (corr) TBPM_TRY(launch_dot(ctx, g.r, pl.precision, ctx->ws_psi.p, ctx->ws_psi.p, d_C, C_len));
 
   const double shift = lat->H0 / lat->half;
   std::vector<double> coef_full, coef_last;
@@ -1013,8 +1031,8 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
 
   g.acc = ctx->ws_acc.p;
   g.acc_stride = lat->n_sites * (int64_t)pl.Spad;
-  g.psi = ctx->ws_psi.p;
-  g.C = d_C;
+  g.psi = corr ? ctx->ws_psi.p : nullptr;
+  g.C = corr ? d_C : nullptr;
   g.C_len = C_len;
   int64_t start = 0;
   while (start < n_steps) {
@@ -1035,6 +1053,7 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
       g.coef = tab + (size_t)n * bb * 2;
       g.j_lo = j_lo;
       g.first_term = n == 0;
+      if (!corr) done.clear();
       g.j_done = done.empty() ? -1 : done[0];
       g.j_global = done.empty() ? 0 : (int)(start + done[0] + 1);
       TBPM_TRY(launch_accum_step(ctx, g, pl.precision, mode));
@@ -1151,8 +1170,8 @@ int run_qe(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
   const double scale = tphys / (2.0 * M_PI);
   int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
   if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, &b, nullptr, nullptr));
-  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)(n_steps + 1) * pl.Spad));
-  double* dC = (double*)ctx->ws_out.p;
+  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
   for (int dir = 0; dir < 2; ++dir) {
     const double sgn = dir == 0 ? 1.0 : -1.0;
     BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
@@ -1161,8 +1180,8 @@ int run_qe(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
                                 ctx->ws_qe.p, phase, width, (int)(start + j + 1), sgn, scale, nE));
       return TBPM_OK;
     };
-    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, dC, sgn * pl.tau, hook));
-    if (dir == 0)  // j = 0 term, tau a(E,0) psi, once; run_blocks left psi in ws_psi
+    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, nullptr, sgn * pl.tau, hook, ctx->ws_psi.p, false));
+    if (dir == 0)  // j = 0 term, tau a(E,0) psi, once
       TBPM_TRY(launch_qe_axpy(ctx, ra, pl.precision, ctx->ws_psi.p, ctx->ws_qe.p, phase, width, 0, 1.0, scale, nE));
   }
   return TBPM_OK;
@@ -1248,12 +1267,10 @@ int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
     // psi_1(t_j) = e^{-iHt_j} J psi in time blocks; each block's b states meet all N_E kets at once
     int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
     if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pl, n_steps, &b, nullptr, nullptr));
-    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)W * pl.Spad));
-    double* dC = (double*)ctx->ws_recon.p;  // <J psi|psi_1(t)>, unused
     BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
       return launch_xdot(ctx, pl.precision, pl.Spad, n, first, bb, kets, nE, C, (int64_t)nE * W, 1, W, start + 1);
     };
-    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, dC, 0.0, hook, ctx->ws_jpsi.p));
+    TBPM_TRY(run_blocks(ctx, lat, req, pl, n_steps, b, nullptr, 0.0, hook, ctx->ws_jpsi.p, false));
     TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_jpsi.p, 1, kets, nE, C, (int64_t)nE * W, 0, W, 0));
     phase_end(ctx, tok);
   }
@@ -1294,13 +1311,10 @@ int fermi_series(tbpm_ctx* ctx, const tbpm_lattice* lat, double mu, double kT, i
   return TBPM_OK;
 }
 
-// out = sum_{n < n_terms} coef_n T_n(H~) X for one state block of plan pc (X and out distinct
-// from ws_phi).
-int apply_series(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, const void* X, void* out, const double* coef,
-                 int n_terms) {
-  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pc.state_bytes));
-  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pc.state_bytes));
-  TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, X, pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+// out = sum_{n < n_terms} coef_n T_n(H~) X for one state block of plan pc.  The recurrence runs
+// in b0 (which holds X on entry and is overwritten) and b1; out is distinct from both.
+int apply_series_bufs(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, void* b0, void* b1, void* out,
+                      const double* coef, int n_terms) {
   AccumArgs g;
   memset(&g, 0, sizeof(g));
   TBPM_TRY(base_args(ctx, lat, pc, &g.r, 3));
@@ -1309,10 +1323,11 @@ int apply_series(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, const void* X
   g.b = 1;
   g.j_lo = 0;
   g.j_done = -1;
+  void* buf[2] = {b0, b1};
   for (int n = 0; n < n_terms; ++n) {
     const int mode = (n == n_terms - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
-    g.r.cur = ctx->ws_phi[n & 1].p;
-    g.r.prev_out = ctx->ws_phi[(n + 1) & 1].p;
+    g.r.cur = buf[n & 1];
+    g.r.prev_out = buf[(n + 1) & 1];
     g.coef = coef + 2 * (size_t)n;
     g.first_term = n == 0;
     TBPM_TRY(launch_accum_step(ctx, g, pc.precision, mode));
@@ -1320,32 +1335,25 @@ int apply_series(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, const void* X
   return TBPM_OK;
 }
 
+// Largest power-of-two number of states per pass (<= cap) for which `blocks` state blocks of
+// that width fit in 85% of the free device memory; 0 when not even one state fits.
+int states_per_pass(const tbpm_lattice* lat, size_t elem, int cap, double blocks) {
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  int k = cap;
+  while (k >= 1 && blocks * (double)lat->n_sites * k * elem > 0.85 * (double)free_b) k >>= 1;
+  return k;
+}
+
 // Optical conductivity (op 0: X = J_alpha, O = J_beta) or dynamical polarization (op 1:
-// X = rho(q), O = rho(-q)) correlation C(t_j) = <psi_1(t_j)|X|psi_2(t_j)> of all Sh states into
-// ws_out [Sh][n_steps+1][2]; the pair plan's time step is returned in *tphys.
+// X = rho(q), O = rho(-q)) correlation C(t_j) = <psi_1(t_j)|X|psi_2(t_j)> of the plan's Sh states
+// (the request's states pl.s0 .. pl.s0 + S - 1) into ws_out [Sh][n_steps+1][2]; the pair plan's
+// time step is returned in *tphys.  Live memory: three pair blocks during the Fermi-Dirac series,
+// 2 + b during the propagation.
 int run_response(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int op, int alpha,
                  int beta, const double q[3], double mu, double kT, double** d_C, double* tphys) {
   const int64_t n_steps = req->n_steps;
-  if (n_steps < 1 || n_steps > (1 << 22)) {
-    set_error("n_steps must lie in [1, 2^22]");
-    return TBPM_EINVAL;
-  }
-  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
-    set_error("optical conductivity and polarization take the SEQUENTIAL or CONCURRENT_S form");
-    return TBPM_EINVAL;
-  }
   const int Sh = pl.Spad;
-  if (2 * Sh > 32) {
-    set_error("optical conductivity and polarization support at most 16 states per call");
-    return TBPM_EINVAL;
-  }
-  if (op == 0) {
-    const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
-    if (alpha < 0 || alpha >= dims || beta < 0 || beta >= dims) {
-      set_error("directions must lie in [0, %d)", dims);
-      return TBPM_EINVAL;
-    }
-  }
   tbpm_request rc = *req;
   rc.n_states = 2 * Sh;
   rc.states = TBPM_STATES_RANDOM;
@@ -1354,39 +1362,62 @@ int run_response(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, cons
   pc.tau = req->tau == 0.0 ? M_PI / 2 : req->tau;
   *tphys = pc.tau / lat->half;
   const int64_t n = lat->n_sites;
-  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
-  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+  const double* coef = nullptr;
+  int nf = 0;
+  TBPM_TRY(fermi_series(ctx, lat, mu, kT, 0, &coef, &nf));
   const double2* phase = nullptr;
   if (op == 1) {
     TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double2) * (size_t)n));
     phase = (const double2*)ctx->ws_ec.p;
     TBPM_TRY(launch_density_phases(ctx, lat, q, (double2*)ctx->ws_ec.p));
-  } else {
-    TBPM_TRY(ensure(ctx, ctx->ws_jpsi, pl.state_bytes));
-    TBPM_TRY(launch_current(ctx, lat, pl.precision, Sh, beta, ctx->ws_psi.p, ctx->ws_jpsi.p));
   }
-  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pc.state_bytes));
-  TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pc.state_bytes));
+  // O psi, formed from psi (twice: before the series and for the split after it)
+  auto make_states = [&]() -> int {
+    TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
+    TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
+    if (op == 0) {
+      TBPM_TRY(ensure(ctx, ctx->ws_jpsi, pl.state_bytes));
+      TBPM_TRY(launch_current(ctx, lat, pl.precision, Sh, beta, ctx->ws_psi.p, ctx->ws_jpsi.p));
+    }
+    return TBPM_OK;
+  };
+  TBPM_TRY(make_states());
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pc.state_bytes));
   TBPM_TRY(launch_pair_init(ctx, pl.precision, n, Sh, ctx->ws_psi.p, op == 0 ? ctx->ws_jpsi.p : nullptr, phase,
-                            ctx->ws_phi2[0].p));
-  const double* coef = nullptr;
-  int nf = 0;
-  TBPM_TRY(fermi_series(ctx, lat, mu, kT, 0, &coef, &nf));
-  TBPM_TRY(apply_series(ctx, lat, pc, ctx->ws_phi2[0].p, ctx->ws_phi2[1].p, coef, nf));
-  TBPM_TRY(launch_pair_split(ctx, pl.precision, n, Sh, ctx->ws_phi2[0].p, ctx->ws_phi2[1].p));
-  const void* Y0 = ctx->ws_phi2[1].p;
+                            ctx->ws_phi[0].p));
+  release(ctx, ctx->ws_psi);
+  release(ctx, ctx->ws_jpsi);
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pc.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pc.state_bytes));
+  // F = f(H) X, consuming X in ws_phi[0]
+  TBPM_TRY(apply_series_bufs(ctx, lat, pc, ctx->ws_phi[0].p, ctx->ws_phi[1].p, ctx->ws_phi2[1].p, coef, nf));
+  release(ctx, ctx->ws_phi[0]);
+  TBPM_TRY(make_states());
+  TBPM_TRY(launch_pair_split(ctx, pl.precision, n, Sh, ctx->ws_psi.p, op == 0 ? ctx->ws_jpsi.p : nullptr, phase,
+                             ctx->ws_phi2[1].p));
+  release(ctx, ctx->ws_psi);
+  release(ctx, ctx->ws_jpsi);
+  release(ctx, ctx->ws_phi2[0]);
+  std::swap(ctx->ws_phi[0], ctx->ws_phi2[1]);  // Y(0) = [f psi | (1 - f) O psi] starts the propagation
   const int64_t W = n_steps + 1;
   TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * 2 * (size_t)W * Sh));
   double* C = (double*)ctx->ws_out.p;
   const int tok = phase_begin(ctx, 0);
-  TBPM_TRY(launch_xmy(ctx, lat, pl.precision, Sh, alpha, phase, Y0, 1, pc.state_bytes, C, W, 0));
+  TBPM_TRY(launch_xmy(ctx, lat, pl.precision, Sh, alpha, phase, ctx->ws_phi[0].p, 1, pc.state_bytes, C, W, 0));
   int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
-  if (b <= 0) TBPM_TRY(choose_block(ctx, lat, &rc, pc, n_steps, &b, nullptr, nullptr));
-  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)W * pc.Spad));
+  if (b <= 0) {
+    // time the passes on copies, leaving Y(0) in ws_phi[0] untouched
+    std::swap(ctx->ws_phi[0], ctx->ws_phi2[0]);
+    const int r = choose_block(ctx, lat, &rc, pc, n_steps, &b, nullptr, nullptr);
+    std::swap(ctx->ws_phi[0], ctx->ws_phi2[0]);
+    release(ctx, ctx->ws_phi2[0]);
+    release(ctx, ctx->ws_psi);
+    TBPM_TRY(r);
+  }
   BlockHook hook = [&](int64_t start, int bb, const void* first) -> int {
     return launch_xmy(ctx, lat, pl.precision, Sh, alpha, phase, first, bb, pc.state_bytes, C, W, start + 1);
   };
-  TBPM_TRY(run_blocks(ctx, lat, &rc, pc, n_steps, b, (double*)ctx->ws_recon.p, 0.0, hook, Y0));
+  TBPM_TRY(run_blocks(ctx, lat, &rc, pc, n_steps, b, nullptr, 0.0, hook, ctx->ws_phi[0].p, false));
   phase_end(ctx, tok);
   *d_C = C;
   return TBPM_OK;
@@ -1711,13 +1742,14 @@ int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reques
   Plan pl;
   TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
-  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
-  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
-  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
   const double* coef = nullptr;
   int nf = 0;
   TBPM_TRY(fermi_series(ctx, lat, mu, kT, sqrt_f ? 1 : 0, &coef, &nf));
-  TBPM_TRY(apply_series(ctx, lat, pl, ctx->ws_psi.p, ctx->ws_phi2[0].p, coef, nf));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+  TBPM_TRY(apply_series_bufs(ctx, lat, pl, ctx->ws_phi[0].p, ctx->ws_phi[1].p, ctx->ws_phi2[0].p, coef, nf));
   const int64_t n = lat->n_sites;
   for (int s = 0; s < pl.S; ++s)
     TBPM_CK(cudaMemcpy2DAsync((char*)out + (size_t)s * n * pl.elem, pl.elem,
@@ -1727,85 +1759,120 @@ int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reques
   return TBPM_OK;
 }
 
+namespace {
+// Shared checks and the state-chunk loop of the OC, DP and CD entry points: `pass` runs the
+// request's states s0 .. s0 + k - 1 with the chunk's plan.
+int response_chunks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, int64_t min_steps,
+                    double pair_blocks, const std::function<int(const tbpm_request*, const Plan&)>& pass) {
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  if (req->n_steps < min_steps || req->n_steps > (1 << 22)) {
+    set_error("n_steps must lie in [%lld, 2^22]", (long long)min_steps);
+    return TBPM_EINVAL;
+  }
+  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
+    set_error("this quantity takes the SEQUENTIAL or CONCURRENT_S form");
+    return TBPM_EINVAL;
+  }
+  int cap = std::min(pl.Spad, 16);
+  if (ctx->max_pass_states > 0)
+    while (cap > ctx->max_pass_states) cap >>= 1;
+  const int k = states_per_pass(lat, pl.elem, cap, pair_blocks);
+  if (k < 1) {
+    set_error("not enough device memory for one state of %lld sites", (long long)lat->n_sites);
+    return TBPM_ENOMEM;
+  }
+  for (int s0 = 0; s0 < pl.S; s0 += k) {
+    tbpm_request rq = *req;
+    rq.n_states = std::min(k, pl.S - s0);
+    if (req->states == TBPM_STATES_SITES) rq.sites = req->sites + s0;
+    Plan pk;
+    TBPM_TRY(make_plan(lat, &rq, &pk));
+    pk.s0 = s0;
+    TBPM_TRY(pass(&rq, pk));
+  }
+  return TBPM_OK;
+}
+}  // namespace
+
 int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int alpha,
                               int beta, double mu, double kT, double omega_max, int64_t n_omega, double* C,
                               double* sigma) {
   clear_error();
-  if (!ctx || !sigma || n_omega < 2 || n_omega > (1 << 20) || !(omega_max > 0.0)) {
+  if (!ctx || !req || !sigma || n_omega < 2 || n_omega > (1 << 20) || !(omega_max > 0.0)) {
     set_error("tbpm_optical_conductivity: invalid argument (n_omega in [2, 2^20], omega_max > 0)");
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
-  Plan pl;
-  TBPM_TRY(make_plan(lat, req, &pl));
+  const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
+  if (alpha < 0 || alpha >= dims || beta < 0 || beta >= dims) {
+    set_error("directions must lie in [0, %d)", dims);
+    return TBPM_EINVAL;
+  }
   TBPM_CK(cudaSetDevice(ctx->device));
-  double* d_C = nullptr;
-  double tphys = 0.0;
-  const double q0[3] = {0, 0, 0};
-  TBPM_TRY(run_response(ctx, lat, req, pl, 0, alpha, beta, q0, mu, kT, &d_C, &tphys));
-  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pl.S));
-  double* d_sig = (double*)ctx->ws_recon.p;
   const double area = lat->desc.kind == TBPM_HONEYCOMB ? 3.0 * sqrt(3.0) / 4.0 : 1.0;
-  TBPM_TRY(launch_oc_spectrum(ctx, d_C, pl.S, (int)req->n_steps, omega_max / (double)(n_omega - 1), (int)n_omega,
-                              kT, tphys, area, req->window, d_sig));
-  if (C)
-    TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * (size_t)pl.S * (req->n_steps + 1), cudaMemcpyDeviceToHost,
-                            ctx->stream));
-  TBPM_CK(cudaMemcpyAsync(sigma, d_sig, sizeof(double) * 2 * (size_t)pl.S * n_omega, cudaMemcpyDeviceToHost,
-                          ctx->stream));
-  TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+  const int64_t W = req->n_steps + 1;
+  const double q0[3] = {0, 0, 0};
+  // 3 pair blocks = 6 single blocks live at a time, plus room for b >= 2 accumulators
+  return response_chunks(ctx, lat, req, 1, 8.0, [&](const tbpm_request* rq, const Plan& pk) -> int {
+    double* d_C = nullptr;
+    double tphys = 0.0;
+    TBPM_TRY(run_response(ctx, lat, rq, pk, 0, alpha, beta, q0, mu, kT, &d_C, &tphys));
+    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pk.S));
+    double* d_sig = (double*)ctx->ws_recon.p;
+    TBPM_TRY(launch_oc_spectrum(ctx, d_C, pk.S, (int)rq->n_steps, omega_max / (double)(n_omega - 1), (int)n_omega,
+                                kT, tphys, area, rq->window, d_sig));
+    if (C)
+      TBPM_CK(cudaMemcpyAsync(C + 2 * (size_t)pk.s0 * W, d_C, sizeof(double) * 2 * (size_t)pk.S * W,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(sigma + 2 * (size_t)pk.s0 * n_omega, d_sig, sizeof(double) * 2 * (size_t)pk.S * n_omega,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
+    return TBPM_OK;
+  });
 }
 
 int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double q[3], double mu,
                       double kT, const double* omegas, int64_t n_omega, double* C, double* Pi) {
   clear_error();
-  if (!ctx || !q || !omegas || !Pi || n_omega < 1 || n_omega > (1 << 20)) {
+  if (!ctx || !req || !q || !omegas || !Pi || n_omega < 1 || n_omega > (1 << 20)) {
     set_error("tbpm_polarization: invalid argument");
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
-  Plan pl;
-  TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
-  double* d_C = nullptr;
-  double tphys = 0.0;
-  TBPM_TRY(run_response(ctx, lat, req, pl, 1, 0, 0, q, mu, kT, &d_C, &tphys));
-  TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)n_omega));
-  TBPM_CK(cudaMemcpyAsync(ctx->ws_energies.p, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice, ctx->stream));
-  TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pl.S));
-  double* d_pi = (double*)ctx->ws_recon.p;
   const double area = lat->desc.kind == TBPM_HONEYCOMB ? 3.0 * sqrt(3.0) / 4.0 : 1.0;
-  TBPM_TRY(launch_dp_spectrum(ctx, d_C, pl.S, (int)req->n_steps, (const double*)ctx->ws_energies.p, (int)n_omega,
-                              tphys, area, req->window, d_pi));
-  if (C)
-    TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * (size_t)pl.S * (req->n_steps + 1), cudaMemcpyDeviceToHost,
+  const int64_t W = req->n_steps + 1;
+  return response_chunks(ctx, lat, req, 1, 8.0, [&](const tbpm_request* rq, const Plan& pk) -> int {
+    double* d_C = nullptr;
+    double tphys = 0.0;
+    TBPM_TRY(run_response(ctx, lat, rq, pk, 1, 0, 0, q, mu, kT, &d_C, &tphys));
+    TBPM_TRY(ensure(ctx, ctx->ws_energies, sizeof(double) * (size_t)n_omega));
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_energies.p, omegas, sizeof(double) * n_omega, cudaMemcpyHostToDevice,
                             ctx->stream));
-  TBPM_CK(cudaMemcpyAsync(Pi, d_pi, sizeof(double) * 2 * (size_t)pl.S * n_omega, cudaMemcpyDeviceToHost, ctx->stream));
-  TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)n_omega * pk.S));
+    double* d_pi = (double*)ctx->ws_recon.p;
+    TBPM_TRY(launch_dp_spectrum(ctx, d_C, pk.S, (int)rq->n_steps, (const double*)ctx->ws_energies.p, (int)n_omega,
+                                tphys, area, rq->window, d_pi));
+    if (C)
+      TBPM_CK(cudaMemcpyAsync(C + 2 * (size_t)pk.s0 * W, d_C, sizeof(double) * 2 * (size_t)pk.S * W,
+                              cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(Pi + 2 * (size_t)pk.s0 * n_omega, d_pi, sizeof(double) * 2 * (size_t)pk.S * n_omega,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
+    return TBPM_OK;
+  });
 }
 
 int tbpm_charge_density(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double mu, double kT,
                         double* rho) {
   clear_error();
-  if (!ctx || !rho) {
+  if (!ctx || !req || !rho) {
     set_error("tbpm_charge_density: invalid argument");
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
-  Plan pl;
-  TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
-  const int64_t n_steps = req->n_steps;
-  if (n_steps < 0 || n_steps > (1 << 22)) {
-    set_error("n_steps must lie in [0, 2^22]");
-    return TBPM_EINVAL;
-  }
-  if (req->form != TBPM_SEQUENTIAL && req->form != TBPM_CONCURRENT_S) {
-    set_error("charge density takes the SEQUENTIAL or CONCURRENT_S form");
-    return TBPM_EINVAL;
-  }
   double tau = req->tau;
   if (tau == 0.0) {
     const double occ = std::min(lat->E_max, mu + 20.0 * kT) - lat->E_min;
@@ -1815,38 +1882,52 @@ int tbpm_charge_density(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_req
     }
     tau = M_PI * lat->half / occ;
   }
-  Plan pc = pl;
-  pc.tau = tau;
   const int64_t n = lat->n_sites;
-  TBPM_TRY(ensure(ctx, ctx->ws_psi, pl.state_bytes));
-  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
-  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_psi.p, nullptr));
-  const double* coef = nullptr;
-  int nf = 0;
-  TBPM_TRY(fermi_series(ctx, lat, mu, kT, 1, &coef, &nf));
-  TBPM_TRY(apply_series(ctx, lat, pl, ctx->ws_psi.p, ctx->ws_phi2[0].p, coef, nf));
-  const int64_t elems = n * pl.Spad;
-  TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double) * (size_t)elems));
-  double* z = (double*)ctx->ws_ec.p;
-  TBPM_CK(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)elems, ctx->stream));
-  const int tok = phase_begin(ctx, 0);
-  TBPM_TRY(launch_abs2py(ctx, pl.precision, ctx->ws_phi2[0].p, 1, pl.state_bytes, elems, 0.5, z));
-  if (n_steps >= 1) {
-    int64_t b = req->form == TBPM_SEQUENTIAL ? 1 : req->time_block;
-    if (b <= 0) TBPM_TRY(choose_block(ctx, lat, req, pc, n_steps, &b, nullptr, nullptr));
-    TBPM_TRY(ensure(ctx, ctx->ws_recon, sizeof(double) * 2 * (size_t)(n_steps + 1) * pl.Spad));
-    BlockHook hook = [&](int64_t, int bb, const void* first) -> int {
-      return launch_abs2py(ctx, pl.precision, first, bb, pl.state_bytes, elems, 1.0, z);
-    };
-    TBPM_TRY(run_blocks(ctx, lat, req, pc, n_steps, b, (double*)ctx->ws_recon.p, 0.0, hook, ctx->ws_phi2[0].p));
-  }
-  phase_end(ctx, tok);
-  TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * (size_t)n * pl.S));
-  const double wsum = 0.5 + (double)n_steps;
-  TBPM_TRY(launch_cd_finish(ctx, z, n, pl.S, pl.Spad, (double)n / wsum, (double*)ctx->ws_out.p));
-  TBPM_CK(cudaMemcpyAsync(rho, ctx->ws_out.p, sizeof(double) * (size_t)n * pl.S, cudaMemcpyDeviceToHost, ctx->stream));
-  TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+  // live: three state blocks in the series, then 2 + b blocks and the FP64 accumulator (2 blocks)
+  return response_chunks(ctx, lat, req, 0, 6.0, [&](const tbpm_request* rq, const Plan& pl) -> int {
+    Plan pc = pl;
+    pc.tau = tau;
+    const double* coef = nullptr;
+    int nf = 0;
+    TBPM_TRY(fermi_series(ctx, lat, mu, kT, 1, &coef, &nf));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+    TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+    TBPM_TRY(init_states(ctx, lat, rq, pl, ctx->ws_phi[0].p, nullptr));
+    // phi = f^{1/2}(H) psi into ws_phi2[0], consuming psi in ws_phi[0]
+    TBPM_TRY(apply_series_bufs(ctx, lat, pl, ctx->ws_phi[0].p, ctx->ws_phi[1].p, ctx->ws_phi2[0].p, coef, nf));
+    std::swap(ctx->ws_phi[0], ctx->ws_phi2[0]);
+    release(ctx, ctx->ws_phi2[0]);
+    const int64_t elems = n * pl.Spad;
+    TBPM_TRY(ensure(ctx, ctx->ws_ec, sizeof(double) * (size_t)elems));
+    double* z = (double*)ctx->ws_ec.p;
+    TBPM_CK(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)elems, ctx->stream));
+    const int tok = phase_begin(ctx, 0);
+    TBPM_TRY(launch_abs2py(ctx, pl.precision, ctx->ws_phi[0].p, 1, pl.state_bytes, elems, 0.5, z));
+    if (rq->n_steps >= 1) {
+      int64_t b = rq->form == TBPM_SEQUENTIAL ? 1 : rq->time_block;
+      if (b <= 0) {
+        std::swap(ctx->ws_phi[0], ctx->ws_phi2[0]);
+        const int r = choose_block(ctx, lat, rq, pc, rq->n_steps, &b, nullptr, nullptr);
+        std::swap(ctx->ws_phi[0], ctx->ws_phi2[0]);
+        release(ctx, ctx->ws_phi2[0]);
+        release(ctx, ctx->ws_psi);
+        TBPM_TRY(r);
+      }
+      BlockHook hook = [&](int64_t, int bb, const void* first) -> int {
+        return launch_abs2py(ctx, pl.precision, first, bb, pl.state_bytes, elems, 1.0, z);
+      };
+      TBPM_TRY(run_blocks(ctx, lat, rq, pc, rq->n_steps, b, nullptr, 0.0, hook, ctx->ws_phi[0].p, false));
+    }
+    phase_end(ctx, tok);
+    TBPM_TRY(ensure(ctx, ctx->ws_out, sizeof(double) * (size_t)n * pl.S));
+    const double wsum = 0.5 + (double)rq->n_steps;
+    TBPM_TRY(launch_cd_finish(ctx, z, n, pl.S, pl.Spad, (double)n / wsum, (double*)ctx->ws_out.p));
+    TBPM_CK(cudaMemcpyAsync(rho + (size_t)pl.s0 * n, ctx->ws_out.p, sizeof(double) * (size_t)n * pl.S,
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
+    return TBPM_OK;
+  });
 }
 
 // ---------------------------------------------------------------- cost model (Sec. II.B, Tab. I)

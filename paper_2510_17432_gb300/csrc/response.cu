@@ -9,7 +9,8 @@
 //  * Both Fermi-filtered states of one random state travel in one state block of 2 Sh states:
 //    states [0, Sh) hold psi_1 = f(H) psi, states [Sh, 2Sh) hold psi_2 = [1 - f(H)] O psi with
 //    O = J_beta (OC) or rho(-q) (DP), so one recurrence pass propagates both.  1 - f is applied
-//    as O psi - f(H) O psi.
+//    as O psi - f(H) O psi, with O psi formed again after the series (the series consumes its
+//    input block in place, so at most three pair blocks are live).
 //  * xmy: C(t) = <psi_1(t)| X |psi_2(t)> with X = J_alpha (bonds, weights -i t (r_j - r_i)_alpha)
 //    or rho(q) (diagonal e^{i q.r_i}), for every state of a time block in one launch.
 //  * Re sigma(w) = 2 (e^{-w/kT} - 1)/(w a_site) tau sum_j w_j sin(w t_j) Im C(t_j)   (w > 0),
@@ -137,18 +138,31 @@ __global__ void k_pair_init(int64_t n, int Sh, const void* psi_v, const void* op
   }
 }
 
-// F[i][Sh+s] = Xc[i][Sh+s] - F[i][Sh+s]: the second half becomes [1 - f(H)] O psi.
+// F[i][Sh+s] = (O psi)[i][s] - F[i][Sh+s]: the second half becomes [1 - f(H)] O psi.  O psi is
+// opsi, or conj(phase_i) psi_i when phase != null.
 template <typename R>
-__global__ void k_pair_split(int64_t n, int Sh, const void* xc_v, void* f_v) {
+__global__ void k_pair_split(int64_t n, int Sh, const void* psi_v, const void* opsi_v, const double2* phase,
+                             void* f_v) {
   using T = typename C2<R>::T;
-  const T* xc = reinterpret_cast<const T*>(xc_v);
+  const T* psi = reinterpret_cast<const T*>(psi_v);
+  const T* opsi = reinterpret_cast<const T*>(opsi_v);
   T* f = reinterpret_cast<T*>(f_v);
   const int64_t total = n * Sh;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / Sh;
     const int s = (int)(e - i * Sh);
+    T x;
+    if (phase) {
+      const T p = psi[e];
+      const double2 ph = phase[i];
+      const R cr = (R)ph.x, ci = (R)-ph.y;
+      x.x = cr * p.x - ci * p.y;
+      x.y = cr * p.y + ci * p.x;
+    } else {
+      x = opsi[e];
+    }
     const int64_t o = i * 2 * Sh + Sh + s;
-    const T x = xc[o], y = f[o];
+    const T y = f[o];
     f[o] = T{x.x - y.x, x.y - y.y};
   }
 }
@@ -399,12 +413,13 @@ int launch_pair_init(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void
   return TBPM_OK;
 }
 
-int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* xc, void* f) {
+int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* psi, const void* opsi,
+                      const double2* phase, void* f) {
   const int g = grid_of(ctx, n * Sh);
   if (precision == TBPM_C128)
-    k_pair_split<double><<<g, 256, 0, ctx->stream>>>(n, Sh, xc, f);
+    k_pair_split<double><<<g, 256, 0, ctx->stream>>>(n, Sh, psi, opsi, phase, f);
   else
-    k_pair_split<float><<<g, 256, 0, ctx->stream>>>(n, Sh, xc, f);
+    k_pair_split<float><<<g, 256, 0, ctx->stream>>>(n, Sh, psi, opsi, phase, f);
   TBPM_CK_LAUNCH(ctx);
   return TBPM_OK;
 }

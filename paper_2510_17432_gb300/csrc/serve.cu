@@ -27,7 +27,16 @@
 
 namespace tbpm {
 
-constexpr int kServeTU = 8 * kThreads;  // units per tile (8 per thread)
+constexpr int kServeTU = 32 * kThreads;  // largest tile (32 units per thread, FP32 partial sums)
+
+// Units per tile of a request with `units` thread units: 32 per thread (the per-tile reduction
+// and bookkeeping amortised) unless the request would get fewer than 64 tiles, then fewer.
+// Depends only on the request, so its partial sums (and results) are the same alone and in any mix.
+__host__ __device__ inline int serve_tile_units(int64_t units) {
+  int upt = 1;
+  while (upt < 32 && (int64_t)upt * kThreads * 64 < units) upt <<= 1;
+  return upt * kThreads;
+}
 
 struct ServeItem {
   Geom geom;
@@ -43,7 +52,8 @@ struct ServeItem {
   int upr;              // units per x-line (stencil)
   int tiles_per_line;   // > 0: tiles are segments of one line
   int lines_per_tile;   // > 0: tiles hold whole short lines
-  uint32_t line_magic;  // ceil(2^32 / upr), for u / upr with u < kServeTU
+  uint32_t line_magic;  // ceil(2^32 / upr), for u / upr with u < tu <= kServeTU
+  int tu;               // units per tile (a multiple of kThreads, <= kServeTU)
   int64_t n_tiles, tile_begin;
   double* tile_partials;  // [n_tiles][S][3]
   unsigned* counter;
@@ -137,22 +147,25 @@ __device__ void serve_tile(const ServeItem* itp, ServeItem* git, int64_t lt, dou
   if constexpr (CSR) {
     const int64_t n_units = it.n_sites * P;
     const LineBases b{};
-    for (int k = 0; k < kServeTU / kThreads; ++k) {
-      const int64_t u = lt * kServeTU + k * kThreads + threadIdx.x;
+#pragma unroll 4
+    for (int k = 0; k < it.tu / kThreads; ++k) {
+      const int64_t u = lt * it.tu + k * kThreads + threadIdx.x;
       if (u < n_units) serve_unit<KIND, CSR, R, SPT>(it, cur, po, b, u, 0, p, first, th, dc, acc);
     }
   } else if (it.tiles_per_line > 0) {
     const int64_t line = lt / it.tiles_per_line;
     const int seg = (int)(lt - line * it.tiles_per_line);
     const LineBases b = line_bases<KIND>(it.geom, line, it.upr);
-    for (int k = 0; k < kServeTU / kThreads; ++k) {
-      const int u = seg * kServeTU + k * kThreads + threadIdx.x;
+#pragma unroll 4
+    for (int k = 0; k < it.tu / kThreads; ++k) {
+      const int u = seg * it.tu + k * kThreads + threadIdx.x;
       if (u < it.upr) serve_unit<KIND, CSR, R, SPT>(it, cur, po, b, b.own + u, u, p, first, th, dc, acc);
     }
   } else {
     const int L = it.lines_per_tile;
     const int64_t line0 = lt * L;
-    for (int k = 0; k < kServeTU / kThreads; ++k) {
+#pragma unroll 4
+    for (int k = 0; k < it.tu / kThreads; ++k) {
       const uint32_t uu = (uint32_t)(k * kThreads + threadIdx.x);
       const uint32_t lo = (uint32_t)(((uint64_t)uu * it.line_magic) >> 32);
       const int u = (int)(uu - lo * (uint32_t)it.upr);
@@ -164,7 +177,7 @@ __device__ void serve_tile(const ServeItem* itp, ServeItem* git, int64_t lt, dou
     }
   }
 
-  // tile partial sums: FP32 (at most 8 units per thread) -> FP64 warp and block trees
+  // tile partial sums: FP32 (at most 32 units per thread) -> FP64 warp and block trees
   double v[3 * SPT];
 #pragma unroll
   for (int k = 0; k < 3 * SPT; ++k) v[k] = (double)acc[k];
@@ -226,7 +239,7 @@ __device__ __forceinline__ void serve_dispatch_prec(const ServeItem* it, ServeIt
   else serve_tile<KIND, CSR, float, 1>(it, git, lt, red, ticket);
 }
 
-__global__ void __launch_bounds__(kThreads) k_serve_step(ServeItem* items, int n_items, int64_t total_tiles) {
+__global__ void __launch_bounds__(kThreads, 4) k_serve_step(ServeItem* items, int n_items, int64_t total_tiles) {
   __shared__ double red[kWarps][32][6];
   __shared__ unsigned ticket;
   __shared__ ServeItem sit;  // the tile's work item, staged once per tile
@@ -341,8 +354,10 @@ static int64_t full_sites(const tbpm_lattice_desc& d) {
 
 // geometry-only tiling, identical alone and in a mix
 static void plan_tiles(ServeJob* j, int64_t n_sites, const Geom& g, int path) {
+  const int tu = serve_tile_units(n_sites * j->P);
+  j->item.tu = tu;
   if (path == TBPM_PATH_CSR) {
-    j->n_tiles = (n_sites * j->P + kServeTU - 1) / kServeTU;
+    j->n_tiles = (n_sites * j->P + tu - 1) / tu;
     j->item.upr = 0;
     j->item.tiles_per_line = 0;
     j->item.lines_per_tile = 0;
@@ -350,13 +365,13 @@ static void plan_tiles(ServeJob* j, int64_t n_sites, const Geom& g, int path) {
   }
   const int upr = (int)(g.row_sites * j->P);
   j->item.upr = upr;
-  if (upr >= kServeTU) {
-    j->item.tiles_per_line = (upr + kServeTU - 1) / kServeTU;
+  if (upr >= tu) {
+    j->item.tiles_per_line = (upr + tu - 1) / tu;
     j->item.lines_per_tile = 0;
     j->n_tiles = g.n_rows * j->item.tiles_per_line;
   } else {
     j->item.tiles_per_line = 0;
-    j->item.lines_per_tile = kServeTU / upr;
+    j->item.lines_per_tile = tu / upr;
     j->item.line_magic = (uint32_t)(((1ull << 32) + upr - 1) / upr);
     j->n_tiles = (g.n_rows + j->item.lines_per_tile - 1) / j->item.lines_per_tile;
   }
@@ -736,7 +751,8 @@ int tbpm_submit(tbpm_server* srv, const tbpm_lattice_desc* ldesc, const tbpm_req
   const int64_t nf = full_sites(j->ldesc);
   const int z = ldesc->kind == TBPM_SQUARE ? 4 : ldesc->kind == TBPM_HONEYCOMB ? 3 : 6;
   j->state_bytes = (size_t)nf * j->Spad * j->elem;
-  j->n_tiles = (nf * j->P + kServeTU - 1) / kServeTU + (ldesc->L[1] * (ldesc->kind == TBPM_CUBIC ? ldesc->L[2] : 1));
+  const int tu = serve_tile_units(nf * j->P);
+  j->n_tiles = (nf * j->P + tu - 1) / tu + (ldesc->L[1] * (ldesc->kind == TBPM_CUBIC ? ldesc->L[2] : 1));
   j->footprint = job_footprint(j, nf, nf, z);
   if (cudaMallocHost((void**)&j->hD, sizeof(double) * n_energies * j->S) != cudaSuccess ||
       cudaMallocHost((void**)&j->h_err, sizeof(int)) != cudaSuccess) {

@@ -154,6 +154,7 @@ struct tbpm_ctx {
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
       ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi;
   int fusion = 0;  // temporal-fusion mode of the moment pass (0 = one step per pass, the default)
+  int max_pass_states = 0;  // cap on states per pass of the OC, DP and CD drivers (0 = by memory)
   double* pinned = nullptr;
   size_t pinned_cap = 0;
   // phase timing with CUDA events on the context stream (tbpm_profile)
@@ -298,7 +299,8 @@ int launch_fermi_coefficients(tbpm_ctx* ctx, double mu, double kT, double H0, do
 int launch_density_phases(tbpm_ctx* ctx, const tbpm_lattice* lat, const double q[3], double2* phase);
 int launch_pair_init(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* psi, const void* opsi,
                      const double2* phase, void* xc);
-int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* xc, void* f);
+int launch_pair_split(tbpm_ctx* ctx, int precision, int64_t n, int Sh, const void* psi, const void* opsi,
+                      const double2* phase, void* f);
 int launch_xmy(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int Sh, int alpha, const double2* phase,
                const void* Y, int bb, size_t pair_bytes, double* C, int64_t os, int64_t off);
 int launch_abs2py(tbpm_ctx* ctx, int precision, const void* Y, int bb, size_t block_bytes, int64_t n_elems,

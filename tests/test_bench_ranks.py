@@ -57,3 +57,19 @@ def test_reference_arm_is_silent_on_other_ranks():
                        timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_state_based_schedule_matches_table_one_counts():
+    """bench.py's pass schedule of the time-block form: one pass per generated Chebyshev term
+    (Tab. I amxsy, T_0 included) of which all but the last of each block apply H, and one
+    accumulator update per (time, term) pair (Tab. I axpy)."""
+    import math
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import cost, bessel
+    for Nt, b in [(100, 1), (100, 7), (2048, 40), (33, 33)]:
+        apps, passes, blocks = bench.state_based_schedule(Nt, b, math.pi, bessel.truncation_order)
+        c = cost.block_counts(Nt, b, math.pi)
+        assert len(passes) == c["amxsy"]
+        assert apps == c["amxsy"] - blocks
+        assert sum(p[0] for p in passes) == c["axpy"]

@@ -162,10 +162,6 @@ def test_response_rejects_invalid_requests(capi, ctx):
                                        5.0, 4, C, sig)
     with pytest.raises(capi.TbpmError):   # z direction on a 2-D lattice
         capi.tbpm_optical_conductivity(ctx, lat, ok, 2, 0, 0.0, 0.1, 5.0, 4, C, sig)
-    big = np.zeros((17, 5), np.complex128)
-    with pytest.raises(capi.TbpmError):   # 17 states need a 64-state pair block
-        capi.tbpm_polarization(ctx, lat, capi.request(n_states=17, n_steps=4, form=0), (0.1, 0, 0), 0.0, 0.1,
-                               np.array([1.0]), big, np.zeros((17, 1), np.complex128))
     capi.tbpm_lattice_destroy(lat)
 
 
@@ -187,4 +183,33 @@ def test_charge_density_matches_oracle(capi, ctx, name, spec, form, b, Nt, prec)
     for s in range(S):
         ref = ocd.charge_density_sequential(ol, psi[s], mu, kT, Nt, tau)
         assert _rel(rho[s], ref) <= TOL[prec], (s, _rel(rho[s], ref))
+    capi.tbpm_lattice_destroy(lat)
+
+
+def test_passes_of_fewer_states_give_the_same_results(capi, ctx):
+    """OC, DP and CD with the states split into passes of one and of two states (the memory
+    control used on large lattices) agree with one pass of all states (complex128)."""
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(1, (10, 8), t=-2.7, W=1.0, seed=46))
+    S, Nt, nw = 3, 15, 17
+    om = np.linspace(0.0, 9.0, 5)
+    res = []
+    for k in (0, 1, 2):
+        capi.tbpm_set_pass_states(ctx, k)
+        C = np.zeros((S, Nt + 1), np.complex128)
+        sig = np.zeros((S, nw), np.complex128)
+        capi.tbpm_optical_conductivity(ctx, lat, capi.request(n_states=S, precision=1, form=2, n_steps=Nt,
+                                                              time_block=4, state_seed=5), 0, 1, 0.2, 0.3, 12.0,
+                                       nw, C, sig)
+        Cd = np.zeros((S, Nt + 1), np.complex128)
+        Pi = np.zeros((S, om.size), np.complex128)
+        capi.tbpm_polarization(ctx, lat, capi.request(n_states=S, precision=1, form=0, n_steps=Nt, state_seed=5),
+                               (0.4, 0.1, 0.0), 0.2, 0.3, om, Cd, Pi)
+        rho = np.zeros((S, 160))
+        capi.tbpm_charge_density(ctx, lat, capi.request(n_states=S, precision=1, form=2, n_steps=Nt, time_block=4,
+                                                        state_seed=5), 0.2, 0.3, rho)
+        res.append((C, sig, Cd, Pi, rho))
+    capi.tbpm_set_pass_states(ctx, 0)
+    for k in (1, 2):
+        for a, b in zip(res[k], res[0]):
+            assert _rel(a, b) < 1e-12, k
     capi.tbpm_lattice_destroy(lat)
