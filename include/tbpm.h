@@ -149,7 +149,9 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
  * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least one tile wide).
  * mode: 0 = one step per pass (default: on GB300 the one-step pass reaches ~82% of HBM
  * bandwidth while the shared-memory passes are limited by shared-memory instruction issue);
- * 1 = 4 steps per pass; 2 = 2 steps per pass.  Results agree within the complex64 tolerance. */
+ * 1 = 4 steps per pass (2-D tiles); 2 = 2 steps per pass (2-D tiles); 3 and 4 = 2 steps per pass
+ * by a row sweep (bands of cells, rows streamed through a shared-memory ring two rows ahead;
+ * 128- and 256-thread CTAs).  Results agree within the complex64 tolerance. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
 /* Memory control of the Fermi-Dirac filtered quantities (tbpm_optical_conductivity,
  * tbpm_polarization, tbpm_charge_density): their states are processed in passes of at most

@@ -409,8 +409,8 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     set_error("tbpm_set_fusion: ctx is NULL");
     return TBPM_EINVAL;
   }
-  if (enable < 0 || enable > 2) {
-    set_error("tbpm_set_fusion: mode %d unknown (0..2)", enable);
+  if (enable < 0 || enable > 4) {
+    set_error("tbpm_set_fusion: mode %d unknown (0..4)", enable);
     return TBPM_EINVAL;
   }
   ctx->fusion = enable;

@@ -205,17 +205,28 @@ __global__ void __launch_bounds__(kThreads) k_moment_step(RecurrenceArgs a) {
 }
 
 // ------------------------------------------------------------------ stencil moment pass (fast path)
-// Matrix-free stencil version of the moment pass.  Work is walked in super-tiles of 2 x 256
-// thread units along one x-line, so each thread keeps two independent units in flight; the
+// Launch shape of the pass: units per thread per super-tile and the CTAs per SM the register
+// budget is sized for (overridable at build time for sweeps).
+#ifndef TBPM_STENCIL_UPT
+#define TBPM_STENCIL_UPT 2
+#endif
+#ifndef TBPM_STENCIL_MINB
+#define TBPM_STENCIL_MINB 4
+#endif
+constexpr int kStencilUPT = TBPM_STENCIL_UPT;
+constexpr int kStencilMinBlocks = TBPM_STENCIL_MINB;
+
+// Matrix-free stencil version of the moment pass.  Work is walked in super-tiles of UPT x 256
+// thread units along one x-line, so each thread keeps UPT independent units in flight; the
 // line index advances incrementally (no division per unit) and neighbour offsets inside a
 // line are 32-bit.  The inner products are summed in FP32 over at most 32 units per thread
 // and then folded into FP64 (GB300 issues only 2 FP64 operations per clock per SM, so FP64
 // work per unit is kept to a fraction of an operation).
 template <int KIND, typename R, int SPT, bool FIRST>
-__global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a) {
+__global__ void __launch_bounds__(kThreads, kStencilMinBlocks) k_moment_stencil(RecurrenceArgs a) {
   using PK = Pack<R, SPT>;
   constexpr int Z = KIND == TBPM_HONEYCOMB ? 3 : (KIND == TBPM_SQUARE ? 4 : 6);
-  constexpr int TU = 2 * kThreads;
+  constexpr int TU = kStencilUPT * kThreads;
   const PK* __restrict__ cur = reinterpret_cast<const PK*>(a.cur);
   PK* __restrict__ po = reinterpret_cast<PK*>(a.prev_out);
   const R* __restrict__ diag = reinterpret_cast<const R*>(a.diag);
@@ -239,12 +250,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a
       b = line_bases<KIND>(g, row, upr);
       cached = row;
     }
-    PK ph[2], h[2], pv[2];
-    bool valid[2];
-    int64_t own[2];
-    R d[2];
+    PK ph[kStencilUPT], h[kStencilUPT], pv[kStencilUPT];
+    bool valid[kStencilUPT];
+    int64_t own[kStencilUPT];
+    R d[kStencilUPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kStencilUPT; ++k) {
       const int u = chunk * TU + k * kThreads + threadIdx.x;
       valid[k] = u < upr;
 #pragma unroll
@@ -271,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a
       }
     }
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kStencilUPT; ++k) {
       if (!valid[k]) continue;
       PK o;
 #pragma unroll
@@ -288,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_moment_stencil(RecurrenceArgs a
         Bi[q].add(orr * pi - oi * pr);
       }
     }
-    if (++fold == 16) {
+    if (++fold == 32 / kStencilUPT) {
       fold = 0;
 #pragma unroll
       for (int q = 0; q < SPT; ++q) {
@@ -613,7 +624,7 @@ static void* moment_kernel(int kind, bool csr, bool first) {
 // super-tiles of the stencil moment pass (2 x 256 units along one line)
 static int64_t stencil_supertiles(const Geom& g, int P) {
   const int64_t upr = g.row_sites * P;
-  return g.n_rows * ((upr + 2 * kThreads - 1) / (2 * kThreads));
+  return g.n_rows * ((upr + kStencilUPT * kThreads - 1) / (kStencilUPT * kThreads));
 }
 
 template <typename R, int SPT, int MODE>

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "stencil.cuh"
@@ -279,7 +280,326 @@ __global__ void __launch_bounds__(C::NT, 2) k_fused_cols(FusedArgs a) {
 using V1 = Cfg2<4>;  // 4 steps per pass
 using V2 = Cfg2<2>;  // 2 steps per pass
 
+// ------------------------------------------------------------------ row-sweep two-step kernel
+// One CTA owns a band of BX interior cells (plus one halo cell on each side: on the honeycomb the
+// dependence of two steps reaches one cell, alternating A -> B(x-1) -> A(x-1)/A(x)) and a segment
+// of SY rows, and sweeps the segment upwards.  Row r of phi_n streams into a ring of shared-memory
+// rows with cp.async PD rows ahead; the step n+1 row r is formed from rows r-1, r, r+1 of phi_n
+// and phi_{n-1}(r) (read straight into registers), kept in a three-row ring, and step n+2 row r-1
+// follows from that ring.  Both new rows go to HBM once, so per two steps each state crosses HBM
+// four times (plus the halo rows and columns) instead of six.  A tile row is CW = NT/P cells of
+// 2 sites x P state pairs (contiguous in memory); thread t owns cell t/P, pair t%P, and both of
+// its sites, so one of the three neighbours of each site is the thread's other site.  A shared row
+// stores the A plane and the B plane of the tile separately (consecutive threads read consecutive
+// 16-byte units, free of bank conflicts), each with P zero units before and after, which stand in
+// for the neighbours outside the tile.
+template <int NT_>
+struct RowCfg {
+  static constexpr int NT = NT_;
+  static constexpr int RU = 2 * NT;      // thread units per tile row (two per thread)
+  static constexpr int PD = 1;           // rows of phi_n in flight ahead of the one being waited for
+  static constexpr int NSLOT0 = PD + 3;  // phi_n rows r-1 .. r+PD+1
+  static constexpr int NSLOT1 = 3;       // phi_{n+1} rows r-2 .. r
+  static constexpr int NV = 12;          // 2 steps x {A, Re B, Im B} x 2 states
+  static constexpr int FOLD = 16;        // rows per FP32 partial (32 unit terms per thread)
+  static constexpr int MINB = NT >= 256 ? 3 : 6;
+  static size_t smem(int P) {
+    return (size_t)(NSLOT0 + NSLOT1) * (RU + 4 * P) * 16 + (size_t)(NT / 32) * P * NV * 8;
+  }
+};
+
+struct RowArgs {
+  const float4* prev_in;  // phi_{n-1}
+  const float4* cur_in;   // phi_n
+  float4* prev_out;       // phi_{n+1}
+  float4* cur_out;        // phi_{n+2}
+  const float* diag;      // rescaled D_i or null
+  float dc2, th2;
+  int64_t Lx, Ly;
+  int pbc_x, pbc_y;
+  int P, logP, S;
+  int CW, BX, SY;         // tile row cells, interior cells, rows per segment
+  int nbx, nsy;           // bands, segments
+  double* partials;       // [grid][P][NV]
+  unsigned* counter;
+  double* mu;
+  int M;
+  int step0;
+};
+
+__device__ __forceinline__ float4 f4lin(float d, float4 own, float th, float4 h, float4 pv) {
+  return make_float4(d * own.x + th * h.x - pv.x, d * own.y + th * h.y - pv.y, d * own.z + th * h.z - pv.z,
+                     d * own.w + th * h.w - pv.w);
+}
+
+template <int NT_, bool HAS_DIAG, bool OPEN>
+__global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a) {
+  using RowC = RowCfg<NT_>;
+  constexpr int NT = RowC::NT, RU = RowC::RU, NV = RowC::NV, NS0 = RowC::NSLOT0, NS1 = RowC::NSLOT1;
+  extern __shared__ float4 smr[];
+  __shared__ unsigned ticket;
+  const int P = a.P, logP = a.logP, CW = a.CW, HALF = NT + 2 * P, RS = 2 * HALF;
+  float4* ring0 = smr;                                  // [NS0][RS]
+  float4* ring1 = smr + NS0 * RS;                       // [NS1][RS]
+  double* red = reinterpret_cast<double*>(smr + (NS0 + NS1) * RS);  // [warps][P][NV]
+  const int bx = blockIdx.x % a.nbx, sy = blockIdx.x / a.nbx;
+  const int64_t x0 = (int64_t)bx * a.BX;                // first interior cell
+  const int64_t ys = (int64_t)sy * a.SY;
+  const int64_t ye = ys + a.SY < a.Ly ? ys + a.SY : a.Ly;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = threadIdx.x; i < (NS0 + NS1) * RS; i += NT) smr[i] = zero;
+  for (int i = threadIdx.x; i < (NT / 32) * P * NV; i += NT) red[i] = 0.0;
+
+  // this thread's cell c and pair p; a shared row holds the A units and then the B units of the
+  // tile (each plane padded with P zero units on both sides), so a warp reads consecutive units
+  const int c = threadIdx.x >> logP, p = threadIdx.x & (P - 1);
+  const int wA = P + (int)threadIdx.x, wB = HALF + P + (int)threadIdx.x;
+  int64_t x = x0 - 1 + c;
+  bool ghx = false;
+  if (x < 0 || x >= a.Lx) {
+    if (OPEN && !a.pbc_x) ghx = true;
+    else x = x < 0 ? x + a.Lx : (x >= a.Lx ? x - a.Lx : x);
+    if (x < 0 || x >= a.Lx) ghx = true;  // a band wider than the lattice: never interior
+  }
+  const bool intx = c >= 1 && c <= CW - 2 && x0 + c - 1 < a.Lx;
+  const int64_t colA = 2 * x * P + p;                  // unit offset of A(c) within a lattice row
+  const int64_t row_units = 2 * a.Lx * P;
+  auto grow = [&](int64_t r) -> int64_t {              // wrapped lattice row, or -1 for a ghost row
+    if (r >= 0 && r < a.Ly) return r;
+    if (OPEN && !a.pbc_y) return -1;
+    return r < 0 ? r + a.Ly : r - a.Ly;
+  };
+  // ring slot of row r (r >= ys - 2: the offset keeps the C remainder non-negative)
+  auto slot0 = [&](int64_t r) -> float4* { return ring0 + (int)((r - ys + 1 + 4 * NS0) % NS0) * RS; };
+  auto slot1 = [&](int64_t r) -> float4* { return ring1 + (int)((r - ys + 1 + 4 * NS1) % NS1) * RS; };
+  auto load_row = [&](int64_t r) {  // phi_n row r into its ring slot (zero for ghosts / rows past the end)
+    const int64_t gy = (r <= ye) ? grow(r) : -1;
+    float4* dst = slot0(r);
+    const bool ok = gy >= 0 && !ghx;
+    const float4* src = ok ? a.cur_in + gy * row_units + colA : a.cur_in;
+    cp_async16(dst + wA, src, ok ? 16 : 0);
+    cp_async16(dst + wB, ok ? src + P : a.cur_in, ok ? 16 : 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto diag2 = [&](int64_t gy) -> float2 {             // 2 D of A(c) and B(c) in row gy
+    if (!HAS_DIAG) return make_float2(a.dc2, a.dc2);
+    if (gy < 0 || ghx) return make_float2(0.f, 0.f);
+    const float2 d = __ldg(reinterpret_cast<const float2*>(a.diag + 2 * (gy * a.Lx + x)));
+    return make_float2(2.f * d.x, 2.f * d.y);
+  };
+
+  float acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  int folded = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double t = (double)acc[v];
+      for (int off = 16; off >= P; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (lane < P) red[(warp * P + lane) * NV + v] += t;
+      acc[v] = 0.f;
+    }
+  };
+  auto moments = [&](int base, float4 own, float4 o) {
+    acc[base + 0] += own.x * own.x + own.y * own.y;
+    acc[base + 1] += o.x * own.x + o.y * own.y;
+    acc[base + 2] += o.x * own.y - o.y * own.x;
+    acc[base + 3] += own.z * own.z + own.w * own.w;
+    acc[base + 4] += o.z * own.z + o.w * own.w;
+    acc[base + 5] += o.z * own.w - o.w * own.z;
+  };
+
+  const float th = a.th2;
+  // prologue: rows ys-1 .. ys+PD (the first iteration reads r-1 .. r+1 = ys-2 .. ys; row ys-2 only
+  // feeds A sites of the halo row ys-1, which no interior value uses, and its slot holds zeros)
+  for (int k = -1; k <= RowC::PD; ++k) load_row(ys + k);
+  float4 pvA, pvB;  // phi_{n-1} of the row being advanced
+  {
+    const int64_t gy = grow(ys - 1);
+    const bool ok = gy >= 0 && !ghx;
+    pvA = ok ? __ldcs(a.prev_in + gy * row_units + colA) : zero;
+    pvB = ok ? __ldcs(a.prev_in + gy * row_units + colA + P) : zero;
+  }
+  float2 dPrev = make_float2(0.f, 0.f);  // 2 D of the row below (step n+2 runs one row behind)
+  for (int64_t r = ys - 1; r <= ye; ++r) {
+    // rows up to r+1 complete; rows r+2 .. r+PD may still be in flight
+    asm volatile("cp.async.wait_group %0;" ::"n"(RowC::PD - 1) : "memory");
+    __syncthreads();
+    load_row(r + RowC::PD + 1);  // overwrites row r-2, which the previous iteration used last
+    const float4* Rm = slot0(r - 1);
+    const float4* R0 = slot0(r);
+    const float4* Rp = slot0(r + 1);
+    float4* Q0 = slot1(r);
+    const int64_t gy = grow(r);
+    const bool ghost = gy < 0 || ghx;
+    // ---- step n+1 at row r: A(c) <- B(c), B(c-1), B(c, r-1);  B(c) <- A(c), A(c+1), A(c, r+1)
+    {
+      const float4 a0 = R0[wA], b0 = R0[wB];
+      const float4 hA = f4add(f4add(b0, R0[wB - P]), Rm[wB]);
+      const float4 hB = f4add(f4add(a0, R0[wA + P]), Rp[wA]);
+      const float2 d = diag2(gy);
+      float4 oA = f4lin(d.x, a0, th, hA, pvA);
+      float4 oB = f4lin(d.y, b0, th, hB, pvB);
+      if (OPEN && ghost) {
+        oA = zero;
+        oB = zero;
+      }
+      Q0[wA] = oA;
+      Q0[wB] = oB;
+      if (r >= ys && r < ye && intx) {
+        const int64_t u = gy * row_units + colA;
+        __stcs(a.prev_out + u, oA);
+        __stcs(a.prev_out + u + P, oB);
+        moments(0, a0, oA);
+        moments(0, b0, oB);
+      }
+      // phi_{n-1} of the next row, in flight during the second step
+      const int64_t gn = (r + 1 <= ye) ? grow(r + 1) : -1;
+      const bool okn = gn >= 0 && !ghx;
+      pvA = okn ? __ldcs(a.prev_in + gn * row_units + colA) : zero;
+      pvB = okn ? __ldcs(a.prev_in + gn * row_units + colA + P) : zero;
+      const float2 dq = dPrev;
+      dPrev = d;
+      __syncthreads();
+      // ---- step n+2 at row r-1
+      const int64_t q = r - 1;
+      if (q >= ys && q < ye && intx) {
+        const float4* Qm = slot1(q - 1);
+        const float4* Qc = slot1(q);
+        const float4 a1 = Qc[wA], b1 = Qc[wB];
+        const float4 gA = f4add(f4add(b1, Qc[wB - P]), Qm[wB]);
+        const float4 gB = f4add(f4add(a1, Qc[wA + P]), Q0[wA]);
+        const float4 nA = f4lin(dq.x, a1, th, gA, Rm[wA]);
+        const float4 nB = f4lin(dq.y, b1, th, gB, Rm[wB]);
+        const int64_t u = grow(q) * row_units + colA;
+        __stcs(a.cur_out + u, nA);
+        __stcs(a.cur_out + u + P, nB);
+        moments(6, a1, nA);
+        moments(6, b1, nB);
+      }
+    }
+    if (++folded == RowC::FOLD) {
+      folded = 0;
+      fold();
+    }
+  }
+  fold();
+  __syncthreads();
+  // per-CTA partials [P][NV] (warps in order), then the last CTA sums them in CTA order
+  for (int q = threadIdx.x; q < P * NV; q += NT) {
+    const int pp = q / NV, v = q - pp * NV;
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[(w * P + pp) * NV + v];
+    a.partials[(size_t)blockIdx.x * P * NV + q] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(a.counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int nval = 2 * a.S * 3;
+  for (int v = warp; v < nval; v += NT / 32) {
+    const int k = v / (a.S * 3), rem = v - k * a.S * 3, s = rem / 3, comp = rem - s * 3;
+    const int pr = s >> 1, sub = s & 1;
+    const int idx = k * 6 + sub * 3 + comp;
+    double sum = 0.0;
+    for (int t = lane; t < (int)gridDim.x; t += 32) sum += __ldcg(a.partials + ((size_t)t * P + pr) * NV + idx);
+    for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) {
+      const int j = a.step0 + k;
+      double* ms = a.mu + (size_t)s * a.M * 2;
+      if (comp == 0) {
+        ms[4 * j] = 2.0 * sum - ms[0];
+        ms[4 * j + 1] = -ms[1];
+      } else if (comp == 1) {
+        ms[4 * j + 2] = 2.0 * sum - ms[2];
+      } else {
+        ms[4 * j + 3] = 2.0 * sum - ms[3];
+      }
+    }
+  }
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
 }  // namespace fused
+
+template <int NT, bool D, bool O>
+static cudaError_t set_rows_smem() {
+  return cudaFuncSetAttribute(fused::k_fused_rows<NT, D, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fused::RowCfg<NT>::smem(16));
+}
+
+template <int NT>
+static int launch_rows(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                       const void* cur_in, void* prev_out, void* cur_out, int step0) {
+  using namespace fused;
+  using RowC = RowCfg<NT>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t e[4] = {set_rows_smem<NT, false, false>(), set_rows_smem<NT, false, true>(),
+                        set_rows_smem<NT, true, false>(), set_rows_smem<NT, true, true>()};
+    for (cudaError_t x : e)
+      if (x != cudaSuccess) attr = x;
+  });
+  TBPM_CK(attr);
+  RowArgs a;
+  memset(&a, 0, sizeof(a));
+  a.prev_in = (const float4*)prev_in;
+  a.cur_in = (const float4*)cur_in;
+  a.prev_out = (float4*)prev_out;
+  a.cur_out = (float4*)cur_out;
+  a.diag = (const float*)ra.diag;
+  a.dc2 = ra.dc2f;
+  a.th2 = ra.th2f;
+  a.Lx = lat->geom.Lx;
+  a.Ly = lat->geom.Ly;
+  a.pbc_x = lat->geom.pbc_x;
+  a.pbc_y = lat->geom.pbc_y;
+  a.P = ra.S / 2;
+  a.logP = 0;
+  while ((1 << a.logP) < a.P) ++a.logP;
+  a.S = ra.S;
+  a.CW = RowC::RU / (2 * a.P);
+  a.BX = a.CW - 2;
+  a.nbx = (int)((a.Lx + a.BX - 1) / a.BX);
+  // one wave: as many row segments as leave every resident CTA slot busy once (long segments also
+  // keep the halo-row overhead, 2 rows per segment, small)
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_rows<NT, false, false>, NT,
+                                                      RowC::smem(a.P)) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  const int64_t slots = (int64_t)ctx->num_sms * per_sm;
+  const int64_t nsy = std::max<int64_t>(1, std::min<int64_t>(a.Ly / 4 > 0 ? a.Ly / 4 : 1, slots / a.nbx));
+  a.SY = (int)((a.Ly + nsy - 1) / nsy);
+  a.nsy = (int)((a.Ly + a.SY - 1) / a.SY);
+  a.mu = ra.mu;
+  a.M = ra.M;
+  a.step0 = step0;
+  const int64_t grid = (int64_t)a.nbx * a.nsy;
+  TBPM_TRY(ensure(ctx, ctx->ws_fused_partials, sizeof(double) * RowC::NV * (size_t)a.P * (size_t)grid));
+  a.partials = (double*)ctx->ws_fused_partials.p;
+  a.counter = ra.counter;
+  const bool open = !(a.pbc_x && a.pbc_y);
+  const dim3 gr((unsigned)grid), bl(NT);
+  const size_t sm = RowC::smem(a.P);
+  if (a.diag) {
+    if (open) k_fused_rows<NT, true, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_fused_rows<NT, true, false><<<gr, bl, sm, ctx->stream>>>(a);
+  } else {
+    if (open) k_fused_rows<NT, false, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_fused_rows<NT, false, false><<<gr, bl, sm, ctx->stream>>>(a);
+  }
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
 
 bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad) {
   const Geom& g = lat->geom;
@@ -287,7 +607,7 @@ bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad) {
          g.Lx >= fused::V1::WX && g.Ly >= fused::V1::WY;
 }
 
-int fused_steps(int variant) { return variant == 2 ? fused::V2::K : fused::V1::K; }
+int fused_steps(int variant) { return variant == 1 ? fused::V1::K : 2; }
 
 template <class C, bool D, bool O>
 static cudaError_t set_smem_attr() {
@@ -348,6 +668,8 @@ static int launch_variant(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurren
 // One fused pass: steps step0 .. step0+K-1 from (prev_in, cur_in) into (prev_out, cur_out).
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant) {
+  if (variant == 3) return launch_rows<128>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+  if (variant == 4) return launch_rows<256>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 2) return launch_variant<fused::V2>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   return launch_variant<fused::V1>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
 }

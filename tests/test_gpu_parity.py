@@ -300,7 +300,7 @@ def test_full_size_graphene_sampled(capi, ctx):
     capi.tbpm_lattice_destroy(lat)
 
 
-# ---------------------------------------------------------------- temporal fusion (4 steps per pass)
+# ---------------------------------------------------------------- temporal fusion (2 or 4 steps per pass)
 
 FUSED_CASES = [
     ("honey48x32_exact_tile", dict(kind=1, L=(48, 32), t=-2.7, W=0.0), 2, 64),
@@ -309,10 +309,11 @@ FUSED_CASES = [
     ("honey90x70_open_x", dict(kind=1, L=(90, 70), t=-2.7, W=0.5, pbc=(0, 1, 1)), 4, 130),
     ("honey60x100_open_y", dict(kind=1, L=(60, 100), t=1.0, W=2.0, pbc=(1, 0, 1)), 16, 96),
     ("honey50x40_open_xy_S32", dict(kind=1, L=(50, 40), t=-2.7, W=1.0, pbc=(0, 0, 1)), 32, 38),
+    ("honey300x150_three_segments", dict(kind=1, L=(300, 150), t=-2.7, W=0.7), 8, 40),
 ]
 
 
-@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4])
 @pytest.mark.parametrize("name,spec,S,M", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
 def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode):
     lat, ol = make(capi, ctx, **spec)
