@@ -63,7 +63,7 @@ def parse():
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--fusion", type=int, default=0,
+    p.add_argument("--fusion", type=int, default=4,
                    help="moment-pass fusion mode: 0 = one step per pass, 1 = 4-step tiles, 2 = 2-step tiles, "
                         "3 = 2-step row sweep")
     p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
@@ -359,12 +359,13 @@ def run_gpu(args, work):
     per_site_step = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
     total_alg = per_site_step * (M // 2) * args.steps
     if prof["fused_launches"] > 0:
-        steps_per_launch = {1: 4, 2: 2, 3: 2, 4: 2}[args.fusion]
+        steps_per_launch = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2}[args.fusion]
         kname = (f"k_fused_cols ({steps_per_launch} Chebyshev steps per pass, complex64 state pairs)"
-                 if args.fusion in (1, 2) else "k_fused_rows (2 Chebyshev steps per pass, row sweep)")
+                 if args.fusion in (1, 2) else
+                 f"k_fused_rows ({steps_per_launch} Chebyshev steps per pass, row sweep)")
         per_launch_ms = prof["fused_ms"] / prof["fused_launches"]
         traffic_key = (f"k_fused_cols{steps_per_launch}/{work.name}" if args.fusion in (1, 2)
-                       else f"k_fused_rows/{work.name}")
+                       else f"k_fused_rows{steps_per_launch}/{work.name}")
     else:
         steps_per_launch = 1
         kname = "k_moment_stencil<honeycomb, complex64 x2 per thread>"

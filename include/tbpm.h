@@ -146,13 +146,25 @@ int tbpm_sync(tbpm_ctx* ctx);
 int64_t tbpm_launch_count(const tbpm_ctx* ctx);
 /* Temporal fusion of the moment pass (several Chebyshev steps per pass in shared memory, so
  * each state vector crosses HBM twice per pass instead of three times per step), used where a
- * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least one tile wide).
- * mode: 0 = one step per pass (default: on GB300 the one-step pass reaches ~82% of HBM
- * bandwidth while the shared-memory passes are limited by shared-memory instruction issue);
- * 1 = 4 steps per pass (2-D tiles); 2 = 2 steps per pass (2-D tiles); 3 and 4 = 2 steps per pass
- * by a row sweep (bands of cells, rows streamed through a shared-memory ring two rows ahead;
- * 128- and 256-thread CTAs).  Results agree within the complex64 tolerance. */
+ * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least 48 x 32 cells).
+ * mode: 0 = one step per pass; 1 = 4 steps per pass (2-D tiles); 2 = 2 steps per pass (2-D
+ * tiles); 3 and 4 = 2 steps per pass by a row sweep (bands of cells, rows streamed through a
+ * shared-memory ring one row ahead; 128- and 256-thread CTAs).  Default 4, the fastest measured
+ * on GB300 (honeycomb 2048 x 2048, 8 states: 1.52x the one-step pass).  Results of different
+ * modes agree within the complex64 tolerance, not bit for bit; each mode is deterministic. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
+/* mode -1 = autotuned: the first moment request on a lattice shape (kind, sizes, boundaries,
+ * path, padded S, precision, disorder) with at least 128 moments times 24 steps of each of modes
+ * 0, 3 and 4 on scratch buffers and keeps the fastest for that shape in the context.  Results of
+ * different modes agree within the complex64 tolerance, not bit for bit.
+ * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode, -1 = not timed). */
+int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[5]);
+/* CUDA graphs for the moment pass (default on): a moment request whose pass sequence (buffers,
+ * lattice, sizes, fusion mode) repeats a previous one is captured into a CUDA graph on its
+ * second occurrence and replayed from the third on, so a small lattice no longer pays one host
+ * launch per Chebyshev step.  Results are bit-identical with graphs on or off.  Phase timing
+ * (tbpm_profile) runs the passes without graphs.  enable = 0 drops the cached graphs. */
+int tbpm_set_graphs(tbpm_ctx* ctx, int enable);
 /* Memory control of the Fermi-Dirac filtered quantities (tbpm_optical_conductivity,
  * tbpm_polarization, tbpm_charge_density): their states are processed in passes of at most
  * max_states states (rounded down to a power of two; 0 = as many as fit in 85% of the free device

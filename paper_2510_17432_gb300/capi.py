@@ -111,6 +111,8 @@ def load():
                                         _P, _P]),
         "tbpm_charge_density": (C.c_int, [_P, _P, C.POINTER(Request), C.c_double, C.c_double, _P]),
         "tbpm_set_pass_states": (C.c_int, [_P, C.c_int]),
+        "tbpm_fusion_report": (C.c_int, [_P, C.POINTER(C.c_double)]),
+        "tbpm_set_graphs": (C.c_int, [_P, C.c_int]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -132,7 +134,7 @@ def exported_symbols():
             "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
-            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_fusion_report", "tbpm_set_graphs", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
 
@@ -324,6 +326,17 @@ def tbpm_polarization(ctx, lat, req: Request, q, mu: float, kT: float, omegas: n
     w = np.ascontiguousarray(omegas, dtype=np.float64)
     _check(load().tbpm_polarization(ctx, lat, C.byref(req), _host_ptr(qa), float(mu), float(kT), _host_ptr(w),
                                     int(w.size), _host_ptr(C_out), _host_ptr(Pi)))
+
+
+def tbpm_set_graphs(ctx, enable: bool):
+    _check(load().tbpm_set_graphs(ctx, int(bool(enable))))
+
+
+def tbpm_fusion_report(ctx) -> dict:
+    """ms per step of each fusion mode timed by the last autotune (mode -> ms)."""
+    out = (C.c_double * 5)()
+    _check(load().tbpm_fusion_report(ctx, out))
+    return {m: out[m] for m in range(5) if out[m] >= 0.0}
 
 
 def tbpm_set_pass_states(ctx, max_states: int):

@@ -378,6 +378,8 @@ int tbpm_destroy(tbpm_ctx* ctx) {
                     &ctx->ws_jpsi, &ctx->ws_ec, &ctx->ws_fermi};
   for (DevBuf* b : bufs) release(ctx, *b);
   cudaStreamSynchronize(ctx->stream);
+  for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  ctx->graphs.clear();
   for (auto& ph : ctx->phases) {
     cudaEventDestroy(ph.a);
     cudaEventDestroy(ph.b);
@@ -409,11 +411,38 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     set_error("tbpm_set_fusion: ctx is NULL");
     return TBPM_EINVAL;
   }
-  if (enable < 0 || enable > 4) {
-    set_error("tbpm_set_fusion: mode %d unknown (0..4)", enable);
+  if (enable < -1 || enable > 7) {
+    set_error("tbpm_set_fusion: mode %d unknown (-1..7)", enable);
     return TBPM_EINVAL;
   }
   ctx->fusion = enable;
+  return TBPM_OK;
+}
+
+int tbpm_set_graphs(tbpm_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_set_graphs: ctx is NULL");
+    return TBPM_EINVAL;
+  }
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->use_graphs = enable != 0;
+  if (!ctx->use_graphs) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+    ctx->graph_seen.clear();
+  }
+  return TBPM_OK;
+}
+
+int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[5]) {
+  clear_error();
+  if (!ctx || !ms_per_step) {
+    set_error("tbpm_fusion_report: invalid argument");
+    return TBPM_EINVAL;
+  }
+  for (int m = 0; m < 5; ++m) ms_per_step[m] = -1.0;
+  for (auto& t : ctx->fusion_timings) ms_per_step[t.first] = t.second;
   return TBPM_OK;
 }
 
@@ -821,6 +850,79 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
   return TBPM_OK;
 }
 
+// Fusion mode for a moment request: ctx->fusion, or under -1 the fastest mode measured on this
+// lattice shape (a few passes of each applicable mode on scratch buffers; cached per shape).
+int choose_fusion(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t M, int* mode) {
+  if (ctx->fusion >= 0) {
+    *mode = ctx->fusion;
+    return TBPM_OK;
+  }
+  *mode = 0;
+  if (!fused_applicable(lat, pl.precision, pl.Spad) || M / 2 < 64) return TBPM_OK;
+  const Geom& g = lat->geom;
+  const std::vector<int64_t> key = {g.kind, g.Lx, g.Ly, g.Lz, g.pbc_x | (g.pbc_y << 1) | (g.pbc_z << 2), lat->path,
+                                    pl.Spad, pl.precision, lat->has_v ? 1 : 0};
+  for (auto& kv : ctx->fusion_choice)
+    if (kv.first == key) {
+      *mode = kv.second;
+      return TBPM_OK;
+    }
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
+  TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pl.state_bytes));
+  const int Ms = 64;  // scratch moments: steps 1 .. 31
+  TBPM_TRY(ensure(ctx, ctx->ws_aux, sizeof(double) * 2 * (size_t)Ms * pl.Spad));
+  TBPM_CK(cudaMemsetAsync(ctx->ws_aux.p, 0, sizeof(double) * 2 * (size_t)Ms * pl.Spad, ctx->stream));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+  TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[1].p, nullptr));
+  RecurrenceArgs a;
+  TBPM_TRY(base_args(ctx, lat, pl, &a, 3));
+  a.mu = (double*)ctx->ws_aux.p;
+  a.M = Ms;
+  cudaEvent_t e0, e1;
+  TBPM_CK(cudaEventCreate(&e0));
+  TBPM_CK(cudaEventCreate(&e1));
+  const int modes[] = {0, 3, 4};
+  double best_ms = 1e300;
+  ctx->fusion_timings.clear();
+  int r = TBPM_OK;
+  for (int m : modes) {
+    const int K = m == 0 ? 1 : fused_steps(m);
+    const int passes = 24 / K;  // 24 steps per measurement, after 8 warm-up steps
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && r == TBPM_OK; ++rep) {
+      const int np = rep == 0 ? 8 / K : passes;
+      if (rep == 1) cudaEventRecord(e0, ctx->stream);
+      for (int i = 0; i < np && r == TBPM_OK; ++i) {
+        if (m == 0) {
+          a.cur = ctx->ws_phi[0].p;
+          a.prev_out = ctx->ws_phi[1].p;
+          a.step = 1 + (i % 16);
+          r = launch_moment_step(ctx, a, pl.precision, false);
+        } else {
+          r = launch_fused_pass(ctx, lat, a, ctx->ws_phi[0].p, ctx->ws_phi[1].p, ctx->ws_phi2[0].p, ctx->ws_phi2[1].p,
+                                1 + (i % 8) * K, m);
+        }
+      }
+      if (rep == 1) cudaEventRecord(e1, ctx->stream);
+    }
+    if (r != TBPM_OK) break;
+    if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    const double per_step = ms / 24.0;
+    ctx->fusion_timings.push_back({m, per_step});
+    if (per_step < best_ms) {
+      best_ms = per_step;
+      *mode = m;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TBPM_TRY(r);
+  ctx->fusion_choice.push_back({key, *mode});
+  return TBPM_OK;
+}
+
 // Moments of all Spad states into d_mu [Spad][M][2].
 int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t M,
                 double* d_mu) {
@@ -835,43 +937,105 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
   TBPM_TRY(base_args(ctx, lat, pl, &a, 3));
   a.mu = d_mu;
   a.M = (int)M;
-  const int tok = phase_begin(ctx, 0);
-  // step n reads cur = phi_n, overwrites prev (phi_{n-1}) with phi_{n+1}; then the roles swap
-  void* cur = ctx->ws_phi[0].p;
-  void* prev = ctx->ws_phi[1].p;
-  int64_t n = 0;
-  const int K = fused_steps(ctx->fusion);
-  const bool fuse = ctx->fusion > 0 && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= K;
+  int fmode = 0;
+  TBPM_TRY(choose_fusion(ctx, lat, req, pl, M, &fmode));
+  const int K = fused_steps(fmode);
+  const bool fuse = fmode > 0 && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= K;
   if (fuse) {
     TBPM_TRY(ensure(ctx, ctx->ws_phi2[0], pl.state_bytes));
     TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pl.state_bytes));
   }
-  auto unfused = [&]() -> int {
-    a.cur = cur;
-    a.prev_out = prev;
-    a.step = (int)n;
-    TBPM_TRY(launch_moment_step(ctx, a, pl.precision, n == 0));
-    std::swap(cur, prev);
-    ++n;
+  // the pass sequence: step n reads cur = phi_n and overwrites prev (phi_{n-1}) with phi_{n+1}
+  auto body = [&]() -> int {
+    void* cur = ctx->ws_phi[0].p;
+    void* prev = ctx->ws_phi[1].p;
+    int64_t n = 0;
+    auto unfused = [&]() -> int {
+      a.cur = cur;
+      a.prev_out = prev;
+      a.step = (int)n;
+      TBPM_TRY(launch_moment_step(ctx, a, pl.precision, n == 0));
+      std::swap(cur, prev);
+      ++n;
+      return TBPM_OK;
+    };
+    TBPM_TRY(unfused());  // phi_1 = H~ phi_0, m_0, m_1
+    if (fuse) {
+      const int ftok = phase_begin(ctx, 2);
+      void* pair_out[2] = {ctx->ws_phi2[0].p, ctx->ws_phi2[1].p};
+      while (n + K <= M / 2) {
+        TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n, fmode));
+        void* old_prev = prev;
+        void* old_cur = cur;
+        prev = pair_out[0];
+        cur = pair_out[1];
+        pair_out[0] = old_prev;
+        pair_out[1] = old_cur;
+        n += K;
+      }
+      phase_end(ctx, ftok);
+    }
+    while (n < M / 2) TBPM_TRY(unfused());
     return TBPM_OK;
   };
-  TBPM_TRY(unfused());  // phi_1 = H~ phi_0, m_0, m_1
-  if (fuse) {
-    const int ftok = phase_begin(ctx, 2);
-    void* pair_out[2] = {ctx->ws_phi2[0].p, ctx->ws_phi2[1].p};
-    while (n + K <= M / 2) {
-      TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n, ctx->fusion));
-      void* old_prev = prev;
-      void* old_cur = cur;
-      prev = pair_out[0];
-      cur = pair_out[1];
-      pair_out[0] = old_prev;
-      pair_out[1] = old_cur;
-      n += K;
+  const int tok = phase_begin(ctx, 0);
+  if (!ctx->use_graphs || ctx->profiling) {
+    TBPM_TRY(body());
+  } else {
+    auto bits = [](double v) {
+      uint64_t u;
+      memcpy(&u, &v, 8);
+      return u;
+    };
+    const Geom& g = lat->geom;
+    const std::vector<uint64_t> key = {
+        (uint64_t)ctx->ws_phi[0].p, (uint64_t)ctx->ws_phi[1].p, (uint64_t)ctx->ws_phi2[0].p,
+        (uint64_t)ctx->ws_phi2[1].p, (uint64_t)d_mu, (uint64_t)lat, (uint64_t)lat->d32, (uint64_t)lat->d64,
+        (uint64_t)lat->ell, (uint64_t)a.partials, (uint64_t)a.counter, (uint64_t)ctx->ws_fused_partials.p,
+        (uint64_t)M, (uint64_t)fmode, (uint64_t)pl.precision, (uint64_t)pl.Spad, bits(a.thop), bits(a.diag_const),
+        (uint64_t)g.Lx, (uint64_t)g.Ly, (uint64_t)g.Lz, (uint64_t)g.kind,
+        (uint64_t)(g.pbc_x | (g.pbc_y << 1) | (g.pbc_z << 2)), (uint64_t)lat->path, (uint64_t)lat->n_sites};
+    tbpm_ctx::Graph* hit = nullptr;
+    for (auto& e : ctx->graphs)
+      if (e.key == key) hit = &e;
+    if (!hit) {
+      bool seen = false;
+      for (auto& k : ctx->graph_seen) seen = seen || k == key;
+      if (!seen) {
+        // first time: run eagerly (this also sizes every workspace the sequence touches)
+        if (ctx->graph_seen.size() >= 16) ctx->graph_seen.erase(ctx->graph_seen.begin());
+        ctx->graph_seen.push_back(key);
+        TBPM_TRY(body());
+      } else {
+        cudaGraph_t graph = nullptr;
+        const int64_t l0 = ctx->launches;
+        TBPM_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const int r = body();
+        const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
+        const int64_t kernels = ctx->launches - l0;
+        ctx->launches = l0;
+        if (r != TBPM_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return r;
+        }
+        TBPM_CK(ec);
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TBPM_CK(ei);
+        if (ctx->graphs.size() >= 8) {
+          cudaGraphExecDestroy(ctx->graphs.front().exec);
+          ctx->graphs.erase(ctx->graphs.begin());
+        }
+        ctx->graphs.push_back({key, exec, kernels});
+        hit = &ctx->graphs.back();
+      }
     }
-    phase_end(ctx, ftok);
+    if (hit) {
+      TBPM_CK(cudaGraphLaunch(hit->exec, ctx->stream));
+      ctx->launches += hit->kernels;
+    }
   }
-  while (n < M / 2) TBPM_TRY(unfused());
   phase_end(ctx, tok);
   return TBPM_OK;
 }

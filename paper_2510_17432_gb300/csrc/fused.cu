@@ -370,12 +370,10 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
     if (OPEN && !a.pbc_y) return -1;
     return r < 0 ? r + a.Ly : r - a.Ly;
   };
-  // ring slot of row r (r >= ys - 2: the offset keeps the C remainder non-negative)
-  auto slot0 = [&](int64_t r) -> float4* { return ring0 + (int)((r - ys + 1 + 4 * NS0) % NS0) * RS; };
-  auto slot1 = [&](int64_t r) -> float4* { return ring1 + (int)((r - ys + 1 + 4 * NS1) % NS1) * RS; };
-  auto load_row = [&](int64_t r) {  // phi_n row r into its ring slot (zero for ghosts / rows past the end)
+  // ring slots: tile row ys-1+k lives in ring0 slot k % NS0 and ring1 slot k % NS1
+  auto load_row = [&](int64_t r, int slot) {  // phi_n row r (zero for ghosts / rows past the end)
     const int64_t gy = (r <= ye) ? grow(r) : -1;
-    float4* dst = slot0(r);
+    float4* dst = ring0 + slot * RS;
     const bool ok = gy >= 0 && !ghx;
     const float4* src = ok ? a.cur_in + gy * row_units + colA : a.cur_in;
     cp_async16(dst + wA, src, ok ? 16 : 0);
@@ -393,28 +391,30 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.f;
   int folded = 0;
+  // every FOLD rows: each thread's FP32 partials (32 unit terms) are summed over the lanes of its
+  // pair by a fixed FP32 tree and added in FP64 to the warp's slot
   auto fold = [&]() {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      double t = (double)acc[v];
+      float t = acc[v];
       for (int off = 16; off >= P; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      if (lane < P) red[(warp * P + lane) * NV + v] += t;
+      if (lane < P) red[(warp * P + lane) * NV + v] += (double)t;
       acc[v] = 0.f;
     }
   };
-  auto moments = [&](int base, float4 own, float4 o) {
-    acc[base + 0] += own.x * own.x + own.y * own.y;
-    acc[base + 1] += o.x * own.x + o.y * own.y;
-    acc[base + 2] += o.x * own.y - o.y * own.x;
-    acc[base + 3] += own.z * own.z + own.w * own.w;
-    acc[base + 4] += o.z * own.z + o.w * own.w;
-    acc[base + 5] += o.z * own.w - o.w * own.z;
+  auto moments = [&](int base, float4 own, float4 o) {  // FFMA chains into the FP32 partials
+    acc[base + 0] = fmaf(own.x, own.x, fmaf(own.y, own.y, acc[base + 0]));
+    acc[base + 1] = fmaf(o.x, own.x, fmaf(o.y, own.y, acc[base + 1]));
+    acc[base + 2] = fmaf(o.x, own.y, fmaf(-o.y, own.x, acc[base + 2]));
+    acc[base + 3] = fmaf(own.z, own.z, fmaf(own.w, own.w, acc[base + 3]));
+    acc[base + 4] = fmaf(o.z, own.z, fmaf(o.w, own.w, acc[base + 4]));
+    acc[base + 5] = fmaf(o.z, own.w, fmaf(-o.w, own.z, acc[base + 5]));
   };
 
   const float th = a.th2;
-  // prologue: rows ys-1 .. ys+PD (the first iteration reads r-1 .. r+1 = ys-2 .. ys; row ys-2 only
+  // prologue: rows ys-1 .. ys-1+PD (the first iteration reads r-1 .. r+1 = ys-2 .. ys; row ys-2 only
   // feeds A sites of the halo row ys-1, which no interior value uses, and its slot holds zeros)
-  for (int k = -1; k <= RowC::PD; ++k) load_row(ys + k);
+  for (int k = 0; k <= RowC::PD; ++k) load_row(ys - 1 + k, k);
   float4 pvA, pvB;  // phi_{n-1} of the row being advanced
   {
     const int64_t gy = grow(ys - 1);
@@ -423,15 +423,19 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
     pvB = ok ? __ldcs(a.prev_in + gy * row_units + colA + P) : zero;
   }
   float2 dPrev = make_float2(0.f, 0.f);  // 2 D of the row below (step n+2 runs one row behind)
+  int k0 = 0, k1 = 0;                    // ring0 / ring1 slots of row r
   for (int64_t r = ys - 1; r <= ye; ++r) {
     // rows up to r+1 complete; rows r+2 .. r+PD may still be in flight
     asm volatile("cp.async.wait_group %0;" ::"n"(RowC::PD - 1) : "memory");
     __syncthreads();
-    load_row(r + RowC::PD + 1);  // overwrites row r-2, which the previous iteration used last
-    const float4* Rm = slot0(r - 1);
-    const float4* R0 = slot0(r);
-    const float4* Rp = slot0(r + 1);
-    float4* Q0 = slot1(r);
+    const int km1 = k0 == 0 ? NS0 - 1 : k0 - 1;   // row r-1
+    const int kp1 = k0 == NS0 - 1 ? 0 : k0 + 1;   // row r+1
+    const int km2 = km1 == 0 ? NS0 - 1 : km1 - 1; // row r-2 = row r+PD+1 (NS0 = PD+3)
+    load_row(r + RowC::PD + 1, km2);              // the previous iteration used row r-2 last
+    const float4* Rm = ring0 + km1 * RS;
+    const float4* R0 = ring0 + k0 * RS;
+    const float4* Rp = ring0 + kp1 * RS;
+    float4* Q0 = ring1 + k1 * RS;
     const int64_t gy = grow(r);
     const bool ghost = gy < 0 || ghx;
     // ---- step n+1 at row r: A(c) <- B(c), B(c-1), B(c, r-1);  B(c) <- A(c), A(c+1), A(c, r+1)
@@ -463,11 +467,11 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
       const float2 dq = dPrev;
       dPrev = d;
       __syncthreads();
-      // ---- step n+2 at row r-1
+      // ---- step n+2 at row q = r-1 from phi_{n+1} rows q-1, q, q+1 = r and phi_n(q)
       const int64_t q = r - 1;
       if (q >= ys && q < ye && intx) {
-        const float4* Qm = slot1(q - 1);
-        const float4* Qc = slot1(q);
+        const float4* Qc = ring1 + (k1 == 0 ? 2 : k1 - 1) * RS;  // row r-1
+        const float4* Qm = ring1 + (k1 == 2 ? 0 : k1 + 1) * RS;  // row r-2
         const float4 a1 = Qc[wA], b1 = Qc[wB];
         const float4 gA = f4add(f4add(b1, Qc[wB - P]), Qm[wB]);
         const float4 gB = f4add(f4add(a1, Qc[wA + P]), Q0[wA]);
@@ -484,6 +488,8 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
       folded = 0;
       fold();
     }
+    k0 = kp1;
+    k1 = k1 == 2 ? 0 : k1 + 1;
   }
   fold();
   __syncthreads();
@@ -501,6 +507,229 @@ __global__ void __launch_bounds__(NT_, RowCfg<NT_>::MINB) k_fused_rows(RowArgs a
   if (ticket != gridDim.x - 1) return;
   __threadfence();
   const int nval = 2 * a.S * 3;
+  for (int v = warp; v < nval; v += NT / 32) {
+    const int k = v / (a.S * 3), rem = v - k * a.S * 3, s = rem / 3, comp = rem - s * 3;
+    const int pr = s >> 1, sub = s & 1;
+    const int idx = k * 6 + sub * 3 + comp;
+    double sum = 0.0;
+    for (int t = lane; t < (int)gridDim.x; t += 32) sum += __ldcg(a.partials + ((size_t)t * P + pr) * NV + idx);
+    for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) {
+      const int j = a.step0 + k;
+      double* ms = a.mu + (size_t)s * a.M * 2;
+      if (comp == 0) {
+        ms[4 * j] = 2.0 * sum - ms[0];
+        ms[4 * j + 1] = -ms[1];
+      } else if (comp == 1) {
+        ms[4 * j + 2] = 2.0 * sum - ms[2];
+      } else {
+        ms[4 * j + 3] = 2.0 * sum - ms[3];
+      }
+    }
+  }
+  if (threadIdx.x == 0) *a.counter = 0u;
+}
+
+// ------------------------------------------------------------------ row sweep, K steps per pass
+// The same sweep with K (even) levels: at tile row r level L forms phi_{n+L} at row r - (L-1) from
+// level L-1's ring (rows r-L .. r-L+2) and phi_{n+L-2} at that row (level L-2's ring, phi_n's ring
+// for L = 2, registers for L = 1).  Levels 1 .. K-1 keep three-row rings; levels K-1 and K go to
+// HBM.  The exact region shrinks by one cell / row per two steps, so the tile carries K/2 halo
+// cells on each side and the segment K/2 halo rows below and above.
+template <int NT_, int K_>
+struct RowKCfg {
+  static constexpr int NT = NT_, K = K_, H = K_ / 2;
+  static constexpr int RU = 2 * NT;
+  static constexpr int PD = 1;
+  static constexpr int NSLOT0 = PD + 3;
+  static constexpr int NV = 6 * K;
+  static constexpr int FOLD = 16;
+  static constexpr int MINB = K == 2 ? (NT >= 256 ? 3 : 6) : (NT >= 256 ? 2 : 4);
+  static size_t smem(int P) {
+    return (size_t)(NSLOT0 + 3 * (K - 1)) * (RU + 4 * P) * 16 + (size_t)(NT / 32) * P * NV * 8;
+  }
+};
+
+template <int NT_, int K_, bool HAS_DIAG, bool OPEN>
+__global__ void __launch_bounds__(NT_, RowKCfg<NT_, K_>::MINB) k_fused_rowsK(RowArgs a) {
+  using RC = RowKCfg<NT_, K_>;
+  constexpr int NT = RC::NT, K = RC::K, H = RC::H, RU = RC::RU, NV = RC::NV, NS0 = RC::NSLOT0;
+  extern __shared__ float4 smr[];
+  __shared__ unsigned ticket;
+  const int P = a.P, logP = a.logP, CW = a.CW, HALF = NT + 2 * P, RS = 2 * HALF;
+  float4* ring0 = smr;                                   // [NS0][RS]
+  float4* ringL = smr + NS0 * RS;                        // [K-1][3][RS]: level L at ringL + (L-1)*3*RS
+  double* red = reinterpret_cast<double*>(smr + (NS0 + 3 * (K - 1)) * RS);  // [warps][P][NV]
+  const int bx = blockIdx.x % a.nbx, sy = blockIdx.x / a.nbx;
+  const int64_t x0 = (int64_t)bx * a.BX;
+  const int64_t ys = (int64_t)sy * a.SY;
+  const int64_t ye = ys + a.SY < a.Ly ? ys + a.SY : a.Ly;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = threadIdx.x; i < (NS0 + 3 * (K - 1)) * RS; i += NT) smr[i] = zero;
+  for (int i = threadIdx.x; i < (NT / 32) * P * NV; i += NT) red[i] = 0.0;
+
+  const int c = threadIdx.x >> logP, p = threadIdx.x & (P - 1);
+  const int wA = P + (int)threadIdx.x, wB = HALF + P + (int)threadIdx.x;
+  int64_t x = x0 - H + c;
+  bool ghx = false;
+  if (x < 0 || x >= a.Lx) {
+    if (OPEN && !a.pbc_x) ghx = true;
+    else x = x < 0 ? x + a.Lx : (x >= a.Lx ? x - a.Lx : x);
+    if (x < 0 || x >= a.Lx) ghx = true;
+  }
+  const bool intx = c >= H && c < CW - H && x0 + c - H < a.Lx;
+  const int64_t colA = 2 * x * P + p;
+  const int64_t row_units = 2 * a.Lx * P;
+  const int64_t r0 = ys - H;                  // first tile row; tile row r0+k: ring0 slot k % NS0, ring slot k % 3
+  const int64_t rlast_load = ye + H - 1;      // last phi_n row that any exact value needs
+  auto grow = [&](int64_t r) -> int64_t {
+    if (r >= 0 && r < a.Ly) return r;
+    if (OPEN && !a.pbc_y) return -1;
+    return r < 0 ? r + a.Ly : r - a.Ly;
+  };
+  auto load_row = [&](int64_t r, int slot) {
+    const int64_t gy = (r <= rlast_load) ? grow(r) : -1;
+    float4* dst = ring0 + slot * RS;
+    const bool ok = gy >= 0 && !ghx;
+    const float4* src = ok ? a.cur_in + gy * row_units + colA : a.cur_in;
+    cp_async16(dst + wA, src, ok ? 16 : 0);
+    cp_async16(dst + wB, ok ? src + P : a.cur_in, ok ? 16 : 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  auto diag2 = [&](int64_t gy) -> float2 {
+    if (!HAS_DIAG) return make_float2(a.dc2, a.dc2);
+    if (gy < 0 || ghx) return make_float2(0.f, 0.f);
+    const float2 d = __ldg(reinterpret_cast<const float2*>(a.diag + 2 * (gy * a.Lx + x)));
+    return make_float2(2.f * d.x, 2.f * d.y);
+  };
+  float acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  int folded = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float t = acc[v];
+      for (int off = 16; off >= P; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (lane < P) red[(warp * P + lane) * NV + v] += (double)t;
+      acc[v] = 0.f;
+    }
+  };
+  auto moments = [&](int base, float4 own, float4 o) {
+    acc[base + 0] = fmaf(own.x, own.x, fmaf(own.y, own.y, acc[base + 0]));
+    acc[base + 1] = fmaf(o.x, own.x, fmaf(o.y, own.y, acc[base + 1]));
+    acc[base + 2] = fmaf(o.x, own.y, fmaf(-o.y, own.x, acc[base + 2]));
+    acc[base + 3] = fmaf(own.z, own.z, fmaf(own.w, own.w, acc[base + 3]));
+    acc[base + 4] = fmaf(o.z, own.z, fmaf(o.w, own.w, acc[base + 4]));
+    acc[base + 5] = fmaf(o.z, own.w, fmaf(-o.w, own.z, acc[base + 5]));
+  };
+
+  const float th = a.th2;
+  for (int k = 0; k <= RC::PD; ++k) load_row(r0 + k, k);
+  float4 pvA, pvB;
+  {
+    const int64_t gy = grow(r0);
+    const bool ok = gy >= 0 && !ghx && r0 <= rlast_load;
+    pvA = ok ? __ldcs(a.prev_in + gy * row_units + colA) : zero;
+    pvB = ok ? __ldcs(a.prev_in + gy * row_units + colA + P) : zero;
+  }
+  float2 dRow[K];  // 2 D of rows r, r-1, .., r-K+1
+#pragma unroll
+  for (int l = 0; l < K; ++l) dRow[l] = make_float2(0.f, 0.f);
+  int k0 = 0, k1 = 0;  // ring0 / level-ring slots of row r
+  const int64_t r_end = ye + K - 2;
+  for (int64_t r = r0; r <= r_end; ++r) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(RC::PD - 1) : "memory");
+    __syncthreads();
+    const int km1 = k0 == 0 ? NS0 - 1 : k0 - 1;
+    const int kp1 = k0 == NS0 - 1 ? 0 : k0 + 1;
+    const int km2 = km1 == 0 ? NS0 - 1 : km1 - 1;
+    load_row(r + RC::PD + 1, km2);
+#pragma unroll
+    for (int l = K - 1; l > 0; --l) dRow[l] = dRow[l - 1];
+    dRow[0] = diag2(grow(r));
+    // ring slot (0..2) of row r - j
+    auto rs = [&](int j) -> int { return (k1 - j + 6) % 3; };
+#pragma unroll
+    for (int L = 1; L <= K; ++L) {
+      const int64_t q = r - (L - 1);
+      const int64_t gq = grow(q);
+      const bool ghost = gq < 0 || ghx;
+      float4 own_a, own_b, nA, nB;
+      if (L == 1) {
+        const float4* Rm = ring0 + km1 * RS;
+        const float4* R0 = ring0 + k0 * RS;
+        const float4* Rp = ring0 + kp1 * RS;
+        own_a = R0[wA];
+        own_b = R0[wB];
+        const float4 hA = f4add(f4add(own_b, R0[wB - P]), Rm[wB]);
+        const float4 hB = f4add(f4add(own_a, R0[wA + P]), Rp[wA]);
+        nA = f4lin(dRow[0].x, own_a, th, hA, pvA);
+        nB = f4lin(dRow[0].y, own_b, th, hB, pvB);
+      } else {
+        const float4* In = ringL + (L - 2) * 3 * RS;      // level L-1
+        const float4* Qm = In + rs(L) * RS;               // row q-1 = r-L
+        const float4* Qc = In + rs(L - 1) * RS;           // row q
+        const float4* Qp = In + rs(L - 2) * RS;           // row q+1
+        const float4* Pv = (L == 2) ? ring0 + km1 * RS : ringL + (L - 3) * 3 * RS + rs(L - 1) * RS;
+        own_a = Qc[wA];
+        own_b = Qc[wB];
+        const float4 gA = f4add(f4add(own_b, Qc[wB - P]), Qm[wB]);
+        const float4 gB = f4add(f4add(own_a, Qc[wA + P]), Qp[wA]);
+        nA = f4lin(dRow[L - 1].x, own_a, th, gA, Pv[wA]);
+        nB = f4lin(dRow[L - 1].y, own_b, th, gB, Pv[wB]);
+      }
+      if (OPEN && ghost) {
+        nA = zero;
+        nB = zero;
+      }
+      if (L < K) {
+        float4* Out = ringL + (L - 1) * 3 * RS + rs(L - 1) * RS;
+        Out[wA] = nA;
+        Out[wB] = nB;
+      }
+      const bool inside = q >= ys && q < ye && intx;
+      if (inside) {
+        if (L >= K - 1) {
+          float4* dst = (L == K - 1) ? a.prev_out : a.cur_out;
+          const int64_t u = gq * row_units + colA;
+          __stcs(dst + u, nA);
+          __stcs(dst + u + P, nB);
+        }
+        moments((L - 1) * 6, own_a, nA);
+        moments((L - 1) * 6, own_b, nB);
+      }
+      if (L == 1) {  // phi_{n-1} of the next row, in flight during the later levels
+        const int64_t gn = (r + 1 <= rlast_load) ? grow(r + 1) : -1;
+        const bool okn = gn >= 0 && !ghx;
+        pvA = okn ? __ldcs(a.prev_in + gn * row_units + colA) : zero;
+        pvB = okn ? __ldcs(a.prev_in + gn * row_units + colA + P) : zero;
+      }
+      if (L < K) __syncthreads();
+    }
+    if (++folded == RC::FOLD) {
+      folded = 0;
+      fold();
+    }
+    k0 = kp1;
+    k1 = k1 == 2 ? 0 : k1 + 1;
+  }
+  fold();
+  __syncthreads();
+  for (int q = threadIdx.x; q < P * NV; q += NT) {
+    const int pp = q / NV, v = q - pp * NV;
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[(w * P + pp) * NV + v];
+    a.partials[(size_t)blockIdx.x * P * NV + q] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) ticket = atomicAdd(a.counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int nval = K * a.S * 3;
   for (int v = warp; v < nval; v += NT / 32) {
     const int k = v / (a.S * 3), rem = v - k * a.S * 3, s = rem / 3, comp = rem - s * 3;
     const int pr = s >> 1, sub = s & 1;
@@ -576,8 +805,23 @@ static int launch_rows(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceA
       per_sm = 1;
     }
   }
+  // segments per band: the count whose CTAs fill the resident slots best over whole waves, weighed
+  // by what each segment adds (one wave when it fits, e.g. 2048 x 2048)
   const int64_t slots = (int64_t)ctx->num_sms * per_sm;
-  const int64_t nsy = std::max<int64_t>(1, std::min<int64_t>(a.Ly / 4 > 0 ? a.Ly / 4 : 1, slots / a.nbx));
+  const int64_t max_nsy = std::max<int64_t>(1, std::min<int64_t>(a.Ly / 4, 8 * slots / a.nbx + 1));
+  int64_t nsy = 1;
+  double best = -1.0;
+  for (int64_t k = 1; k <= max_nsy; ++k) {
+    const int64_t sy = (a.Ly + k - 1) / k;
+    const int64_t ctas = a.nbx * ((a.Ly + sy - 1) / sy);
+    const int64_t waves = (ctas + slots - 1) / slots;
+    // a segment costs its two halo rows plus the fill and drain of the row pipeline (~6 rows)
+    const double eff = (double)ctas / (double)(waves * slots) * (double)sy / (double)(sy + 8);
+    if (eff > best + 1e-9) {
+      best = eff;
+      nsy = k;
+    }
+  }
   a.SY = (int)((a.Ly + nsy - 1) / nsy);
   a.nsy = (int)((a.Ly + a.SY - 1) / a.SY);
   a.mu = ra.mu;
@@ -601,13 +845,102 @@ static int launch_rows(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceA
   return TBPM_OK;
 }
 
+template <int NT, int K, bool D, bool O>
+static cudaError_t set_rowsK_smem() {
+  return cudaFuncSetAttribute(fused::k_fused_rowsK<NT, K, D, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fused::RowKCfg<NT, K>::smem(16));
+}
+
+template <int NT, int K>
+static int launch_rowsK(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                        const void* cur_in, void* prev_out, void* cur_out, int step0) {
+  using namespace fused;
+  using RC = RowKCfg<NT, K>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t e[4] = {set_rowsK_smem<NT, K, false, false>(), set_rowsK_smem<NT, K, false, true>(),
+                        set_rowsK_smem<NT, K, true, false>(), set_rowsK_smem<NT, K, true, true>()};
+    for (cudaError_t x : e)
+      if (x != cudaSuccess) attr = x;
+  });
+  TBPM_CK(attr);
+  RowArgs a;
+  memset(&a, 0, sizeof(a));
+  a.prev_in = (const float4*)prev_in;
+  a.cur_in = (const float4*)cur_in;
+  a.prev_out = (float4*)prev_out;
+  a.cur_out = (float4*)cur_out;
+  a.diag = (const float*)ra.diag;
+  a.dc2 = ra.dc2f;
+  a.th2 = ra.th2f;
+  a.Lx = lat->geom.Lx;
+  a.Ly = lat->geom.Ly;
+  a.pbc_x = lat->geom.pbc_x;
+  a.pbc_y = lat->geom.pbc_y;
+  a.P = ra.S / 2;
+  a.logP = 0;
+  while ((1 << a.logP) < a.P) ++a.logP;
+  a.S = ra.S;
+  a.CW = RC::RU / (2 * a.P);
+  a.BX = a.CW - 2 * RC::H;
+  if (a.BX < 1) {
+    set_error("fused pass: tile too narrow for %d states", a.S);
+    return TBPM_EUNSUPPORTED;
+  }
+  a.nbx = (int)((a.Lx + a.BX - 1) / a.BX);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_rowsK<NT, K, false, false>, NT,
+                                                      RC::smem(a.P)) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  const int64_t slots = (int64_t)ctx->num_sms * per_sm;
+  const int64_t max_nsy = std::max<int64_t>(1, std::min<int64_t>(a.Ly / 4, 8 * slots / a.nbx + 1));
+  int64_t nsy = 1;
+  double best = -1.0;
+  for (int64_t k = 1; k <= max_nsy; ++k) {
+    const int64_t sy = (a.Ly + k - 1) / k;
+    const int64_t ctas = a.nbx * ((a.Ly + sy - 1) / sy);
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots) * (double)sy / (double)(sy + K + 6);
+    if (eff > best + 1e-9) {
+      best = eff;
+      nsy = k;
+    }
+  }
+  a.SY = (int)((a.Ly + nsy - 1) / nsy);
+  a.nsy = (int)((a.Ly + a.SY - 1) / a.SY);
+  a.mu = ra.mu;
+  a.M = ra.M;
+  a.step0 = step0;
+  const int64_t grid = (int64_t)a.nbx * a.nsy;
+  TBPM_TRY(ensure(ctx, ctx->ws_fused_partials, sizeof(double) * RC::NV * (size_t)a.P * (size_t)grid));
+  a.partials = (double*)ctx->ws_fused_partials.p;
+  a.counter = ra.counter;
+  const bool open = !(a.pbc_x && a.pbc_y);
+  const dim3 gr((unsigned)grid), bl(NT);
+  const size_t sm = RC::smem(a.P);
+  if (a.diag) {
+    if (open) k_fused_rowsK<NT, K, true, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_fused_rowsK<NT, K, true, false><<<gr, bl, sm, ctx->stream>>>(a);
+  } else {
+    if (open) k_fused_rowsK<NT, K, false, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_fused_rowsK<NT, K, false, false><<<gr, bl, sm, ctx->stream>>>(a);
+  }
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
 bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad) {
   const Geom& g = lat->geom;
   return lat->path == TBPM_PATH_STENCIL && g.kind == TBPM_HONEYCOMB && precision == TBPM_C64 && Spad >= 2 &&
          g.Lx >= fused::V1::WX && g.Ly >= fused::V1::WY;
 }
 
-int fused_steps(int variant) { return variant == 1 ? fused::V1::K : 2; }
+int fused_steps(int variant) { return (variant == 1 || variant == 5 || variant == 6) ? 4 : 2; }
 
 template <class C, bool D, bool O>
 static cudaError_t set_smem_attr() {
@@ -668,6 +1001,9 @@ static int launch_variant(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurren
 // One fused pass: steps step0 .. step0+K-1 from (prev_in, cur_in) into (prev_out, cur_out).
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant) {
+  if (variant == 5) return launch_rowsK<128, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+  if (variant == 6) return launch_rowsK<256, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+  if (variant == 7) return launch_rowsK<256, 2>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 3) return launch_rows<128>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 4) return launch_rows<256>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 2) return launch_variant<fused::V2>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);

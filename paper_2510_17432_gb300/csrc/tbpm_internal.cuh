@@ -153,7 +153,20 @@ struct tbpm_ctx {
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
       ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi;
-  int fusion = 0;  // temporal-fusion mode of the moment pass (0 = one step per pass, the default)
+  int fusion = 4;  // temporal-fusion mode of the moment pass (4 = two-step row sweep; -1 = autotuned)
+  // autotuned fusion modes: key (kind, Lx, Ly, Lz, pbc bits, path, Spad, precision, disorder) -> mode
+  std::vector<std::pair<std::vector<int64_t>, int>> fusion_choice;
+  std::vector<std::pair<int, double>> fusion_timings;  // last autotune: (mode, ms per step)
+  // CUDA graphs of moment-pass sequences: a sequence seen twice with the same key (buffers,
+  // lattice, sizes, mode) is captured once and replayed afterwards
+  struct Graph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec;
+    int64_t kernels;
+  };
+  bool use_graphs = true;
+  std::vector<Graph> graphs;
+  std::vector<std::vector<uint64_t>> graph_seen;
   int max_pass_states = 0;  // cap on states per pass of the OC, DP and CD drivers (0 = by memory)
   double* pinned = nullptr;
   size_t pinned_cap = 0;

@@ -313,7 +313,7 @@ FUSED_CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("name,spec,S,M", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
 def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode):
     lat, ol = make(capi, ctx, **spec)
@@ -321,9 +321,44 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
     mf = gpu_moments(capi, ctx, lat, S, M, 0)
     capi.tbpm_set_fusion(ctx, 0)
     mu = gpu_moments(capi, ctx, lat, S, M, 0)
+    capi.tbpm_set_fusion(ctx, 4)
     assert np.max(np.abs(mf - mu)) <= 1e-6
     psi = oprop.random_phase_states(ol, 3, S)
     for s in (0, S - 1):
         ref = oprop.moments(ol, psi[s], psi[s], M)
         assert np.max(np.abs(mf[s] - ref)) <= 1e-5
+    capi.tbpm_lattice_destroy(lat)
+
+
+def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
+    """Mode -1 times modes 0, 3, 4 on the request's lattice shape and uses the fastest; the moments
+    agree with the one-step pass within the complex64 tolerance."""
+    lat, ol = make(capi, ctx, kind=1, L=(256, 200), t=-2.7, W=0.5)
+    capi.tbpm_set_fusion(ctx, -1)
+    ma = gpu_moments(capi, ctx, lat, 8, 160, 0)
+    rep = capi.tbpm_fusion_report(ctx)
+    capi.tbpm_set_fusion(ctx, 0)
+    m0 = gpu_moments(capi, ctx, lat, 8, 160, 0)
+    capi.tbpm_set_fusion(ctx, 4)
+    assert set(rep) == {0, 3, 4} and all(v > 0 for v in rep.values())
+    assert np.max(np.abs(ma - m0)) <= 1e-6
+    capi.tbpm_lattice_destroy(lat)
+
+
+@pytest.mark.parametrize("spec,S,prec", [(dict(kind=1, L=(96, 64), t=-2.7, W=0.5), 8, 0),
+                                         (dict(kind=0, L=(64, 64), t=1.0, W=1.0), 1, 1)])
+def test_graph_replay_is_bit_identical(capi, ctx, spec, S, prec):
+    """The second identical moment request is captured into a CUDA graph, the third replays it;
+    all equal the eager result bit for bit, and replays count their kernels."""
+    lat, _ = make(capi, ctx, **spec)
+    capi.tbpm_set_graphs(ctx, False)
+    ref = gpu_moments(capi, ctx, lat, S, 256, prec)
+    capi.tbpm_set_graphs(ctx, True)
+    outs = []
+    for _ in range(3):
+        c0 = capi.tbpm_launch_count(ctx)
+        outs.append(gpu_moments(capi, ctx, lat, S, 256, prec))
+        assert capi.tbpm_launch_count(ctx) - c0 >= 2
+    for o in outs:
+        assert np.array_equal(o, ref)
     capi.tbpm_lattice_destroy(lat)
