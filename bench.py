@@ -40,6 +40,7 @@ WORKLOADS = {
     "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
                                n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
     "graphene22528": wl.GRAPHENE_22528,
+    "square64": wl.SQUARE_64,
     "vacancy4096": wl.GRAPHENE_4096_VAC,
     "vacancy1024": wl.Workload("honeycomb1024x1024_vac1pct_W2_Nt256", wl.honeycomb(1024, 1024, t=-2.7, W=2.0,
                                                                                  vacancy_frac=0.01, path=wl.PATH_CSR),
@@ -63,9 +64,10 @@ def parse():
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--fusion", type=int, default=4,
+    p.add_argument("--fusion", type=int, default=5,
                    help="moment-pass fusion mode: 0 = one step per pass, 1 = 4-step tiles, 2 = 2-step tiles, "
-                        "3 = 2-step row sweep")
+                        "3/4 = 2-step row sweep, 5/6 = 4-step row sweep, 7 = 2-step sweep (K-step code), "
+                        "-1 = autotuned")
     p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
     p.add_argument("--requests", type=int, default=512)
     p.add_argument("--log2-max-sites", type=int, default=20)
@@ -290,7 +292,9 @@ def run_gpu(args, work):
     S, M, nE = work.n_states, work.n_moments, work.n_energies
     E = wl.uniform_energy_grid(nE, info.H0 - info.half_width, info.H0 + info.half_width)
     recon = capi.RECON_TENSOR if args.recon == "tensor" else capi.RECON_FP64
-    req = capi.request(n_states=S, precision=capi.C64, form=capi.CONCURRENT_M, n_moments=M,
+    prec = work.precision
+    elem = 8 if prec == capi.C64 else 16
+    req = capi.request(n_states=S, precision=prec, form=capi.CONCURRENT_M, n_moments=M,
                        state_seed=1 + 1000 * rank, dos_method=capi.DOS_JACKSON, recon=recon)
     dev = torch.device("cuda", local)
     d_E = torch.tensor(E, device=dev, dtype=torch.float64)
@@ -356,7 +360,7 @@ def run_gpu(args, work):
 
     # ---- roofline of the dominant kernel, from the live events.  Algorithmic bytes: 24 B per
     # site-update (read phi_n, read phi_{n-1}, write phi_{n+1}, complex64) + 4 B per site with disorder.
-    per_site_step = 24.0 * info.n_sites * S + (4.0 * info.n_sites if spec.W != 0.0 else 0.0)
+    per_site_step = 3.0 * elem * info.n_sites * S + ((elem / 2) * info.n_sites if spec.W != 0.0 else 0.0)
     total_alg = per_site_step * (M // 2) * args.steps
     if prof["fused_launches"] > 0:
         steps_per_launch = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2}[args.fusion]
@@ -368,7 +372,9 @@ def run_gpu(args, work):
                        else f"k_fused_rows{steps_per_launch}/{work.name}")
     else:
         steps_per_launch = 1
-        kname = "k_moment_stencil<honeycomb, complex64 x2 per thread>"
+        kname = (f"k_moment_stencil<{wl.KIND_NAMES[spec.kind]}, "
+                 + ("complex64 x2 per thread>" if prec == capi.C64 and S >= 2 else
+                    "complex64 x1 per thread>" if prec == capi.C64 else "complex128>"))
         per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
         traffic_key = f"k_moment_stencil/{work.name}"
     bytes_per_launch = per_site_step * steps_per_launch
@@ -395,12 +401,12 @@ def run_gpu(args, work):
     out = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == capi.C64 else "f64",
         "data": "synthetic (seeded Philox random-phase states on a "
-                + ("clean " if spec.W == 0 else f"disordered (W={spec.W}) ") + "honeycomb lattice)",
+                + ("clean " if spec.W == 0 else f"disordered (W={spec.W}) ") + f"{wl.KIND_NAMES[spec.kind]} lattice)",
         "config": {"workload": work.name, "sites": info.n_sites, "states": S, "moments": M, "energies": nE,
                    "form": "concurrent moment-based, cost-halving (M/2 matrix applications)",
-                   "precision": "complex64 states, FP64 reductions",
+                   "precision": "complex64 states, FP64 reductions" if prec == capi.C64 else "complex128",
                    "reconstruction": args.recon, "fusion_mode": args.fusion, "l2": "inputs larger than L2 (2 state blocks of "
                    f"{info.n_sites * S * 8 / 1e6:.0f} MB)", "parallelism": f"replicas x{world}"},
         "roofline": roofline,
@@ -416,7 +422,7 @@ def run_gpu(args, work):
         Ef = wl.uniform_energy_grid(512, info.H0 - info.half_width, info.H0 + info.half_width)
         res = {}
         for name, form in (("concurrent_m", capi.CONCURRENT_M), ("sequential", capi.SEQUENTIAL)):
-            r = capi.request(n_states=S, precision=capi.C64, form=form, n_steps=Nt, state_seed=1,
+            r = capi.request(n_states=S, precision=prec, form=form, n_steps=Nt, state_seed=1,
                              dos_method=capi.DOS_FOURIER, window=capi.WINDOW_HANN)
             Dout = np.zeros((S, Ef.size))
             lat = capi.tbpm_lattice_create(ctx, desc)

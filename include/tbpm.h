@@ -144,18 +144,20 @@ void* tbpm_stream(tbpm_ctx* ctx);
 int tbpm_sync(tbpm_ctx* ctx);
 /* Number of kernels the library has launched on this context since creation. */
 int64_t tbpm_launch_count(const tbpm_ctx* ctx);
-/* Temporal fusion of the moment pass (several Chebyshev steps per pass in shared memory, so
- * each state vector crosses HBM twice per pass instead of three times per step), used where a
- * fused kernel exists (honeycomb stencil, complex64, S >= 2, lattice at least 48 x 32 cells).
- * mode: 0 = one step per pass; 1 = 4 steps per pass (2-D tiles); 2 = 2 steps per pass (2-D
- * tiles); 3 and 4 = 2 steps per pass by a row sweep (bands of cells, rows streamed through a
- * shared-memory ring one row ahead; 128- and 256-thread CTAs).  Default 4, the fastest measured
- * on GB300 (honeycomb 2048 x 2048, 8 states: 1.52x the one-step pass).  Results of different
- * modes agree within the complex64 tolerance, not bit for bit; each mode is deterministic. */
+/* Temporal fusion of the moment pass (several Chebyshev steps per pass, so each state vector
+ * crosses HBM twice per pass instead of three times per step), used where a fused kernel exists
+ * (honeycomb stencil, complex64, S >= 2, lattice at least 48 x 32 cells).
+ * mode: 0 = one step per pass; 1 = 4 steps per pass (2-D tiles); 2 = 2 steps per pass (2-D tiles);
+ * 3, 4 = 2 steps per pass by a row sweep (bands of cells, rows of phi_n streamed through a
+ * shared-memory ring one row ahead, each further step one row behind the previous; 128- and
+ * 256-thread CTAs); 5, 6 = the row sweep with 4 steps per pass (128- and 256-thread CTAs);
+ * 7 = the 2-step sweep in the same code as 5 and 6.  Default 5, the fastest measured on GB300
+ * (honeycomb 2048 x 2048, 8 states: 1.87x the one-step pass).  Results of different modes agree
+ * within the complex64 tolerance, not bit for bit; each mode is deterministic. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
 /* mode -1 = autotuned: the first moment request on a lattice shape (kind, sizes, boundaries,
  * path, padded S, precision, disorder) with at least 128 moments times 24 steps of each of modes
- * 0, 3 and 4 on scratch buffers and keeps the fastest for that shape in the context.  Results of
+ * 0, 4 and 5 on scratch buffers and keeps the fastest for that shape in the context.  Results of
  * different modes agree within the complex64 tolerance, not bit for bit.
  * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode, -1 = not timed). */
 int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[5]);

@@ -883,9 +883,10 @@ int choose_fusion(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, con
   cudaEvent_t e0, e1;
   TBPM_CK(cudaEventCreate(&e0));
   TBPM_CK(cudaEventCreate(&e1));
-  const int modes[] = {0, 3, 4};
+  const int modes[] = {0, 4, 5};
   double best_ms = 1e300;
   ctx->fusion_timings.clear();
+  // 24 steps per mode after 8 warm-up steps (multiples of every mode's steps per pass)
   int r = TBPM_OK;
   for (int m : modes) {
     const int K = m == 0 ? 1 : fused_steps(m);

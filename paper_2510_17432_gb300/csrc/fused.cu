@@ -545,8 +545,10 @@ struct RowKCfg {
   static constexpr int NV = 6 * K;
   static constexpr int FOLD = 16;
   static constexpr int MINB = K == 2 ? (NT >= 256 ? 3 : 6) : (NT >= 256 ? 2 : 4);
+  // rows: [P zero][A plane: NT units][P zero][B plane: NT units][P zero]; the middle pad serves
+  // both A(c+1) past the last cell and B(c-1) before the first
   static size_t smem(int P) {
-    return (size_t)(NSLOT0 + 3 * (K - 1)) * (RU + 4 * P) * 16 + (size_t)(NT / 32) * P * NV * 8;
+    return (size_t)(NSLOT0 + 3 * (K - 1)) * (RU + 3 * P) * 16 + (size_t)(NT / 32) * P * NV * 8;
   }
 };
 
@@ -556,7 +558,7 @@ __global__ void __launch_bounds__(NT_, RowKCfg<NT_, K_>::MINB) k_fused_rowsK(Row
   constexpr int NT = RC::NT, K = RC::K, H = RC::H, RU = RC::RU, NV = RC::NV, NS0 = RC::NSLOT0;
   extern __shared__ float4 smr[];
   __shared__ unsigned ticket;
-  const int P = a.P, logP = a.logP, CW = a.CW, HALF = NT + 2 * P, RS = 2 * HALF;
+  const int P = a.P, logP = a.logP, CW = a.CW, RS = 2 * NT + 3 * P;
   float4* ring0 = smr;                                   // [NS0][RS]
   float4* ringL = smr + NS0 * RS;                        // [K-1][3][RS]: level L at ringL + (L-1)*3*RS
   double* red = reinterpret_cast<double*>(smr + (NS0 + 3 * (K - 1)) * RS);  // [warps][P][NV]
@@ -570,7 +572,7 @@ __global__ void __launch_bounds__(NT_, RowKCfg<NT_, K_>::MINB) k_fused_rowsK(Row
   for (int i = threadIdx.x; i < (NT / 32) * P * NV; i += NT) red[i] = 0.0;
 
   const int c = threadIdx.x >> logP, p = threadIdx.x & (P - 1);
-  const int wA = P + (int)threadIdx.x, wB = HALF + P + (int)threadIdx.x;
+  const int wA = P + (int)threadIdx.x, wB = NT + 2 * P + (int)threadIdx.x;
   int64_t x = x0 - H + c;
   bool ghx = false;
   if (x < 0 || x >= a.Lx) {
@@ -607,6 +609,7 @@ __global__ void __launch_bounds__(NT_, RowKCfg<NT_, K_>::MINB) k_fused_rowsK(Row
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.f;
   int folded = 0;
+  // every FOLD rows: FP32 lane tree per pair, added in FP64 to the warp's slots
   auto fold = [&]() {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(NT_, RowKCfg<NT_, K_>::MINB) k_fused_rowsK(Row
   }
   fold();
   __syncthreads();
-  for (int q = threadIdx.x; q < P * NV; q += NT) {
+  for (int q = threadIdx.x; q < P * NV; q += NT) {  // warps in order
     const int pp = q / NV, v = q - pp * NV;
     double t = 0.0;
     for (int w = 0; w < NT / 32; ++w) t += red[(w * P + pp) * NV + v];

@@ -153,7 +153,7 @@ struct tbpm_ctx {
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
       ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi;
-  int fusion = 4;  // temporal-fusion mode of the moment pass (4 = two-step row sweep; -1 = autotuned)
+  int fusion = 5;  // temporal-fusion mode of the moment pass (5 = four-step row sweep; -1 = autotuned)
   // autotuned fusion modes: key (kind, Lx, Ly, Lz, pbc bits, path, Spad, precision, disorder) -> mode
   std::vector<std::pair<std::vector<int64_t>, int>> fusion_choice;
   std::vector<std::pair<int, double>> fusion_timings;  // last autotune: (mode, ms per step)

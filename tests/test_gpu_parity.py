@@ -321,7 +321,7 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
     mf = gpu_moments(capi, ctx, lat, S, M, 0)
     capi.tbpm_set_fusion(ctx, 0)
     mu = gpu_moments(capi, ctx, lat, S, M, 0)
-    capi.tbpm_set_fusion(ctx, 4)
+    capi.tbpm_set_fusion(ctx, 5)
     assert np.max(np.abs(mf - mu)) <= 1e-6
     psi = oprop.random_phase_states(ol, 3, S)
     for s in (0, S - 1):
@@ -331,7 +331,7 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
 
 
 def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
-    """Mode -1 times modes 0, 3, 4 on the request's lattice shape and uses the fastest; the moments
+    """Mode -1 times modes 0, 4, 5 on the request's lattice shape and uses the fastest; the moments
     agree with the one-step pass within the complex64 tolerance."""
     lat, ol = make(capi, ctx, kind=1, L=(256, 200), t=-2.7, W=0.5)
     capi.tbpm_set_fusion(ctx, -1)
@@ -339,8 +339,8 @@ def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
     rep = capi.tbpm_fusion_report(ctx)
     capi.tbpm_set_fusion(ctx, 0)
     m0 = gpu_moments(capi, ctx, lat, 8, 160, 0)
-    capi.tbpm_set_fusion(ctx, 4)
-    assert set(rep) == {0, 3, 4} and all(v > 0 for v in rep.values())
+    capi.tbpm_set_fusion(ctx, 5)
+    assert set(rep) == {0, 4, 5} and all(v > 0 for v in rep.values())
     assert np.max(np.abs(ma - m0)) <= 1e-6
     capi.tbpm_lattice_destroy(lat)
 

@@ -83,8 +83,8 @@ def cubic(Lx, Ly, Lz, **kw) -> LatticeSpec:
 SQUARE_64 = Workload(
     "square64x64_W1_c128_S1_M1024",
     square(64, 64, t=1.0, W=1.0),
-    n_states=1, n_moments=1024, precision=C128, n_steps=295,
-    description="square 64x64 PBC, t=1, V in [-0.5,0.5], complex128, 1 state, 1024 moments")
+    n_states=1, n_moments=1024, precision=C128, n_steps=295, n_energies=1024,
+    description="square 64x64 PBC, t=1, V in [-0.5,0.5], complex128, 1 state, 1024 moments, DOS on 1024 energies")
 
 GRAPHENE_2048 = Workload(
     "honeycomb2048x2048_S8_M4096",
