@@ -69,6 +69,9 @@ def parse():
                         "3/4 = 2-step row sweep, 5/6 = 4-step row sweep, 7 = 2-step sweep (K-step code), "
                         "-1 = autotuned")
     p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
+    p.add_argument("--oc", action="store_true",
+                   help="also time the optical conductivity on the workload's lattice (0-10 eV, 2048 frequencies)")
+    p.add_argument("--oc-steps", type=int, default=256)
     p.add_argument("--requests", type=int, default=512)
     p.add_argument("--log2-max-sites", type=int, default=20)
     p.add_argument("--load", type=float, default=0.8, help="arrival rate as a fraction of measured capacity")
@@ -415,6 +418,25 @@ def run_gpu(args, work):
         "gpu_launches": launches,
         "clocks": clk,
     }
+
+    # ---- optical conductivity on the same lattice (Fermi-Dirac filtered pair states, time blocks)
+    if args.oc and rank == 0:
+        lat = capi.tbpm_lattice_create(ctx, desc)
+        Nt, nw = args.oc_steps, 2048
+        req_oc = capi.request(n_states=S, precision=capi.C64, form=capi.CONCURRENT_S, n_steps=Nt, state_seed=1,
+                              window=capi.WINDOW_HANN)
+        sig = np.zeros((S, nw), np.complex128)
+        mu_f, kT = info.H0, 0.1
+        c0 = capi.tbpm_launch_count(ctx)
+        t0 = time.perf_counter()
+        capi.tbpm_optical_conductivity(ctx, lat, req_oc, 0, 0, mu_f, kT, 10.0, nw, None, sig)
+        wall = time.perf_counter() - t0
+        capi.tbpm_lattice_destroy(lat)
+        out["optical_conductivity"] = {
+            "sites": info.n_sites, "states": S, "n_steps": Nt, "tau": "pi/2", "frequencies": nw,
+            "omega_max_eV": 10.0, "mu": mu_f, "kT": kT, "form": "time blocks (b autotuned), Hann window",
+            "wall_s": wall, "launches": capi.tbpm_launch_count(ctx) - c0,
+            "finite": bool(np.all(np.isfinite(sig))), "re_sigma_at_2_7eV": float(np.mean(sig[:, int(2.7 / 10 * 2047)].real))}
 
     # ---- sequential form on the same GPU: wall time per converged spectrum
     if not args.no_sequential and rank == 0 and work.n_steps:

@@ -159,8 +159,9 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
  * path, padded S, precision, disorder) with at least 128 moments times 24 steps of each of modes
  * 0, 4 and 5 on scratch buffers and keeps the fastest for that shape in the context.  Results of
  * different modes agree within the complex64 tolerance, not bit for bit.
- * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode, -1 = not timed). */
-int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[5]);
+ * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode 0..7, -1 = not
+ * timed). */
+int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[8]);
 /* CUDA graphs for the moment pass (default on): a moment request whose pass sequence (buffers,
  * lattice, sizes, fusion mode) repeats a previous one is captured into a CUDA graph on its
  * second occurrence and replayed from the third on, so a small lattice no longer pays one host
