@@ -46,8 +46,12 @@ WORKLOADS = {
                                                                                  vacancy_frac=0.01, path=wl.PATH_CSR),
                                n_states=1, n_moments=0, precision=wl.C64, n_steps=256, n_energies=16),
 }
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", f)
-               for f in ("cheb.cu", "fused.cu", "stencil.cuh", "tbpm_internal.cuh")]
+# source files that define each measured kernel family (their hash keys the stored ncu traffic)
+KERNEL_SRCS = {
+    "k_moment_stencil": ("cheb.cu", "stencil.cuh"),
+    "k_fused_cols": ("fused.cu",),
+    "k_fused_rows": ("fused.cu",),
+}
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -221,10 +225,11 @@ def measured_hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(kernel_key: str) -> str:
+    family = kernel_key.split("/")[0].rstrip("0123456789")
     h = hashlib.sha256()
-    for p in KERNEL_SRCS:
-        with open(p, "rb") as f:
+    for name in KERNEL_SRCS[family]:
+        with open(os.path.join(ROOT, "paper_2510_17432_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
 
@@ -234,9 +239,8 @@ def kernel_traffic(kernel_key: str):
     try:
         with open(TRAFFIC) as f:
             rec = json.load(f)
-        sha = kernel_source_hash()
         ent = rec.get(kernel_key)
-        if ent and ent.get("source_sha256") == sha:
+        if ent and ent.get("source_sha256") == kernel_source_hash(kernel_key):
             return float(ent["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass

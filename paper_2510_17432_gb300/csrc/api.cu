@@ -1297,22 +1297,37 @@ int run_qe(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
     TBPM_TRY(ensure(ctx, ctx->ws_phi[0], pl.state_bytes));
     TBPM_TRY(ensure(ctx, ctx->ws_phi[1], pl.state_bytes));
     TBPM_TRY(init_states(ctx, lat, req, pl, ctx->ws_phi[0].p, nullptr));
+    // buffered accumulation: each pass also copies phi_n into slot n % T of a buffer of T states,
+    // and every T terms one flush adds sum_t C_t(E) phi_t to all N_E accumulators
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(qe_flush_max_terms(), need),
+                                                               (int64_t)(0.5 * (double)free_b / pl.state_bytes)));
+    TBPM_TRY(ensure(ctx, ctx->ws_acc, pl.state_bytes * (size_t)T));
+    TBPM_TRY(ensure(ctx, ctx->ws_aux, 2 * sizeof(double)));
+    const double one[2] = {1.0, 0.0};
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_aux.p, one, sizeof(one), cudaMemcpyHostToDevice, ctx->stream));
+    TBPM_CK(cudaMemsetAsync(ctx->ws_qe.p, 0, pl.state_bytes * (size_t)nE, ctx->stream));
     AccumArgs g;
     memset(&g, 0, sizeof(g));
     TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
-    g.acc = ctx->ws_qe.p;
     g.acc_stride = lat->n_sites * (int64_t)pl.Spad;
-    g.b = nE;
+    g.b = 1;
     g.j_lo = 0;
     g.j_done = -1;
+    g.first_term = 1;  // the buffer slot is written, not accumulated
+    g.coef = (const double*)ctx->ws_aux.p;
     const int tok = phase_begin(ctx, 0);
     for (int64_t n = 0; n < need; ++n) {
       const int mode = (n == need - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
       g.r.cur = ctx->ws_phi[n & 1].p;
       g.r.prev_out = ctx->ws_phi[(n + 1) & 1].p;
-      g.coef = coef + (size_t)n * nE * 2;
-      g.first_term = n == 0;
+      g.acc = (char*)ctx->ws_acc.p + (size_t)(n % T) * pl.state_bytes;
       TBPM_TRY(launch_accum_step(ctx, g, pl.precision, mode));
+      if ((n + 1) % T == 0 || n == need - 1) {
+        const int nt = (int)(n % T) + 1;
+        TBPM_TRY(launch_qe_flush(ctx, g.r, pl.precision, ctx->ws_acc.p, nt, ctx->ws_qe.p, nE, coef, (int)(n + 1 - nt)));
+      }
     }
     phase_end(ctx, tok);
     return TBPM_OK;

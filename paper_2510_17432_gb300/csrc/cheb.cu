@@ -604,6 +604,51 @@ __global__ void __launch_bounds__(kThreads) k_qe_axpy(const void* xv, void* qev,
   }
 }
 
+// Buffered form of the energy-based quasi-eigenstate accumulation (Sec. IV, Eq. form2_concurrent):
+// the recurrence writes T Chebyshev states phi_{n0} .. phi_{n0+T-1} once into a buffer, and one
+// pass then adds sum_t C_{n0+t}(E) phi_{n0+t} to every accumulator, so each accumulator is read and
+// written once per T terms instead of once per term.  grid (energy tiles of kQeEB, unit blocks):
+// the energy tiles of one unit block run side by side and share the buffered states through L2.
+constexpr int kQeEB = 16;
+constexpr int kQeMaxT = 32;
+template <typename R, int SPT>
+__global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, int64_t stride_packs, void* qev,
+                                                       int nE, const double* coef, int n0, int64_t n_units) {
+  using PK = Pack<R, SPT>;
+  __shared__ R cs[kQeMaxT][kQeEB];
+  const int e0 = blockIdx.x * kQeEB;
+  const int ne = min(kQeEB, nE - e0);
+  for (int i = threadIdx.x; i < T * kQeEB; i += kThreads) {
+    const int t = i / kQeEB, e = i - t * kQeEB;
+    cs[t][e] = e < ne ? (R)coef[((int64_t)(n0 + t) * nE + e0 + e) * 2] : R(0);  // C_n(E) is real
+  }
+  __syncthreads();
+  const PK* Phi = reinterpret_cast<const PK*>(phiv);
+  PK* Q = reinterpret_cast<PK*>(qev);
+  for (int64_t u = (int64_t)blockIdx.y * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.y * kThreads) {
+    PK acc[kQeEB];
+#pragma unroll
+    for (int e = 0; e < kQeEB; ++e) {
+      if (e < ne) acc[e] = ld(Q + (int64_t)(e0 + e) * stride_packs + u);
+      else
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] = R(0);
+    }
+    for (int t = 0; t < T; ++t) {
+      const PK x = ld(Phi + (int64_t)t * stride_packs + u);
+#pragma unroll
+      for (int e = 0; e < kQeEB; ++e) {
+        const R c = cs[t][e];
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] += c * x.v[k];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < kQeEB; ++e)
+      if (e < ne) st(Q + (int64_t)(e0 + e) * stride_packs + u, acc[e]);
+  }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename R, int SPT>
 static void* moment_kernel(int kind, bool csr, bool first) {
@@ -725,6 +770,35 @@ int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const 
   int64_t nu = n_units;
   void* args[] = {(void*)&x, &qe, &stride, &nu, (void*)&phase, &width, &j, &sgn, &scale, &nE};
   return launch(ctx, fn, grid, args);
+}
+
+int qe_flush_max_terms() { return kQeMaxT; }
+
+int launch_qe_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* qe, int nE,
+                    const double* coef, int n0) {
+  if (T < 1 || T > kQeMaxT) {
+    set_error("quasi-eigenstate flush of %d terms", T);
+    return TBPM_EINVAL;
+  }
+  const int spt = spt_of(precision, a.S);
+  const int64_t n_units = a.n_sites * a.P;
+  const int etiles = (nE + kQeEB - 1) / kQeEB;
+  const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * 8 / etiles);
+  const int ublocks = (int)std::min<int64_t>(std::min<int64_t>(want, (n_units + kThreads - 1) / kThreads), 65535);
+  void* fn;
+  if (precision == TBPM_C128) fn = (void*)k_qe_flush<double, 1>;
+  else if (spt == 2) fn = (void*)k_qe_flush<float, 2>;
+  else fn = (void*)k_qe_flush<float, 1>;
+  int64_t stride = n_units;
+  int64_t nu = n_units;
+  void* args[] = {(void*)&phi, &T, &stride, &qe, &nE, (void*)&coef, &n0, &nu};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(etiles, ublocks), dim3(kThreads), args, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("kernel launch: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  return TBPM_OK;
 }
 
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,

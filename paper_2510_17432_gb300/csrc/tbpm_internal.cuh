@@ -268,6 +268,9 @@ int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
 int launch_qe_axpy(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, void* qe,
                    const double* phase, int width, int j, double sgn, double scale, int nE);
+int qe_flush_max_terms();
+int launch_qe_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* qe, int nE,
+                    const double* coef, int n0);
 int launch_qe_coefficients(tbpm_ctx* ctx, const double* table, int n_steps, int n_terms, const double* energies,
                            int nE, double H0, double tphys, double* phase, double* coef);
 int launch_qe_coefficients_phase_only(tbpm_ctx* ctx, const double* energies, int nE, double tphys, int n_steps,
