@@ -22,6 +22,17 @@ reading used here is Gershgorin, which never underestimates):
     E_max = max_i (V_i + deg_i |t|),  E_min = min_i (V_i - deg_i |t|)
     H0 = (E_max + E_min) / 2,  |H| = (1 + 0.01) (E_max - E_min) / 2.
 
+Long-range hopping (cutoff > 0).  The paper's test system is a dense Hamiltonian whose
+density D_H (non-zeros per row, Sec. II.B) it varies from 60 to 230 (Sec. IV); its
+geometry is not available, so a lattice of the same kinds stands in: every pair of sites
+whose distance r (in units of the nearest-neighbour distance, positions below) satisfies
+0 < r <= cutoff is bonded with t(r) = t exp(-(r - 1)/decay), t(1) = t.  With periodic
+boundaries H_ij sums t(|r_j + R - r_i|) over every period vector R of the sample that
+brings the pair within the cutoff (images add up, as coinciding bonds do above); open
+directions take R = 0 only.  Gershgorin then uses sum_j |t| over all those bonds.
+Positions: square (x, y, 0); cubic (x, y, z); honeycomb x a1 + y a2 + s (1, 0, 0) with
+a1 = (3/2, sqrt3/2, 0), a2 = (3/2, -sqrt3/2, 0), so A(x,y)-B(x,y) has length 1.
+
 Part of the FP64 oracle: test infrastructure only.
 """
 from __future__ import annotations
@@ -34,6 +45,7 @@ import scipy.sparse as sp
 from .philox import draw_u32, STREAM_DISORDER, STREAM_VACANCY
 
 SQUARE, HONEYCOMB, CUBIC = 0, 1, 2
+SQ3 = np.sqrt(3.0)
 COORDINATION = {SQUARE: 4, HONEYCOMB: 3, CUBIC: 6}
 BOUND_MARGIN = 0.01
 
@@ -131,14 +143,68 @@ class Lattice:
     E_max: float
     H0: float
     half_width: float
+    cutoff: float = 0.0       # long-range hopping radius (0: nearest neighbours)
+    decay: float = 0.0        # decay length of t(r)
 
     @property
     def n(self) -> int:
         return int(self.V.shape[0])
 
 
+def site_positions(kind: int, L, full_idx) -> np.ndarray:
+    """[len(full_idx), 3] positions of full sites (nearest-neighbour distance 1)."""
+    Lx, Ly, Lz = L
+    f = np.asarray(full_idx, dtype=np.int64)
+    if kind == HONEYCOMB:
+        s, c = f % 2, f // 2
+        x, y = c % Lx, c // Lx
+        return (x[:, None] * np.array([1.5, SQ3 / 2, 0.0]) + y[:, None] * np.array([1.5, -SQ3 / 2, 0.0])
+                + s[:, None] * np.array([1.0, 0.0, 0.0]))
+    if kind == CUBIC:
+        return np.stack([f % Lx, (f // Lx) % Ly, f // (Lx * Ly)], axis=1).astype(np.float64)
+    return np.stack([f % Lx, f // Lx, np.zeros(f.size)], axis=1).astype(np.float64)
+
+
+def period_vectors(kind: int, L) -> list:
+    """The sample's period vector along each of the three directions."""
+    Lx, Ly, Lz = L
+    if kind == HONEYCOMB:
+        return [Lx * np.array([1.5, SQ3 / 2, 0.0]), Ly * np.array([1.5, -SQ3 / 2, 0.0]), np.zeros(3)]
+    return [np.array([Lx, 0.0, 0.0]), np.array([0.0, Ly, 0.0]), np.array([0.0, 0.0, Lz if kind == CUBIC else 0.0])]
+
+
+def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay: float):
+    """All bonds (i, j, t(r)) between the listed sites, by brute force over site pairs and
+    period images: 0 < |r_j + R - r_i| <= cutoff.  Returns compact rows, columns, values."""
+    pos = site_positions(kind, L, full_idx)
+    per = period_vectors(kind, L)
+    dims = 3 if kind == CUBIC else 2
+    ranges = []
+    for a in range(3):
+        if a < dims and pbc[a]:
+            m = int(np.ceil(cutoff / np.linalg.norm(per[a]))) + 1
+            ranges.append(range(-m, m + 1))
+        else:
+            ranges.append(range(0, 1))
+    rows, cols, vals = [], [], []
+    n = pos.shape[0]
+    for n0 in ranges[0]:
+        for n1 in ranges[1]:
+            for n2 in ranges[2]:
+                R = n0 * per[0] + n1 * per[1] + n2 * per[2]
+                for lo in range(0, n, 512):
+                    d = pos[None, :, :] + R - pos[lo:lo + 512, None, :]
+                    r = np.sqrt(np.sum(d * d, axis=2))
+                    ii, jj = np.nonzero((r > 1e-9) & (r <= cutoff))
+                    rows.append(ii + lo)
+                    cols.append(jj)
+                    vals.append(t * np.exp(-(r[ii, jj] - 1.0) / decay))
+    cat = lambda v, dt: np.concatenate(v).astype(dt) if v else np.zeros(0, dt)
+    return cat(rows, np.int64), cat(cols, np.int64), cat(vals, np.float64)
+
+
 def build_lattice(kind: int, L, t: float, W: float = 0.0, vacancy_frac: float = 0.0,
-                  seed: int = 0, pbc=(1, 1, 1)) -> Lattice:
+                  seed: int = 0, pbc=(1, 1, 1), cutoff: float = 0.0, decay: float = 0.0) -> Lattice:
     L = tuple(int(v) for v in L) + (1,) * (3 - len(L))
     pbc = tuple(bool(v) for v in pbc) + (True,) * (3 - len(pbc))
     n_full = full_site_count(kind, L)
@@ -149,33 +215,44 @@ def build_lattice(kind: int, L, t: float, W: float = 0.0, vacancy_frac: float = 
     compact[active] = np.arange(int(active.sum()), dtype=np.int64)
     V_full = disorder_potential(seed, W, n_full) if W != 0.0 else np.zeros(n_full)
 
-    rows, cols = [], []
     full_idx = np.flatnonzero(active)
-    for k in range(nbr.shape[1]):
-        j = nbr[full_idx, k]
-        keep = j >= 0
-        keep[keep] &= active[j[keep]]
-        rows.append(compact[full_idx[keep]])
-        cols.append(compact[j[keep]])
-    rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
-    cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
     n = full_idx.size
+    if cutoff > 0.0:
+        if not decay > 0.0:
+            raise ValueError("long-range hopping needs decay > 0")
+        rows, cols, tv = long_range_bonds(kind, L, pbc, full_idx, float(t), float(cutoff), float(decay))
+        nbr = None
+    else:
+        rows, cols = [], []
+        for k in range(nbr.shape[1]):
+            j = nbr[full_idx, k]
+            keep = j >= 0
+            keep[keep] &= active[j[keep]]
+            rows.append(compact[full_idx[keep]])
+            cols.append(compact[j[keep]])
+        rows = np.concatenate(rows) if rows else np.zeros(0, np.int64)
+        cols = np.concatenate(cols) if cols else np.zeros(0, np.int64)
+        tv = np.full(rows.size, float(t))
     V = V_full[full_idx].astype(np.float64)
-    hop = sp.coo_matrix((np.full(rows.size, float(t)), (rows, cols)), shape=(n, n)).tocsr()
+    hop = sp.coo_matrix((tv, (rows, cols)), shape=(n, n)).tocsr()
     H = (hop + sp.diags(V)).tocsr()
     H.sum_duplicates()
     degree = np.bincount(rows, minlength=n).astype(np.int64)
+    if cutoff > 0.0:
+        radius = np.bincount(rows, weights=np.abs(tv), minlength=n)   # sum of |t| over bonds
+    else:
+        radius = degree * abs(float(t))
 
     if n == 0:
         raise ValueError("lattice has no active sites")
-    E_max = float(np.max(V + degree * abs(t)))
-    E_min = float(np.min(V - degree * abs(t)))
+    E_max = float(np.max(V + radius))
+    E_min = float(np.min(V - radius))
     if not E_max > E_min:
         raise ValueError("degenerate spectrum: no hopping")
     H0 = (E_max + E_min) / 2.0
     half = (1.0 + BOUND_MARGIN) * (E_max - E_min) / 2.0
     return Lattice(kind, L, pbc, float(t), float(W), float(vacancy_frac), int(seed), n_full,
-                   nbr, active, compact, V, H, degree, E_min, E_max, H0, half)
+                   nbr, active, compact, V, H, degree, E_min, E_max, H0, half, float(cutoff), float(decay))
 
 
 def rescaled_apply(lat: Lattice, x: np.ndarray) -> np.ndarray:
