@@ -42,6 +42,9 @@ WORKLOADS = {
     "graphene22528": wl.GRAPHENE_22528,
     "square64": wl.SQUARE_64,
     "vacancy4096": wl.GRAPHENE_4096_VAC,
+    "dense61": wl.dense_honeycomb(61),
+    "dense124": wl.dense_honeycomb(124),
+    "dense235": wl.dense_honeycomb(235),
     "vacancy1024": wl.Workload("honeycomb1024x1024_vac1pct_W2_Nt256", wl.honeycomb(1024, 1024, t=-2.7, W=2.0,
                                                                                  vacancy_frac=0.01, path=wl.PATH_CSR),
                                n_states=1, n_moments=0, precision=wl.C64, n_steps=256, n_energies=16),
@@ -77,6 +80,8 @@ def parse():
                    help="also time the optical conductivity on the workload's lattice (0-10 eV, 2048 frequencies)")
     p.add_argument("--oc-steps", type=int, default=256)
     p.add_argument("--requests", type=int, default=512)
+    p.add_argument("--seq-steps", type=int, default=0,
+                   help="dense workloads: N_t of the D_H sweep against the sequential form (0 = the workload's)")
     p.add_argument("--log2-max-sites", type=int, default=20)
     p.add_argument("--load", type=float, default=0.8, help="arrival rate as a fraction of measured capacity")
     return p.parse_args()
@@ -162,7 +167,7 @@ sys.path.insert(0, {root!r})
 import numpy as np
 from oracle import lattice as L, propagate as P
 kind, dims, t, W, vac, seed, seconds, reps = {kind}, {dims}, {t}, {W}, {vac}, {seed}, {seconds}, {reps}
-lat = L.build_lattice(kind, dims, t=t, W=W, vacancy_frac=vac, seed=seed)
+lat = L.build_lattice(kind, dims, t=t, W=W, vacancy_frac=vac, seed=seed, cutoff={cutoff}, decay={decay})
 psi = P.random_phase_states(lat, 1, 1)[0]
 t0 = time.perf_counter(); P.moments(lat, psi, psi, 4); one = (time.perf_counter() - t0) / 4
 k = int(max(4, min(4096, seconds / max(one, 1e-6))))
@@ -179,7 +184,10 @@ ORACLE_MAX_SITES = 1 << 25  # larger lattices are sampled on a 2^24-site lattice
 
 def oracle_lattice_dims(spec) -> tuple:
     """The lattice the oracle is timed on: the workload's own, or a 2^24-site one of the same kind
-    when the workload's would not fit the host (the method is O(N), so the rate carries over)."""
+    when the workload's would not fit the host (the method is O(N), so the rate carries over).
+    Long-range lattices: a 46x46-cell sample (the oracle builds H by brute force over site pairs)."""
+    if spec.cutoff > 0:
+        return (46, 46, 1)
     if spec.n_full <= ORACLE_MAX_SITES:
         return tuple(spec.L)
     if spec.kind == wl.HONEYCOMB:
@@ -192,7 +200,8 @@ def oracle_lattice_dims(spec) -> tuple:
 def oracle_sample(work: wl.Workload, seconds: float, reps: int = 1):
     spec = work.lattice
     code = ORACLE_SAMPLE.format(root=ROOT, kind=spec.kind, dims=oracle_lattice_dims(spec), t=spec.t, W=spec.W,
-                                vac=spec.vacancy_frac, seed=spec.seed, seconds=seconds, reps=reps)
+                                vac=spec.vacancy_frac, seed=spec.seed, seconds=seconds, reps=reps,
+                                cutoff=spec.cutoff, decay=spec.decay)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
@@ -206,6 +215,9 @@ def cpu_baseline_obj(work: wl.Workload, samples):
     dims = oracle_lattice_dims(work.lattice)
     where = (f"the full {wl.KIND_NAMES[work.lattice.kind]} {dims[0]}x{dims[1]} lattice ({work.lattice.n_full} sites)"
              if dims == tuple(work.lattice.L) else
+             f"a {wl.KIND_NAMES[work.lattice.kind]} {dims[0]}x{dims[1]} lattice with the same long-range hopping "
+             f"(cutoff {work.lattice.cutoff}; the oracle builds H by brute force over site pairs)"
+             if work.lattice.cutoff > 0 else
              f"a {wl.KIND_NAMES[work.lattice.kind]} {'x'.join(str(d) for d in dims if d > 1)} lattice of the same "
              f"parameters (the {work.lattice.n_full}-site lattice does not fit the host; O(N) method)")
     return {"value": su / sec, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
@@ -733,6 +745,163 @@ def run_serving(args):
                                "S~U{1..16} or LDOS at 32 sites", "reconstruction": args.recon}}))
 
 
+def dense_desc(capi, spec):
+    return capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, vacancy_frac=spec.vacancy_frac, seed=spec.seed,
+                             pbc=spec.pbc, path=spec.path, cutoff=spec.cutoff, decay=spec.decay)
+
+
+def run_dense(args, work):
+    """Dense Hamiltonians (long-range hopping, D_H = 61 / 124 / 235; the stand-in for the paper's
+    twisted bilayer graphene): the moment-based concurrent DOS over N_t steps of tau~ = pi (the
+    paper's DOS-Concurrent-M, Sec. III) is the timed step; the sweep over D_H times it against
+    the sequential form on the same GPU (the paper's speedup-vs-D_H benchmark)."""
+    import torch
+    from paper_2510_17432_gb300 import capi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    dev = torch.device("cuda", local)
+    ctx = capi.tbpm_create(local)
+    spec = work.lattice
+    desc = dense_desc(capi, spec)
+    lat = capi.tbpm_lattice_create(ctx, desc)
+    info = capi.tbpm_lattice_info(lat)
+    S, Nt, nE = work.n_states, work.n_steps, work.n_energies
+    E = wl.uniform_energy_grid(nE, info.H0 - info.half_width, info.H0 + info.half_width)
+    Mtot = capi.tbpm_truncation_order(Nt * math.pi)
+    n_mat = (Mtot + (Mtot & 1)) // 2
+    site_updates = n_mat * info.n_sites * S
+    req = capi.request(n_states=S, precision=work.precision, form=capi.CONCURRENT_M, n_steps=Nt,
+                       state_seed=1 + 1000 * rank, dos_method=capi.DOS_FOURIER, window=capi.WINDOW_HANN)
+    d_E = torch.tensor(E, device=dev, dtype=torch.float64)
+    d_D = torch.empty((S, nE), device=dev, dtype=torch.float64)
+    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
+
+    def step_device():
+        capi.tbpm_dos_device(ctx, lat, req, d_E, nE, d_D)
+
+    def barrier():
+        torch.cuda.synchronize()
+        capi.tbpm_sync(ctx)
+        if pg is not None:
+            pg.barrier()
+
+    for _ in range(args.warmup):
+        step_device()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = capi.tbpm_launch_count(ctx)
+    capi.tbpm_profile(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    ev1.record(stream)
+    barrier()
+    dev_ms = reduce_max(pg, ev0.elapsed_time(ev1), dev)
+    prof = capi.tbpm_profile_read(ctx)
+    capi.tbpm_profile(ctx, False)
+    launches = capi.tbpm_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    ms_per_step = dev_ms / args.steps
+    value = whole_job_rate(site_updates, world, ms_per_step / 1e3)
+    assert np.all(np.isfinite(d_D.cpu().numpy()))
+
+    hE = torch.tensor(E, dtype=torch.float64).pin_memory()
+    hD = torch.empty((S, nE), dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        capi.tbpm_dos(ctx, lat, req, hE.numpy(), hD.numpy())
+    barrier()
+    e2e_s = reduce_max(pg, (time.perf_counter() - t0) / args.steps, dev)
+    e2e = {"value": whole_job_rate(site_updates, world, e2e_s), "unit": "site-updates/s",
+           "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
+
+    # roofline of the recurrence pass: ELL lists (z int32 per site) + three state blocks per step
+    z = info.coordination
+    elem = 8 if work.precision == capi.C64 else 16
+    per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
+    bytes_per_launch = (3.0 * elem * S + 4.0 * z) * info.n_sites
+    peak, peak_kind = measured_hbm_peak()
+    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+    fma_per_launch = 2.0 * z * info.n_sites * S          # real x complex: two FMAs per tap
+    sm_count, lanes, fmax = 152, 128, 2.070e9
+    alu_peak = sm_count * lanes * fmax * 2 / 1e12           # FP32 TFLOP/s (FMA = 2 flops)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_kind,
+                "kernel": "k_moment_step<CSR, complex64 x%d per thread> (ELL lists + per-slot weights)" % (2 if S >= 2 else 1),
+                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
+                "fp32_tflops": 2 * fma_per_launch / (per_launch_ms / 1e3) / 1e12,
+                "fp32_peak_tflops": alu_peak,
+                "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+    out = {
+        "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if work.precision == capi.C64 else "f64",
+        "data": "synthetic (seeded Philox random-phase states on a clean long-range honeycomb lattice)",
+        "config": {"workload": work.name, "sites": info.n_sites, "D_H": z + 1, "states": S, "n_steps": Nt,
+                   "moments": Mtot, "matrix_applications": n_mat, "energies": nE,
+                   "form": "concurrent moment-based DOS (Hann-windowed Fourier of C(t) from moments)",
+                   "l2": "inputs larger than L2 (ELL lists %.1f GB)" % (4.0 * z * info.n_sites / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+    }
+    capi.tbpm_lattice_destroy(lat)
+
+    if rank == 0 and not args.no_sequential:
+        sweep = []
+        Ef = wl.uniform_energy_grid(512, info.H0 - info.half_width, info.H0 + info.half_width)
+        Nseq = args.seq_steps or Nt
+        for dh in sorted(wl.DENSE_CUTOFFS):
+            w2 = wl.dense_honeycomb(dh, n_states=S, n_steps=Nseq)
+            l2 = capi.tbpm_lattice_create(ctx, dense_desc(capi, w2.lattice))
+            i2 = capi.tbpm_lattice_info(l2)
+            res = {}
+            for name, form in (("concurrent_m", capi.CONCURRENT_M), ("sequential", capi.SEQUENTIAL)):
+                r = capi.request(n_states=S, precision=work.precision, form=form, n_steps=Nseq, state_seed=1,
+                                 dos_method=capi.DOS_FOURIER, window=capi.WINDOW_HANN)
+                Dout = np.zeros((S, Ef.size))
+                capi.tbpm_sync(ctx)
+                t0 = time.perf_counter()
+                capi.tbpm_dos(ctx, l2, r, Ef, Dout)
+                res[name] = (time.perf_counter() - t0, Dout)
+            capi.tbpm_lattice_destroy(l2)
+            Ms = capi.tbpm_truncation_order(Nseq * math.pi)
+            conc_m = (Ms + (Ms & 1)) // 2
+            seq_m = Nseq * (capi.tbpm_truncation_order(math.pi) - 1)
+            sweep.append({
+                "D_H": i2.coordination + 1, "n_steps": Nseq,
+                "wall_s_concurrent": res["concurrent_m"][0], "wall_s_sequential": res["sequential"][0],
+                "speedup_wall": res["sequential"][0] / res["concurrent_m"][0],
+                "speedup_theory": seq_m / conc_m,
+                "site_updates_per_s_concurrent": conc_m * i2.n_sites * S / res["concurrent_m"][0],
+                "site_updates_per_s_sequential": seq_m * i2.n_sites * S / res["sequential"][0],
+                "max_rel_dos_difference": float(np.max(np.abs(res["concurrent_m"][1] - res["sequential"][1])) /
+                                                np.max(np.abs(res["sequential"][1])))})
+        out["dh_sweep"] = sweep
+
+    if rank == 0 and not args.no_cpu and world == 1:
+        try:
+            out["cpu_baseline"] = cpu_baseline_obj(work, oracle_sample(work, args.cpu_seconds))
+        except Exception as exc:
+            out["cpu_baseline"] = {"value": None, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"failed: {exc!r}"[:300]}
+    capi.tbpm_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
 def main():
     args = parse()
     work = WORKLOADS[args.workload]
@@ -741,6 +910,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args, work)
+    elif work.lattice.cutoff > 0:
+        run_dense(args, work)
     elif work.n_moments == 0:
         run_state_based(args, work)
     else:

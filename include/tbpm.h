@@ -83,6 +83,18 @@ typedef struct tbpm_lattice tbpm_lattice;
  * the remaining sites are renumbered in order and stored on the CSR/ELL path.
  * Spectral bounds (Gershgorin; Sec. II.A uses Lanczos): E_max = max_i(V_i + deg_i|t|),
  * E_min = min_i(V_i - deg_i|t|), H0 = (E_max+E_min)/2, |H| = 1.01*(E_max-E_min)/2.
+ *
+ * Long-range hopping (cutoff > 0; stands in for the dense Hamiltonians of density D_H =
+ * 60..230 that Sec. IV benchmarks): every site j with 0 < |r_j - r_i| <= cutoff is bonded
+ * with t(r) = t exp(-(r - 1)/decay).  Distances are in units of the nearest-neighbour
+ * distance; positions: square (x, y), cubic (x, y, z), honeycomb x a1 + y a2 + s (1, 0) with
+ * a1 = (3/2, sqrt3/2), a2 = (3/2, -sqrt3/2).  The bonds of a site are its "taps", listed by
+ * tbpm_lattice_taps(); periodic directions wrap each tap's target by modulo (a tap that
+ * lands on a site another tap reaches adds to that bond; one that lands on the site itself
+ * adds to the diagonal), open directions drop it.  The Gershgorin radius is the sum of |t(r)|
+ * over the taps that reach active sites.  Such lattices run on the CSR/ELL path with
+ * per-tap weights (path AUTO or CSR); the conductivity and optical-conductivity drivers
+ * (current operator) and the serving loop reject them (TBPM_EUNSUPPORTED).
  */
 typedef struct {
   int32_t kind;        /* TBPM_SQUARE / TBPM_HONEYCOMB / TBPM_CUBIC */
@@ -94,6 +106,8 @@ typedef struct {
   double W;            /* disorder width: V_i uniform on [-W/2, W/2) */
   double vacancy_frac; /* probability that a site is removed */
   uint64_t seed;       /* Philox key of the disorder and vacancy streams */
+  double cutoff;       /* 0: nearest neighbours only; > 0: long-range hopping radius (<= 12) */
+  double decay;        /* decay length of t(r) (> 0 when cutoff > 0) */
 } tbpm_lattice_desc;
 
 typedef struct {
@@ -198,6 +212,13 @@ int tbpm_lattice_info(const tbpm_lattice* lat, tbpm_lattice_props* out);
  *   V        [n_sites]       FP64 on-site energies
  *   nbr      [n_sites * z]   neighbour compact indices in the fixed order, -1 if none */
 int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, int32_t* nbr);
+/* Taps of the lattice, one per neighbour slot of the ELL lists (any pointer may be NULL):
+ *   offsets [z][4]  (dx, dy, dz, ds): a site of sublattice 0 (every site of the square and
+ *                   cubic lattices) in cell (x,y,z) reaches cell (x+dx, y+dy, z+dz) of
+ *                   sublattice ds; a honeycomb B site reaches (x-dx, y-dy) of sublattice 1-ds
+ *   t       [z]     hopping of the slot, t(r) (t itself on nearest-neighbour lattices)
+ * z = tbpm_lattice_props.coordination.  Nearest-neighbour lattices report their fixed order. */
+int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t);
 
 /* ---------------------------------------------------------------- states */
 

@@ -176,29 +176,39 @@ def period_vectors(kind: int, L) -> list:
 def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay: float):
     """All bonds (i, j, t(r)) between the listed sites, by brute force over site pairs and
     period images: 0 < |r_j + R - r_i| <= cutoff.  Returns compact rows, columns, values."""
-    pos = site_positions(kind, L, full_idx)
-    per = period_vectors(kind, L)
     dims = 3 if kind == CUBIC else 2
+    pos = site_positions(kind, L, full_idx)[:, :dims]
+    per = [v[:dims] for v in period_vectors(kind, L)]
+    # r_j - r_i has fractional coordinates in (-1, 1) along the periods, so an image R = sum n_a
+    # per_a can bring a pair within the cutoff only if |n_a| <= ceil(cutoff / h_a), h_a being the
+    # sample's height across period a (its volume over the area of the other periods' face)
+    vol = abs(np.linalg.det(np.array(per[:dims])))
     ranges = []
     for a in range(3):
         if a < dims and pbc[a]:
-            m = int(np.ceil(cutoff / np.linalg.norm(per[a]))) + 1
+            others = [per[b] for b in range(dims) if b != a]
+            face = np.linalg.norm(others[0]) if dims == 2 else np.linalg.norm(np.cross(others[0], others[1]))
+            m = int(np.ceil(cutoff / (vol / face)))
             ranges.append(range(-m, m + 1))
         else:
             ranges.append(range(0, 1))
     rows, cols, vals = [], [], []
     n = pos.shape[0]
+    c2 = cutoff * cutoff
     for n0 in ranges[0]:
         for n1 in ranges[1]:
             for n2 in ranges[2]:
-                R = n0 * per[0] + n1 * per[1] + n2 * per[2]
-                for lo in range(0, n, 512):
-                    d = pos[None, :, :] + R - pos[lo:lo + 512, None, :]
-                    r = np.sqrt(np.sum(d * d, axis=2))
-                    ii, jj = np.nonzero((r > 1e-9) & (r <= cutoff))
+                R = n0 * per[0] + n1 * per[1] + (n2 * per[2] if dims == 3 else 0.0)
+                for lo in range(0, n, 1024):
+                    d2 = np.zeros((min(1024, n - lo), n))
+                    for a in range(dims):
+                        comp = pos[None, :, a] + R[a] - pos[lo:lo + 1024, None, a]
+                        d2 += comp * comp
+                    ii, jj = np.nonzero((d2 > 1e-18) & (d2 <= c2))
+                    r = np.sqrt(d2[ii, jj])
                     rows.append(ii + lo)
                     cols.append(jj)
-                    vals.append(t * np.exp(-(r[ii, jj] - 1.0) / decay))
+                    vals.append(t * np.exp(-(r - 1.0) / decay))
     cat = lambda v, dt: np.concatenate(v).astype(dt) if v else np.zeros(0, dt)
     return cat(rows, np.int64), cat(cols, np.int64), cat(vals, np.float64)
 

@@ -36,7 +36,8 @@ class TbpmError(RuntimeError):
 class LatticeDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("path", C.c_int32), ("L", C.c_int64 * 3), ("pbc", C.c_int32 * 3),
                 ("reserved", C.c_int32), ("t", C.c_double), ("W", C.c_double),
-                ("vacancy_frac", C.c_double), ("seed", C.c_uint64)]
+                ("vacancy_frac", C.c_double), ("seed", C.c_uint64), ("cutoff", C.c_double),
+                ("decay", C.c_double)]
 
 
 class LatticeProps(C.Structure):
@@ -85,6 +86,7 @@ def load():
         "tbpm_lattice_destroy": (C.c_int, [_P]),
         "tbpm_lattice_info": (C.c_int, [_P, C.POINTER(LatticeProps)]),
         "tbpm_lattice_export": (C.c_int, [_P, _P, _P, _P]),
+        "tbpm_lattice_taps": (C.c_int, [_P, _P, _P]),
         "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
         "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
         "tbpm_moments": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
@@ -131,7 +133,7 @@ def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
-            "tbpm_lattice_export", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
             "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_fusion_report", "tbpm_set_graphs", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
@@ -205,11 +207,13 @@ def tbpm_profile_read(ctx) -> dict:
 
 
 # ---------------------------------------------------------------- lattice
-def lattice_desc(kind, L, t=1.0, W=0.0, vacancy_frac=0.0, seed=0, pbc=(1, 1, 1), path=PATH_AUTO) -> LatticeDesc:
+def lattice_desc(kind, L, t=1.0, W=0.0, vacancy_frac=0.0, seed=0, pbc=(1, 1, 1), path=PATH_AUTO,
+                 cutoff=0.0, decay=0.0) -> LatticeDesc:
     L = tuple(int(v) for v in L) + (1,) * (3 - len(L))
     pbc = tuple(int(bool(v)) for v in pbc) + (1,) * (3 - len(pbc))
     return LatticeDesc(int(kind), int(path), (C.c_int64 * 3)(*L), (C.c_int32 * 3)(*pbc), 0,
-                       float(t), float(W), float(vacancy_frac), int(seed) & 0xFFFFFFFFFFFFFFFF)
+                       float(t), float(W), float(vacancy_frac), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                       float(cutoff), float(decay))
 
 
 def tbpm_lattice_create(ctx, desc: LatticeDesc):
@@ -230,6 +234,15 @@ def tbpm_lattice_info(lat) -> LatticeProps:
 
 def tbpm_lattice_export(lat, compact=None, V=None, nbr=None):
     _check(load().tbpm_lattice_export(lat, _host_ptr(compact), _host_ptr(V), _host_ptr(nbr)))
+
+
+def tbpm_lattice_taps(lat):
+    """(offsets [z][4] int32, t [z] float64) of the lattice's neighbour slots."""
+    z = tbpm_lattice_info(lat).coordination
+    off = np.zeros((z, 4), np.int32)
+    t = np.zeros(z, np.float64)
+    _check(load().tbpm_lattice_taps(lat, _host_ptr(off), _host_ptr(t)))
+    return off, t
 
 
 # ---------------------------------------------------------------- requests

@@ -278,6 +278,65 @@ __global__ void __launch_bounds__(kT) k_build_ell(Geom g, int64_t n, const int64
   block_bounds(acc, part);
 }
 
+// Long-range lattices, pass 3: ELL lists from the taps (dx, dy, dz, ds) of sublattice 0; a
+// honeycomb B site takes every tap mirrored, (x-dx, y-dy) of sublattice 1-ds, so slot d has the
+// same length and weight on both sublattices.  Periodic directions wrap by modulo, open ones
+// drop the tap.  Gershgorin radius = sum of |t_d| over the slots that reach active sites.
+__global__ void __launch_bounds__(kT) k_build_ell_taps(Geom g, int64_t n, const int64_t* full_of,
+                                                       const int64_t* compact, const int4* taps, const double* tabs,
+                                                       uint64_t seed, double W, int32_t* ell, double* v64,
+                                                       Bounds3* part) {
+  Bounds3 acc{-INFINITY, INFINITY, 0.0};
+  const bool hc = g.kind == TBPM_HONEYCOMB;
+  auto wrap = [](int64_t v, int64_t L, int periodic, bool* ok) -> int64_t {
+    if (v >= 0 && v < L) return v;
+    if (!periodic) { *ok = false; return 0; }
+    const int64_t r = v % L;
+    return r < 0 ? r + L : r;
+  };
+  for (int64_t k = (int64_t)blockIdx.x * kT + threadIdx.x; k < n; k += (int64_t)gridDim.x * kT) {
+    const int64_t i = full_of[k];
+    int64_t x, y, zc = 0;
+    int s = 0;
+    if (hc) {
+      s = (int)(i & 1);
+      const int64_t c = i >> 1;
+      x = c % g.Lx;
+      y = c / g.Lx;
+    } else {
+      x = i % g.Lx;
+      y = (i / g.Lx) % g.Ly;
+      zc = i / (g.Lx * g.Ly);
+    }
+    const int64_t sg = s ? -1 : 1;
+    double rad = 0.0;
+    int deg = 0;
+    for (int d = 0; d < g.z; ++d) {
+      const int4 tp = taps[d];
+      bool ok = true;
+      const int64_t tx = wrap(x + sg * tp.x, g.Lx, g.pbc_x, &ok);
+      const int64_t ty = wrap(y + sg * tp.y, g.Ly, g.pbc_y, &ok);
+      const int64_t tz = wrap(zc + sg * tp.z, g.Lz, g.pbc_z, &ok);
+      int64_t cj = -1;
+      if (ok) {
+        const int64_t j = hc ? 2 * (ty * g.Lx + tx) + (s ? 1 - tp.w : tp.w) : (tz * g.Ly + ty) * g.Lx + tx;
+        cj = compact[j];
+      }
+      ell[k * g.z + d] = (int32_t)cj;
+      if (cj >= 0) {
+        rad += tabs[d];
+        ++deg;
+      }
+    }
+    const double v = (W != 0.0) ? disorder_value(seed, W, i) : 0.0;
+    if (v64) v64[k] = v;
+    acc.emax = fmax(acc.emax, v + rad);
+    acc.emin = fmin(acc.emin, v - rad);
+    acc.deg += deg;
+  }
+  block_bounds(acc, part);
+}
+
 // D_i = (V_i - H0)/|H| in FP64 and rounded once to FP32.
 __global__ void k_make_diag(int64_t n, const double* v64, double H0, double half, double* d64, float* d32) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -495,6 +554,41 @@ int64_t tbpm_truncation_order(double tau) { return truncation_order_host(tau); }
 }  // extern "C"
 
 // ------------------------------------------------------------------ lattice construction
+// Taps of a long-range lattice: every (dx, dy, dz, ds) from a site of sublattice 0 with
+// 0 < r <= cutoff, in (dz, dy, dx, ds) order, and its weight t(r)/t = exp(-(r - 1)/decay).
+// r^2 is exact in FP64 for these integer and half-integer coordinates.
+static int make_taps(const tbpm_lattice_desc& d, std::vector<int>& off, std::vector<double>& wrel) {
+  const bool hc = d.kind == TBPM_HONEYCOMB, cu = d.kind == TBPM_CUBIC;
+  const int R = (int)ceil(d.cutoff) + 2;
+  const double c2 = d.cutoff * d.cutoff;
+  off.clear();
+  wrel.clear();
+  for (int dz = cu ? -R : 0; dz <= (cu ? R : 0); ++dz)
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx)
+        for (int ds = 0; ds <= (hc ? 1 : 0); ++ds) {
+          double r2;
+          if (hc) {
+            const double u = 1.5 * (dx + dy) + ds, v = (double)(dx - dy);
+            r2 = u * u + 0.75 * v * v;
+          } else {
+            r2 = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+          }
+          if (r2 == 0.0 || r2 > c2) continue;
+          off.insert(off.end(), {dx, dy, dz, ds});
+          wrel.push_back(exp(-(sqrt(r2) - 1.0) / d.decay));
+        }
+  if (wrel.empty()) {
+    set_error("cutoff %g keeps no neighbour (nearest-neighbour distance is 1)", d.cutoff);
+    return TBPM_EINVAL;
+  }
+  if (wrel.size() > 1024) {
+    set_error("cutoff %g gives %zu neighbours per site (at most 1024)", d.cutoff, wrel.size());
+    return TBPM_EUNSUPPORTED;
+  }
+  return TBPM_OK;
+}
+
 static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
   const tbpm_lattice_desc& d = lat->desc;
   Geom& g = lat->geom;
@@ -511,10 +605,50 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
   g.n_full = g.row_sites * g.n_rows;
   const double abs_t = fabs(d.t);
   const bool vac = d.vacancy_frac > 0.0;
-  lat->path = (d.path == TBPM_PATH_AUTO) ? (vac ? TBPM_PATH_CSR : TBPM_PATH_STENCIL) : d.path;
+  const bool lr = d.cutoff > 0.0;
+  lat->path = (d.path == TBPM_PATH_AUTO) ? (vac || lr ? TBPM_PATH_CSR : TBPM_PATH_STENCIL) : d.path;
   if (vac && lat->path == TBPM_PATH_STENCIL) {
     set_error("vacancies need the CSR path");
     return TBPM_EINVAL;
+  }
+  if (lr && lat->path == TBPM_PATH_STENCIL) {
+    set_error("long-range hopping runs on the CSR path");
+    return TBPM_EINVAL;
+  }
+  std::vector<double> wrel;
+  int4* d_taps = nullptr;
+  double* d_tabs = nullptr;
+  struct Release {  // frees the tap tables on every return path
+    cudaStream_t st;
+    int4** a;
+    double** b;
+    ~Release() {
+      if (*a) cudaFreeAsync(*a, st);
+      if (*b) cudaFreeAsync(*b, st);
+    }
+  } release{ctx->stream, &d_taps, &d_tabs};
+  if (lr) {
+    TBPM_TRY(make_taps(d, lat->tap_off, wrel));
+    g.z = (int)wrel.size();
+    lat->tap_t.resize(wrel.size());
+    std::vector<double> tabs(wrel.size());
+    std::vector<float> w32(wrel.size());
+    for (size_t k = 0; k < wrel.size(); ++k) {
+      lat->tap_t[k] = d.t * wrel[k];
+      tabs[k] = abs_t * wrel[k];
+      w32[k] = (float)wrel[k];
+    }
+    const size_t z = wrel.size();
+    TBPM_TRY(dev_alloc(ctx, &lat->wrel64, z));
+    TBPM_TRY(dev_alloc(ctx, &lat->wrel32, z));
+    TBPM_TRY(dev_alloc(ctx, &d_taps, z));
+    TBPM_TRY(dev_alloc(ctx, &d_tabs, z));
+    TBPM_CK(cudaMemcpyAsync(lat->wrel64, wrel.data(), z * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(lat->wrel32, w32.data(), z * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(d_taps, lat->tap_off.data(), z * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(d_tabs, tabs.data(), z * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    // the pageable sources above must outlive the copies
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
   }
   lat->has_v = d.W != 0.0;
   const uint64_t thr = vac ? (uint64_t)floor(d.vacancy_frac * 4294967296.0) : 0;
@@ -560,10 +694,17 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
     cudaFreeAsync(counts, ctx->stream);
     cudaFreeAsync(offs, ctx->stream);
     nb = grid_for(ctx, n_active, kT);
-    k_build_ell<<<nb, kT, 0, ctx->stream>>>(g, n_active, lat->full_of, lat->compact, d.seed, d.W, abs_t,
-                                             lat->ell, lat->v64, part);
-    TBPM_CK_LAUNCH(ctx);
+    if (lr) {
+      k_build_ell_taps<<<nb, kT, 0, ctx->stream>>>(g, n_active, lat->full_of, lat->compact, d_taps, d_tabs, d.seed,
+                                                    d.W, lat->ell, lat->v64, part);
+      TBPM_CK_LAUNCH(ctx);
+    } else {
+      k_build_ell<<<nb, kT, 0, ctx->stream>>>(g, n_active, lat->full_of, lat->compact, d.seed, d.W, abs_t,
+                                               lat->ell, lat->v64, part);
+      TBPM_CK_LAUNCH(ctx);
+    }
   }
+  if (lr && d.path == TBPM_PATH_AUTO) TBPM_TRY(build_tap_chunks(ctx, lat));
   double* res = (double*)((char*)ctx->ws_aux.p + sizeof(Bounds3) * (size_t)ctx->num_sms * 16);
   k_bounds_final<<<1, kT, 0, ctx->stream>>>(part, nb, res);
   TBPM_CK_LAUNCH(ctx);
@@ -599,7 +740,8 @@ static int ensure_d64(tbpm_lattice* lat) {
 
 static void free_lattice_mem(tbpm_lattice* lat) {
   tbpm_ctx* ctx = lat->ctx;
-  void* ps[] = {lat->d32, lat->d64, lat->v64, lat->ell, lat->compact, lat->full_of};
+  void* ps[] = {lat->d32, lat->d64, lat->v64, lat->ell, lat->compact, lat->full_of, lat->wrel32, lat->wrel64,
+                lat->chunks};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, ctx->stream);
 }
@@ -630,6 +772,10 @@ int tbpm_lattice_create(tbpm_ctx* ctx, const tbpm_lattice_desc* desc, tbpm_latti
   }
   if (!(d.vacancy_frac >= 0.0 && d.vacancy_frac < 1.0)) {
     set_error("vacancy_frac must lie in [0, 1)");
+    return TBPM_EINVAL;
+  }
+  if (!(d.cutoff >= 0.0 && d.cutoff <= 12.0) || (d.cutoff > 0.0 && !(d.decay > 0.0 && isfinite(d.decay)))) {
+    set_error("cutoff must lie in [0, 12], and decay be finite and > 0 when cutoff > 0");
     return TBPM_EINVAL;
   }
   if (d.path < TBPM_PATH_AUTO || d.path > TBPM_PATH_CSR) {
@@ -722,6 +868,33 @@ int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, in
     }
   }
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return TBPM_OK;
+}
+
+int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t) {
+  clear_error();
+  if (!lat) {
+    set_error("tbpm_lattice_taps: NULL lattice");
+    return TBPM_EINVAL;
+  }
+  const int z = lat->geom.z;
+  if (!lat->tap_t.empty()) {
+    if (offsets)
+      for (int k = 0; k < 4 * z; ++k) offsets[k] = lat->tap_off[k];
+    if (t)
+      for (int k = 0; k < z; ++k) t[k] = lat->tap_t[k];
+    return TBPM_OK;
+  }
+  // nearest-neighbour lattices: the fixed neighbour order of a sublattice-0 site
+  static const int sq[4][4] = {{1, 0, 0, 0}, {-1, 0, 0, 0}, {0, 1, 0, 0}, {0, -1, 0, 0}};
+  static const int hc[3][4] = {{0, 0, 0, 1}, {-1, 0, 0, 1}, {0, -1, 0, 1}};
+  static const int cu[6][4] = {{1, 0, 0, 0}, {-1, 0, 0, 0}, {0, 1, 0, 0}, {0, -1, 0, 0}, {0, 0, 1, 0}, {0, 0, -1, 0}};
+  const int(*tab)[4] = lat->geom.kind == TBPM_SQUARE ? sq : lat->geom.kind == TBPM_HONEYCOMB ? hc : cu;
+  for (int d = 0; d < z; ++d) {
+    if (offsets)
+      for (int c = 0; c < 4; ++c) offsets[4 * d + c] = tab[d][c];
+    if (t) t[d] = lat->desc.t;
+  }
   return TBPM_OK;
 }
 
@@ -826,6 +999,14 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
   a->geom = lat->geom;
   a->path = lat->path;
   a->ell = lat->ell;
+  a->wrel = lat->wrel64 ? (pl.precision == TBPM_C128 ? (const void*)lat->wrel64 : (const void*)lat->wrel32) : nullptr;
+  if (lat->chunks && pl.precision == TBPM_C64 && pl.Spad >= 2) {
+    a->taps = lat->chunks;
+    a->taps_n0 = lat->n_chunks[0];
+    a->taps_n1 = lat->n_chunks[1];
+    a->taps_rx = lat->halo_x;
+    a->taps_ry = lat->halo_y;
+  }
   if (lat->has_v) {
     if (pl.precision == TBPM_C128) TBPM_TRY(ensure_d64(lat));
     a->diag = pl.precision == TBPM_C128 ? (const void*)lat->d64 : (const void*)lat->d32;
@@ -848,6 +1029,10 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
     TBPM_CK(cudaMemsetAsync(ctx->ws_counter.p, 0, ctx->ws_counter.cap, ctx->stream));
   }
   a->counter = (unsigned*)ctx->ws_counter.p;
+  if (a->taps) {
+    TBPM_TRY(ensure(ctx, ctx->ws_fused_partials, taps_partials_bytes(*a)));
+    a->tap_partials = (double*)ctx->ws_fused_partials.p;
+  }
   return TBPM_OK;
 }
 
@@ -1871,6 +2056,10 @@ int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  if (lat && lat->wrel64) {
+    set_error("tbpm_conductivity: the current operator is built for nearest-neighbour lattices only");
+    return TBPM_EUNSUPPORTED;
+  }
   Plan pl;
   TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
@@ -1895,6 +2084,10 @@ int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  if (lat && lat->wrel64) {
+    set_error("tbpm_conductivity: the current operator is built for nearest-neighbour lattices only");
+    return TBPM_EUNSUPPORTED;
+  }
   Plan pl;
   TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
@@ -1985,6 +2178,14 @@ int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tb
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  if (!lat) {
+    set_error("tbpm_optical_conductivity: lattice is NULL");
+    return TBPM_EINVAL;
+  }
+  if (lat->wrel64) {
+    set_error("tbpm_optical_conductivity: the current operator is built for nearest-neighbour lattices only");
+    return TBPM_EUNSUPPORTED;
+  }
   const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
   if (alpha < 0 || alpha >= dims || beta < 0 || beta >= dims) {
     set_error("directions must lie in [0, %d)", dims);

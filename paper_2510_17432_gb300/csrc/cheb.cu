@@ -1,7 +1,8 @@
 // Chebyshev recurrence kernels for blocks of S states (App. B, Eq. cheb_relation):
 //     phi_1 = H~ phi_0,   phi_{n+1} = 2 H~ phi_n - phi_{n-1},   H~ = (H - H0)/|H|,
 // with H applied matrix-free on square / honeycomb / simple-cubic stencils, or from
-// compact ELL neighbour lists on vacancy lattices (CSR/ELL path).
+// compact ELL neighbour lists on vacancy and long-range lattices (CSR/ELL path; long-range
+// lattices carry one weight t_d/t per neighbour slot d).
 //
 // States are interleaved [site][state] so one thread unit moves 16 bytes (two complex64
 // states, or one complex128 state) and the neighbour loads of all S states of a site are
@@ -48,7 +49,22 @@ __device__ __forceinline__ void neighbour_sum(const RecurrenceArgs& a, const Pac
   };
   if constexpr (CSR) {
     const int z = a.geom.z;
-    for (int d = 0; d < z; ++d) add((int64_t)__ldg(a.ell + site * z + d));
+    const int32_t* row = a.ell + site * z;
+    if (a.wrel) {
+      // long-range hopping: slot d carries the weight t_d / t
+      const R* w = reinterpret_cast<const R*>(a.wrel);
+      for (int d = 0; d < z; ++d) {
+        const int32_t j = __ldg(row + d);
+        if (j >= 0) {
+          const R wd = __ldg(w + d);
+          const Pack<R, SPT> q = ld(cur + (int64_t)j * a.P + p);
+#pragma unroll
+          for (int k = 0; k < 2 * SPT; ++k) h.v[k] = fma(wd, q.v[k], h.v[k]);
+        }
+      }
+    } else {
+      for (int d = 0; d < z; ++d) add((int64_t)__ldg(row + d));
+    }
   } else if constexpr (KIND == TBPM_HONEYCOMB) {
     const int64_t Lx = a.geom.Lx;
     const int64_t xc = sir >> 1;
@@ -734,6 +750,7 @@ static int launch(tbpm_ctx* ctx, void* fn, int nblocks, void** args) {
 int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first) {
   const bool csr = a.path == TBPM_PATH_CSR;
   const int spt = spt_of(precision, a.S);
+  if (a.taps && precision == TBPM_C64 && spt == 2) return launch_taps_moment(ctx, a, first);
   void* fn;
   if (precision == TBPM_C128) fn = moment_kernel<double, 1>(a.geom.kind, csr, first);
   else if (spt == 2) fn = moment_kernel<float, 2>(a.geom.kind, csr, first);

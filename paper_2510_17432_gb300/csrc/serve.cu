@@ -732,6 +732,10 @@ int tbpm_submit(tbpm_server* srv, const tbpm_lattice_desc* ldesc, const tbpm_req
     set_error("tbpm_submit: invalid lattice");
     return TBPM_EINVAL;
   }
+  if (ldesc->cutoff != 0.0) {
+    set_error("tbpm_submit: long-range hopping lattices are not served");
+    return TBPM_EUNSUPPORTED;
+  }
   ServeJob* j = new ServeJob();
   j->ldesc = *ldesc;
   if (j->ldesc.kind != TBPM_CUBIC) j->ldesc.L[2] = 1;

@@ -181,6 +181,14 @@ struct tbpm_ctx {
   std::vector<cudaEvent_t> event_pool;
 };
 
+// One piece of a column run of long-range taps for the matrix-free tap kernel: the taps
+// (dx, dy0 + k, ds), k < n (n = 4 or 8), of one destination sublattice, with weights t_k/t
+// (0 where the run has a hole or the piece is padded).
+struct TapChunk {
+  int dx, dy0, ds, n;
+  float w[8];
+};
+
 struct tbpm_lattice {
   tbpm_ctx* ctx = nullptr;
   tbpm_lattice_desc desc{};
@@ -196,6 +204,17 @@ struct tbpm_lattice {
   double* v64 = nullptr;       // raw V_i (FP64) per active site, for export
   // CSR/ELL path: compact neighbour lists [n_sites][z] (-1 = none)
   int32_t* ell = nullptr;
+  // long-range hopping: per-slot weights t_k / t (slot k of every ELL list), FP32 and FP64;
+  // null on nearest-neighbour lattices (every bond t)
+  float* wrel32 = nullptr;
+  double* wrel64 = nullptr;
+  std::vector<int> tap_off;      // [z][4] (dx, dy, dz, ds) of each slot (long-range only)
+  std::vector<double> tap_t;     // [z] t(r) of each slot (long-range only)
+  // matrix-free tap kernel (clean long-range square / honeycomb lattices): column-run pieces
+  // of destination sublattice 0 then 1 on the device, their counts and the tile halo
+  TapChunk* chunks = nullptr;
+  int n_chunks[2] = {0, 0};
+  int halo_x = 0, halo_y = 0;
   int64_t* compact = nullptr;  // [n_full] compact index or -1 (CSR path only)
   int64_t* full_of = nullptr;  // [n_sites] full index of each compact site (CSR path only)
 };
@@ -218,6 +237,11 @@ struct RecurrenceArgs {
   Geom geom;
   int path;
   const int32_t* ell;  // CSR/ELL neighbour lists
+  const void* wrel;    // per-slot weights t_k/t (float* or double*), or null (every bond t)
+  // matrix-free tap kernel (complex64, >= 2 states): chunk table, counts, halo, partial sums
+  const TapChunk* taps;
+  int taps_n0, taps_n1, taps_rx, taps_ry;
+  double* tap_partials;
   const void* diag;    // per-site D_i (float* or double*), or null when the lattice is clean
   double diag_const;   // D when diag == null
   double thop;         // t / |H|
@@ -262,6 +286,11 @@ inline void set_float_coefficients(RecurrenceArgs* a) {
 }
 
 int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first);
+// matrix-free tap kernel (csrc/taps.cu): chunk table of a clean long-range lattice, the moment
+// pass over it, and the size of its per-CTA partial sums
+int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat);
+int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);
+size_t taps_partials_bytes(const RecurrenceArgs& a);
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);

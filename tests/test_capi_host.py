@@ -48,8 +48,9 @@ def test_library_exports_every_declared_symbol(capi):
 
 def test_struct_layout_matches_header(capi):
     # offsets follow the C declarations with natural alignment
-    assert ctypes.sizeof(capi.LatticeDesc) == 80
+    assert ctypes.sizeof(capi.LatticeDesc) == 96
     assert capi.LatticeDesc.t.offset == 48 and capi.LatticeDesc.seed.offset == 72
+    assert capi.LatticeDesc.cutoff.offset == 80 and capi.LatticeDesc.decay.offset == 88
     assert ctypes.sizeof(capi.Request) == 72
     assert capi.Request.state_seed.offset == 16 and capi.Request.tau.offset == 48
     assert ctypes.sizeof(capi.LatticeProps) == 64

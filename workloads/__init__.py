@@ -12,7 +12,7 @@ Lattice kinds follow the tight-binding models of the paper's test systems
 (nearest-neighbour graphene, Fig. 1; a square lattice and a simple-cubic lattice as
 further regular stencils).  The paper's own primary test system (twisted bilayer
 graphene, Sec. II.B) is not reproducible without its geometry; honeycomb
-lattices stand in for it.
+lattices stand in for it, with long-range hopping where the density D_H matters.
 """
 from __future__ import annotations
 
@@ -43,6 +43,8 @@ class LatticeSpec:
     seed: int = LATTICE_SEED
     pbc: tuple = (1, 1, 1)
     path: int = PATH_AUTO
+    cutoff: float = 0.0       # long-range hopping radius (0: nearest neighbours)
+    decay: float = 0.0        # decay length of t(r) = t exp(-(r - 1)/decay)
 
     @property
     def n_full(self) -> int:
@@ -106,6 +108,25 @@ GRAPHENE_22528 = Workload(
     n_states=4, n_moments=8192, precision=C64, n_energies=2048,
     description="graphene 22528x22528 cells (1,015,021,568 sites), V in [-0.5,0.5] eV, stencil, "
                 "complex64, 4 states, 8192 moments")
+
+
+# Dense Hamiltonians standing in for the paper's 4,763,200-atom twisted bilayer graphene, whose
+# density D_H it varies over 60, 120 and 230 (Sec. IV): a honeycomb sample of the same number of
+# sites with every neighbour within the cutoff bonded, t(r) = t exp(-(r - 1)/decay), decay
+# 0.3187 nearest-neighbour distances (0.184 lattice constants, the decay of the usual pz model
+# of graphene bilayers).  Cutoffs 5.1, 7.1 and 9.7 give D_H = 61, 124 and 235 (taps + diagonal).
+DENSE_DECAY = 0.3187
+DENSE_CUTOFFS = {61: 5.1, 124: 7.1, 235: 9.7}
+
+
+def dense_honeycomb(dh: int, n_states: int = 2, n_steps: int = 4096) -> Workload:
+    cutoff = DENSE_CUTOFFS[dh]
+    return Workload(
+        f"honeycomb1832x1300_DH{dh}_S{n_states}_Nt{n_steps}",
+        honeycomb(1832, 1300, t=-2.7, W=0.0, cutoff=cutoff, decay=DENSE_DECAY),
+        n_states=n_states, n_moments=0, precision=C64, n_steps=n_steps, n_energies=2048,
+        description=f"honeycomb 1832x1300 cells (4,763,200 sites), long-range hopping within {cutoff} "
+                    f"(D_H = {dh}), complex64, {n_states} states, DOS over N_t = {n_steps} steps of tau~ = pi")
 
 
 def uniform_energy_grid(n: int, lo: float, hi: float) -> np.ndarray:
