@@ -764,6 +764,12 @@ int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bo
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode) {
   const bool csr = g.r.path == TBPM_PATH_CSR;
   const int spt = spt_of(precision, g.r.S);
+  if (g.r.taps && precision == TBPM_C64 && spt == 2 && mode != ACC_NOSPMV) {
+    // long-range lattices: the matrix-free recurrence step, then the accumulate-only pass on phi_n
+    TBPM_TRY(launch_taps_step(ctx, g.r, mode == ACC_FIRST));
+    if (g.j_lo >= g.b && g.j_done < 0) return TBPM_OK;
+    mode = ACC_NOSPMV;
+  }
   void* fn;
   if (precision == TBPM_C128) fn = accum_kernel<double, 1>(g.r.geom.kind, csr, mode);
   else if (spt == 2) fn = accum_kernel<float, 2>(g.r.geom.kind, csr, mode);

@@ -77,7 +77,9 @@ __device__ __forceinline__ void tap_piece(float4 (&acc)[kTapOY], const float4* c
   }
 }
 
-template <int NSUB, bool FIRST>
+// MOM: fuse the moment sums (moment pass); without it the kernel is the plain recurrence step
+// that the accumulation passes pair with an accumulate-only pass.
+template <int NSUB, bool FIRST, bool MOM>
 __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a) {
   constexpr int TX = TapShape<NSUB>::TX;
   extern __shared__ float4 smem[];
@@ -156,14 +158,17 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
         out.w -= pv.w;
       }
       po[off] = out;
-      A0.add(ph.x * ph.x + ph.y * ph.y);
-      R0.add(out.x * ph.x + out.y * ph.y);
-      I0.add(out.x * ph.y - out.y * ph.x);
-      A1.add(ph.z * ph.z + ph.w * ph.w);
-      R1.add(out.z * ph.z + out.w * ph.w);
-      I1.add(out.z * ph.w - out.w * ph.z);
+      if constexpr (MOM) {
+        A0.add(ph.x * ph.x + ph.y * ph.y);
+        R0.add(out.x * ph.x + out.y * ph.y);
+        I0.add(out.x * ph.y - out.y * ph.x);
+        A1.add(ph.z * ph.z + ph.w * ph.w);
+        R1.add(out.z * ph.z + out.w * ph.w);
+        I1.add(out.z * ph.w - out.w * ph.z);
+      }
     }
   }
+  if constexpr (!MOM) return;
 
   // CTA sums (fixed trees), per-CTA partials, the last CTA sums them in CTA order
   double v[6] = {A0.value(), R0.value(), I0.value(), A1.value(), R1.value(), I1.value()};
@@ -241,7 +246,7 @@ size_t taps_partials_bytes(const RecurrenceArgs& a) {
   return sizeof(double) * 6 * (size_t)g;
 }
 
-int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) {
+static int launch_taps(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first, bool mom) {
   const bool hc = a.geom.kind == TBPM_HONEYCOMB;
   const int nch = a.taps_n0 + (hc ? a.taps_n1 : 0);
   const size_t smem = hc ? tap_smem<2>(a.taps_rx, a.taps_ry, nch) : tap_smem<1>(a.taps_rx, a.taps_ry, nch);
@@ -250,8 +255,13 @@ int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) {
     set_error("tap kernel: grid %lld or shared memory %zu out of range", (long long)grid, smem);
     return TBPM_EUNSUPPORTED;
   }
-  void* fn = hc ? (first ? (void*)k_taps_moment<2, true> : (void*)k_taps_moment<2, false>)
-                : (first ? (void*)k_taps_moment<1, true> : (void*)k_taps_moment<1, false>);
+  void* fn;
+  if (mom)
+    fn = hc ? (first ? (void*)k_taps_moment<2, true, true> : (void*)k_taps_moment<2, false, true>)
+            : (first ? (void*)k_taps_moment<1, true, true> : (void*)k_taps_moment<1, false, true>);
+  else
+    fn = hc ? (first ? (void*)k_taps_moment<2, true, false> : (void*)k_taps_moment<2, false, false>)
+            : (first ? (void*)k_taps_moment<1, true, false> : (void*)k_taps_moment<1, false, false>);
   TBPM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   RecurrenceArgs aa = a;
   void* args[] = {&aa};
@@ -263,6 +273,10 @@ int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) {
   }
   return TBPM_OK;
 }
+
+int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) { return launch_taps(ctx, a, first, true); }
+
+int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) { return launch_taps(ctx, a, first, false); }
 
 // Column-run pieces of the taps of every destination sublattice.  Sublattice 1 of the honeycomb
 // takes each tap mirrored, (-dx, -dy, 1-ds), as the ELL builder does.  A run of one (dx, ds)

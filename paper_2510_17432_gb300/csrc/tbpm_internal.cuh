@@ -290,6 +290,7 @@ int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bo
 // pass over it, and the size of its per-CTA partial sums
 int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat);
 int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);
+int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);  // recurrence only
 size_t taps_partials_bytes(const RecurrenceArgs& a);
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
