@@ -825,23 +825,37 @@ def run_dense(args, work):
     e2e = {"value": whole_job_rate(site_updates, world, e2e_s), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
 
-    # roofline of the recurrence pass: ELL lists (z int32 per site) + three state blocks per step
+    # roofline of the recurrence pass.  Clean lattices with complex64 and >= 2 states run the
+    # matrix-free tap kernel, bound by FP32 FMA issue: 2 FMAs (real weight x complex state) per tap
+    # per site-update, against 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (the part's unit
+    # counts and maximum clock).  Otherwise the ELL kernel: HBM-bound on the index lists.
     z = info.coordination
     elem = 8 if work.precision == capi.C64 else 16
     per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
-    bytes_per_launch = (3.0 * elem * S + 4.0 * z) * info.n_sites
     peak, peak_kind = measured_hbm_peak()
-    achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
-    fma_per_launch = 2.0 * z * info.n_sites * S          # real x complex: two FMAs per tap
+    state_bytes = 3.0 * elem * S * info.n_sites
+    flops_per_launch = 4.0 * z * info.n_sites * S
     sm_count, lanes, fmax = 152, 128, 2.070e9
-    alu_peak = sm_count * lanes * fmax * 2 / 1e12           # FP32 TFLOP/s (FMA = 2 flops)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind,
-                "kernel": "k_moment_step<CSR, complex64 x%d per thread> (ELL lists + per-slot weights)" % (2 if S >= 2 else 1),
-                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
-                "fp32_tflops": 2 * fma_per_launch / (per_launch_ms / 1e3) / 1e12,
-                "fp32_peak_tflops": alu_peak,
-                "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+    alu_peak = sm_count * lanes * fmax * 2 / 1e12
+    taps = work.precision == capi.C64 and S >= 2 and spec.vacancy_frac == 0 and spec.kind != wl.CUBIC
+    if taps:
+        achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
+                    "kernel": "k_taps_moment<honeycomb> (matrix-free taps, two complex64 states per pack)",
+                    "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_us": per_launch_ms * 1e3,
+                    "hbm_algorithmic_gbs": state_bytes / (per_launch_ms / 1e3) / 1e9, "hbm_peak_gbs": peak,
+                    "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+    else:
+        bytes_per_launch = state_bytes + 4.0 * z * info.n_sites
+        achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": peak_kind,
+                    "kernel": "k_moment_step<CSR> (ELL lists + per-slot weights)",
+                    "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
+                    "fp32_tflops": flops_per_launch / (per_launch_ms / 1e3) / 1e12, "fp32_peak_tflops": alu_peak,
+                    "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
     out = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -850,7 +864,8 @@ def run_dense(args, work):
         "config": {"workload": work.name, "sites": info.n_sites, "D_H": z + 1, "states": S, "n_steps": Nt,
                    "moments": Mtot, "matrix_applications": n_mat, "energies": nE,
                    "form": "concurrent moment-based DOS (Hann-windowed Fourier of C(t) from moments)",
-                   "l2": "inputs larger than L2 (ELL lists %.1f GB)" % (4.0 * z * info.n_sites / 1e9),
+                   "l2": "working set larger than L2: two state blocks of %.0f MB each are read and one written "
+                         "per launch (L2 129 MB)" % (info.n_sites * S * elem / 1e6),
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
     }
