@@ -2056,10 +2056,6 @@ int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
-  if (lat && lat->wrel64) {
-    set_error("tbpm_conductivity: the current operator is built for nearest-neighbour lattices only");
-    return TBPM_EUNSUPPORTED;
-  }
   Plan pl;
   TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
