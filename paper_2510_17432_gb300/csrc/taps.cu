@@ -28,6 +28,11 @@
 namespace tbpm {
 namespace {
 
+// build-time switch between packed (f32x2) and scalar FMAs in the tap loop
+#ifndef TBPM_TAPS_FFMA2
+#define TBPM_TAPS_FFMA2 0
+#endif
+
 constexpr int kTapOY = 16;        // output rows per thread
 constexpr int kTapThreads = 128;  // 4 warps
 constexpr int kTapMaxSmem = 227 * 1024;
@@ -61,6 +66,27 @@ __device__ __forceinline__ void tap_piece(float4 (&acc)[kTapOY], const float4* c
     wr[k + 2] = q.z;
     wr[k + 3] = q.w;
   }
+#if TBPM_TAPS_FFMA2
+  // packed FP32 pairs: one instruction per two FMAs frees issue slots for the shared loads
+  float2 w2[NW];
+#pragma unroll
+  for (int k = 0; k < NW; ++k) w2[k] = make_float2(wr[k], wr[k]);
+#pragma unroll
+  for (int j = 0; j < kTapOY + NW - 1; ++j) {
+    const float4 v = col[j * rs];
+    const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const int o = j - k;
+      if (o >= 0 && o < kTapOY) {
+        float2 al = make_float2(acc[o].x, acc[o].y), ah = make_float2(acc[o].z, acc[o].w);
+        al = __ffma2_rn(w2[k], lo, al);
+        ah = __ffma2_rn(w2[k], hi, ah);
+        acc[o] = make_float4(al.x, al.y, ah.x, ah.y);
+      }
+    }
+  }
+#else
 #pragma unroll
   for (int j = 0; j < kTapOY + NW - 1; ++j) {
     const float4 v = col[j * rs];
@@ -75,6 +101,7 @@ __device__ __forceinline__ void tap_piece(float4 (&acc)[kTapOY], const float4* c
       }
     }
   }
+#endif
 }
 
 // MOM: fuse the moment sums (moment pass); without it the kernel is the plain recurrence step
@@ -89,8 +116,12 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
   TapChunk* ch = reinterpret_cast<TapChunk*>(smem + (size_t)TH * RS);
   const int nch = a.taps_n0 + (NSUB == 2 ? a.taps_n1 : 0);
   static_assert(sizeof(TapChunk) == 48, "chunk = 3 float4");
-  for (int i = threadIdx.x; i < 3 * nch; i += kTapThreads)
-    reinterpret_cast<float4*>(ch)[i] = __ldg(reinterpret_cast<const float4*>(a.taps) + i);
+  for (int i = threadIdx.x; i < 3 * nch; i += kTapThreads) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<float4*>(ch) + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                 "l"(reinterpret_cast<const float4*>(a.taps) + i)
+                 : "memory");
+  }
 
   const int P = a.P;
   const int p = (int)(blockIdx.x % (unsigned)P);
@@ -101,7 +132,8 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
   const float4* cur = reinterpret_cast<const float4*>(a.cur);
   float4* po = reinterpret_cast<float4*>(a.prev_out);
 
-  // stage phi_n of the tile and its halo (wrapped on periodic sides, zero on open ones)
+  // stage phi_n of the tile and its halo (wrapped on periodic sides, zero on open ones) with
+  // asynchronous 16-byte copies, all in flight at once
   const int total = TH * TW * NSUB;
   for (int e = threadIdx.x; e < total; e += kTapThreads) {
     const int s = NSUB == 2 ? (e & 1) : 0;
@@ -110,10 +142,13 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
     bool ok = true;
     const int64_t gx = tap_wrap(x0 - RX + tx, Lx, a.geom.pbc_x, &ok);
     const int64_t gy = tap_wrap(y0 - RY + ty, Ly, a.geom.pbc_y, &ok);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (ok) v = __ldg(cur + ((gy * Lx + gx) * NSUB + s) * P + p);
-    tile[ty * RS + s * TW + tx] = v;
+    const float4* src = ok ? cur + ((gy * Lx + gx) * NSUB + s) * P + p : cur;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ty * RS + s * TW + tx);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                 : "memory");
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

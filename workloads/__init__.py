@@ -119,13 +119,14 @@ DENSE_DECAY = 0.3187
 DENSE_CUTOFFS = {61: 5.1, 124: 7.1, 235: 9.7}
 
 
-def dense_honeycomb(dh: int, n_states: int = 2, n_steps: int = 4096) -> Workload:
+def dense_honeycomb(dh: int, n_states: int = 2, n_steps: int = 4096, L=(1832, 1300)) -> Workload:
     cutoff = DENSE_CUTOFFS[dh]
+    Lx, Ly = L
     return Workload(
-        f"honeycomb1832x1300_DH{dh}_S{n_states}_Nt{n_steps}",
-        honeycomb(1832, 1300, t=-2.7, W=0.0, cutoff=cutoff, decay=DENSE_DECAY),
+        f"honeycomb{Lx}x{Ly}_DH{dh}_S{n_states}_Nt{n_steps}",
+        honeycomb(Lx, Ly, t=-2.7, W=0.0, cutoff=cutoff, decay=DENSE_DECAY),
         n_states=n_states, n_moments=0, precision=C64, n_steps=n_steps, n_energies=2048,
-        description=f"honeycomb 1832x1300 cells (4,763,200 sites), long-range hopping within {cutoff} "
+        description=f"honeycomb {Lx}x{Ly} cells ({2 * Lx * Ly} sites), long-range hopping within {cutoff} "
                     f"(D_H = {dh}), complex64, {n_states} states, DOS over N_t = {n_steps} steps of tau~ = pi")
 
 
