@@ -30,7 +30,7 @@ namespace {
 
 // build-time switch between packed (f32x2) and scalar FMAs in the tap loop
 #ifndef TBPM_TAPS_FFMA2
-#define TBPM_TAPS_FFMA2 0
+#define TBPM_TAPS_FFMA2 1
 #endif
 
 constexpr int kTapOY = 16;        // output rows per thread
