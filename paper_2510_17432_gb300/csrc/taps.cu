@@ -7,8 +7,8 @@
 // few states the CSR/ELL form of such a matrix reads ~4 D_H bytes of indices per site and
 // step, more than the states themselves.  Here the taps are the same for every site, so no
 // index is stored: a CTA stages a halo'd tile of phi_n (one 16-byte pack = two complex64
-// states per site) in shared memory and each thread computes 16 consecutive rows of one
-// column of cells.  The taps of one destination sublattice, grouped by (dx, source
+// states per site; 64 honeycomb or 128 square cells by 32 rows) in shared memory and each
+// thread computes 16 consecutive rows of one column of cells.  The taps of one destination sublattice, grouped by (dx, source
 // sublattice), form runs along y; a run piece of n = 4 or 8 taps is applied to the 16 rows
 // as a sliding window, so each shared load feeds up to n x 16 FMAs and the pass is bound by
 // FP32 FMA issue rather than by HBM (2 (D_H - 1) FMAs per site-update against 24 bytes).
@@ -33,8 +33,16 @@ namespace {
 #define TBPM_TAPS_FFMA2 1
 #endif
 
-constexpr int kTapOY = 16;        // output rows per thread
-constexpr int kTapThreads = 128;  // 4 warps
+// row blocks of 16 rows per CTA (4 warps each); two give 8-warp CTAs, two per SM
+#ifndef TBPM_TAPS_RB
+#define TBPM_TAPS_RB 2
+#endif
+
+constexpr int kTapOY = 16;                       // output rows per thread
+constexpr int kTapRB = TBPM_TAPS_RB;
+constexpr int kTapTY = kTapOY * kTapRB;          // rows per tile
+constexpr int kTapThreads = 128 * kTapRB;
+constexpr int kTapMinBlocks = kTapRB == 1 ? 3 : 2;
 constexpr int kTapMaxSmem = 227 * 1024;
 
 // cells per tile along x: 64 (two warps per sublattice) on the honeycomb, 128 on the square
@@ -107,11 +115,11 @@ __device__ __forceinline__ void tap_piece(float4 (&acc)[kTapOY], const float4* c
 // MOM: fuse the moment sums (moment pass); without it the kernel is the plain recurrence step
 // that the accumulation passes pair with an accumulate-only pass.
 template <int NSUB, bool FIRST, bool MOM>
-__global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a) {
+__global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(RecurrenceArgs a) {
   constexpr int TX = TapShape<NSUB>::TX;
   extern __shared__ float4 smem[];
   const int RX = a.taps_rx, RY = a.taps_ry;
-  const int TW = TX + 2 * RX, TH = kTapOY + 2 * RY, RS = NSUB * TW;
+  const int TW = TX + 2 * RX, TH = kTapTY + 2 * RY, RS = NSUB * TW;
   float4* tile = smem;
   TapChunk* ch = reinterpret_cast<TapChunk*>(smem + (size_t)TH * RS);
   const int nch = a.taps_n0 + (NSUB == 2 ? a.taps_n1 : 0);
@@ -128,7 +136,7 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
   const int64_t tile_id = blockIdx.x / (unsigned)P;
   const int64_t Lx = a.geom.Lx, Ly = a.geom.Ly;
   const int64_t ntx = (Lx + TX - 1) / TX;
-  const int64_t x0 = (tile_id % ntx) * TX, y0 = (tile_id / ntx) * kTapOY;
+  const int64_t x0 = (tile_id % ntx) * TX, y0 = (tile_id / ntx) * kTapTY;
   const float4* cur = reinterpret_cast<const float4*>(a.cur);
   float4* po = reinterpret_cast<float4*>(a.prev_out);
 
@@ -152,15 +160,17 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sub = NSUB == 2 ? (warp & 1) : 0;
-  const int xl = (NSUB == 2 ? (warp >> 1) : warp) * 32 + lane;
+  const int lw = warp & 3, rb = warp >> 2;  // warp within its row block, row block
+  const int sub = NSUB == 2 ? (lw & 1) : 0;
+  const int xl = (NSUB == 2 ? (lw >> 1) : lw) * 32 + lane;
+  const int r0 = RY + rb * kTapOY;          // tile row of this thread's first output row
   float4 acc[kTapOY];
 #pragma unroll
   for (int o = 0; o < kTapOY; ++o) acc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
   const int c_lo = sub == 0 ? 0 : a.taps_n0, c_hi = sub == 0 ? a.taps_n0 : nch;
   for (int c = c_lo; c < c_hi; ++c) {
     const int4 hd = *reinterpret_cast<const int4*>(ch + c);  // dx, dy0, ds, n
-    const float4* col = tile + (RY + hd.y) * RS + hd.z * TW + RX + xl + hd.x;
+    const float4* col = tile + (r0 + hd.y) * RS + hd.z * TW + RX + xl + hd.x;
     if (hd.w == 8)
       tap_piece<8>(acc, col, RS, ch[c].w);
     else
@@ -173,11 +183,11 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
   const int64_t x = x0 + xl;
 #pragma unroll
   for (int o = 0; o < kTapOY; ++o) {
-    const int64_t y = y0 + o;
+    const int64_t y = y0 + rb * kTapOY + o;
     if (x < Lx && y < Ly) {
       const int64_t site = (y * Lx + x) * NSUB + sub;
       const int64_t off = site * P + p;
-      const float4 ph = tile[(RY + o) * RS + sub * TW + RX + xl];
+      const float4 ph = tile[(r0 + o) * RS + sub * TW + RX + xl];
       float d = a.diag ? __ldg(reinterpret_cast<const float*>(a.diag) + site) : a.dc1f;
       if (!FIRST) d = d + d;
       float4 out;
@@ -265,13 +275,13 @@ __global__ void __launch_bounds__(kTapThreads, 3) k_taps_moment(RecurrenceArgs a
 template <int NSUB>
 int64_t tap_grid(const RecurrenceArgs& a) {
   constexpr int TX = TapShape<NSUB>::TX;
-  return ((a.geom.Lx + TX - 1) / TX) * ((a.geom.Ly + kTapOY - 1) / kTapOY) * a.P;
+  return ((a.geom.Lx + TX - 1) / TX) * ((a.geom.Ly + kTapTY - 1) / kTapTY) * a.P;
 }
 
 template <int NSUB>
 size_t tap_smem(int rx, int ry, int nch) {
   constexpr int TX = TapShape<NSUB>::TX;
-  return (size_t)(kTapOY + 2 * ry) * NSUB * (TX + 2 * rx) * 16 + (size_t)nch * sizeof(TapChunk);
+  return (size_t)(kTapTY + 2 * ry) * NSUB * (TX + 2 * rx) * 16 + (size_t)nch * sizeof(TapChunk);
 }
 
 }  // namespace
