@@ -9,8 +9,8 @@
 // index is stored: a CTA stages a halo'd tile of phi_n (one 16-byte pack = two complex64
 // states per site; 64 honeycomb or 128 square cells by 32 rows) in shared memory and each
 // thread computes 16 consecutive rows of one column of cells.  The taps of one destination sublattice, grouped by (dx, source
-// sublattice), form runs along y; a run piece of n = 4 or 8 taps is applied to the 16 rows
-// as a sliding window, so each shared load feeds up to n x 16 FMAs and the pass is bound by
+// sublattice), form runs along y; a run piece of n <= 8 taps is applied to the 16 rows
+// as a sliding window, so each shared load feeds up to 4n FMAs and the pass is bound by
 // FP32 FMA issue rather than by HBM (2 (D_H - 1) FMAs per site-update against 24 bytes).
 //
 // Reductions follow the other moment kernels: Neumaier-compensated FP32 per thread, an FP64
@@ -28,14 +28,14 @@
 namespace tbpm {
 namespace {
 
-// build-time switch between packed (f32x2) and scalar FMAs in the tap loop
-#ifndef TBPM_TAPS_FFMA2
-#define TBPM_TAPS_FFMA2 1
-#endif
-
 // row blocks of 16 rows per CTA (4 warps each); two give 8-warp CTAs, two per SM
 #ifndef TBPM_TAPS_RB
 #define TBPM_TAPS_RB 2
+#endif
+
+// run pieces: every length 1..8 (1), or lengths 8, 4, 2, 1 only (0: fewer kernel variants)
+#ifndef TBPM_TAPS_EXACT
+#define TBPM_TAPS_EXACT 0
 #endif
 
 constexpr int kTapOY = 16;                       // output rows per thread
@@ -62,54 +62,29 @@ __device__ __forceinline__ int64_t tap_wrap(int64_t v, int64_t L, int periodic, 
   return r < 0 ? r + L : r;
 }
 
-// acc[o] += sum_k w[k] col[(o + k) rs] for the 16 rows o: a sliding window over NW + 15 rows
+// acc[o] += sum_k w[k] col[(o + k) rs] for the 16 rows o: a sliding window over NW + 15 rows.
+// The two states of a pack are two FP32 pairs (lo, hi); each pair takes one packed f32x2 FMA
+// with the tap weight duplicated in both halves (stored that way in the chunk table, read
+// through the read-only cache).
 template <int NW>
-__device__ __forceinline__ void tap_piece(float4 (&acc)[kTapOY], const float4* col, int rs, const float* w) {
-  float wr[NW];
-#pragma unroll
-  for (int k = 0; k < NW; k += 4) {
-    const float4 q = *reinterpret_cast<const float4*>(w + k);
-    wr[k] = q.x;
-    wr[k + 1] = q.y;
-    wr[k + 2] = q.z;
-    wr[k + 3] = q.w;
-  }
-#if TBPM_TAPS_FFMA2
-  // packed FP32 pairs: one instruction per two FMAs frees issue slots for the shared loads
+__device__ __forceinline__ void tap_piece(float2 (&lo)[kTapOY], float2 (&hi)[kTapOY], const float4* col, int rs,
+                                          const float2* w) {
   float2 w2[NW];
 #pragma unroll
-  for (int k = 0; k < NW; ++k) w2[k] = make_float2(wr[k], wr[k]);
+  for (int k = 0; k < NW; ++k) w2[k] = __ldg(w + k);
 #pragma unroll
   for (int j = 0; j < kTapOY + NW - 1; ++j) {
     const float4 v = col[j * rs];
-    const float2 lo = make_float2(v.x, v.y), hi = make_float2(v.z, v.w);
+    const float2 vl = make_float2(v.x, v.y), vh = make_float2(v.z, v.w);
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
       const int o = j - k;
       if (o >= 0 && o < kTapOY) {
-        float2 al = make_float2(acc[o].x, acc[o].y), ah = make_float2(acc[o].z, acc[o].w);
-        al = __ffma2_rn(w2[k], lo, al);
-        ah = __ffma2_rn(w2[k], hi, ah);
-        acc[o] = make_float4(al.x, al.y, ah.x, ah.y);
+        lo[o] = __ffma2_rn(w2[k], vl, lo[o]);
+        hi[o] = __ffma2_rn(w2[k], vh, hi[o]);
       }
     }
   }
-#else
-#pragma unroll
-  for (int j = 0; j < kTapOY + NW - 1; ++j) {
-    const float4 v = col[j * rs];
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      const int o = j - k;
-      if (o >= 0 && o < kTapOY) {
-        acc[o].x = fmaf(wr[k], v.x, acc[o].x);
-        acc[o].y = fmaf(wr[k], v.y, acc[o].y);
-        acc[o].z = fmaf(wr[k], v.z, acc[o].z);
-        acc[o].w = fmaf(wr[k], v.w, acc[o].w);
-      }
-    }
-  }
-#endif
 }
 
 // MOM: fuse the moment sums (moment pass); without it the kernel is the plain recurrence step
@@ -121,15 +96,11 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
   const int RX = a.taps_rx, RY = a.taps_ry;
   const int TW = TX + 2 * RX, TH = kTapTY + 2 * RY, RS = NSUB * TW;
   float4* tile = smem;
-  TapChunk* ch = reinterpret_cast<TapChunk*>(smem + (size_t)TH * RS);
+  // the chunk table stays in global memory: every warp reads the same piece at once (one
+  // broadcast L1 line), which keeps shared memory for two tiles per SM
+  const TapChunk* ch = a.taps;
   const int nch = a.taps_n0 + (NSUB == 2 ? a.taps_n1 : 0);
-  static_assert(sizeof(TapChunk) == 48, "chunk = 3 float4");
-  for (int i = threadIdx.x; i < 3 * nch; i += kTapThreads) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<float4*>(ch) + i);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
-                 "l"(reinterpret_cast<const float4*>(a.taps) + i)
-                 : "memory");
-  }
+  static_assert(sizeof(TapChunk) == 80, "chunk = 5 float4");
 
   const int P = a.P;
   const int p = (int)(blockIdx.x % (unsigned)P);
@@ -164,17 +135,26 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
   const int sub = NSUB == 2 ? (lw & 1) : 0;
   const int xl = (NSUB == 2 ? (lw >> 1) : lw) * 32 + lane;
   const int r0 = RY + rb * kTapOY;          // tile row of this thread's first output row
-  float4 acc[kTapOY];
+  float2 lo[kTapOY], hi[kTapOY];
 #pragma unroll
-  for (int o = 0; o < kTapOY; ++o) acc[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int o = 0; o < kTapOY; ++o) lo[o] = hi[o] = make_float2(0.f, 0.f);
   const int c_lo = sub == 0 ? 0 : a.taps_n0, c_hi = sub == 0 ? a.taps_n0 : nch;
   for (int c = c_lo; c < c_hi; ++c) {
-    const int4 hd = *reinterpret_cast<const int4*>(ch + c);  // dx, dy0, ds, n
+    const int4 hd = __ldg(reinterpret_cast<const int4*>(ch + c));  // dx, dy0, ds, n
     const float4* col = tile + (r0 + hd.y) * RS + hd.z * TW + RX + xl + hd.x;
-    if (hd.w == 8)
-      tap_piece<8>(acc, col, RS, ch[c].w);
-    else
-      tap_piece<4>(acc, col, RS, ch[c].w);
+    const float2* w = ch[c].w;
+    switch (hd.w) {
+      case 8: tap_piece<8>(lo, hi, col, RS, w); break;
+#if TBPM_TAPS_EXACT
+      case 7: tap_piece<7>(lo, hi, col, RS, w); break;
+      case 6: tap_piece<6>(lo, hi, col, RS, w); break;
+      case 5: tap_piece<5>(lo, hi, col, RS, w); break;
+      case 3: tap_piece<3>(lo, hi, col, RS, w); break;
+#endif
+      case 4: tap_piece<4>(lo, hi, col, RS, w); break;
+      case 2: tap_piece<2>(lo, hi, col, RS, w); break;
+      default: tap_piece<1>(lo, hi, col, RS, w); break;
+    }
   }
 
   // phi_{n+1} = d phi_n + th h (- phi_{n-1}) and the moment sums of the two states
@@ -191,10 +171,10 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
       float d = a.diag ? __ldg(reinterpret_cast<const float*>(a.diag) + site) : a.dc1f;
       if (!FIRST) d = d + d;
       float4 out;
-      out.x = d * ph.x + th * acc[o].x;
-      out.y = d * ph.y + th * acc[o].y;
-      out.z = d * ph.z + th * acc[o].z;
-      out.w = d * ph.w + th * acc[o].w;
+      out.x = d * ph.x + th * lo[o].x;
+      out.y = d * ph.y + th * lo[o].y;
+      out.z = d * ph.z + th * hi[o].x;
+      out.w = d * ph.w + th * hi[o].y;
       if (!FIRST) {
         const float4 pv = __ldcs(po + off);
         out.x -= pv.x;
@@ -281,7 +261,7 @@ int64_t tap_grid(const RecurrenceArgs& a) {
 template <int NSUB>
 size_t tap_smem(int rx, int ry, int nch) {
   constexpr int TX = TapShape<NSUB>::TX;
-  return (size_t)(kTapTY + 2 * ry) * NSUB * (TX + 2 * rx) * 16 + (size_t)nch * sizeof(TapChunk);
+  return (size_t)(kTapTY + 2 * ry) * NSUB * (TX + 2 * rx) * 16;
 }
 
 }  // namespace
@@ -325,19 +305,18 @@ int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) { retur
 
 // Column-run pieces of the taps of every destination sublattice.  Sublattice 1 of the honeycomb
 // takes each tap mirrored, (-dx, -dy, 1-ds), as the ELL builder does.  A run of one (dx, ds)
-// spans its lowest to highest dy (holes weigh 0) and is cut into pieces of 8 taps, the last
-// one of 4 when at most 4 taps remain; a piece that would reach past the largest |dy| of any
-// tap starts lower instead (its rows already covered weigh 0), so the tile halo stays that
-// largest |dy|.  Lattices whose tile would not fit shared memory, cubic lattices and lattices
-// with vacancies keep the ELL path only.
+// spans its lowest to highest dy (holes weigh 0) and is cut into pieces of 8 taps and then of
+// 4, 2 and 1 (or one piece of the 1..7 that remain), so the tile halo is the largest |dx| and
+// |dy| of any tap.  Lattices
+// whose tile would not fit shared memory, cubic lattices and lattices with vacancies keep the
+// ELL path only.
 int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
   const tbpm_lattice_desc& d = lat->desc;
   if (lat->tap_t.empty() || d.kind == TBPM_CUBIC || d.vacancy_frac > 0.0) return TBPM_OK;
   const int nsub = d.kind == TBPM_HONEYCOMB ? 2 : 1;
   const size_t z = lat->tap_t.size();
   std::vector<TapChunk> out;
-  int rx = 0, ry = 0, ry_taps = 0;
-  for (size_t k = 0; k < z; ++k) ry_taps = std::max(ry_taps, std::abs(lat->tap_off[4 * k + 1]));
+  int rx = 0, ry = 0;
   for (int sub = 0; sub < nsub; ++sub) {
     std::map<std::pair<int, int>, std::map<int, float>> runs;  // (dx, ds) -> dy -> weight
     for (size_t k = 0; k < z; ++k) {
@@ -357,11 +336,17 @@ int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
         memset(&c, 0, sizeof(c));
         c.dx = kv.first.first;
         c.ds = kv.first.second;
-        c.n = (hi - pos + 1) > 4 ? 8 : 4;
-        c.dy0 = std::min(pos, std::max(ry_taps - c.n + 1, -ry_taps));
+        const int left = hi - pos + 1;
+#if TBPM_TAPS_EXACT
+        c.n = std::min(8, left);
+#else
+        c.n = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
+#endif
+        c.dy0 = pos;
         for (int k = 0; k < c.n; ++k) {
           auto it = kv.second.find(c.dy0 + k);
-          c.w[k] = (c.dy0 + k < pos || it == kv.second.end()) ? 0.f : it->second;
+          const float wk = it == kv.second.end() ? 0.f : it->second;
+          c.w[k] = make_float2(wk, wk);
         }
         rx = std::max(rx, std::abs(c.dx));
         ry = std::max(ry, std::max(std::abs(c.dy0), std::abs(c.dy0 + c.n - 1)));
