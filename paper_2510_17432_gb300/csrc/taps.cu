@@ -33,9 +33,13 @@ namespace {
 #define TBPM_TAPS_RB 2
 #endif
 
-// run pieces: every length 1..8 (1), or lengths 8, 4, 2, 1 only (0: fewer kernel variants)
-#ifndef TBPM_TAPS_EXACT
-#define TBPM_TAPS_EXACT 0
+// run pieces: 2 = pieces of 8 and 4 taps (zero-padded), 1 = every length 1..8, 0 = lengths
+// 8, 4, 2, 1; and whether the chunk table is staged in shared memory (1) or read through L1
+#ifndef TBPM_TAPS_PIECES
+#define TBPM_TAPS_PIECES 2
+#endif
+#ifndef TBPM_TAPS_TABLE_SMEM
+#define TBPM_TAPS_TABLE_SMEM 1
 #endif
 
 constexpr int kTapOY = 16;                       // output rows per thread
@@ -64,14 +68,20 @@ __device__ __forceinline__ int64_t tap_wrap(int64_t v, int64_t L, int periodic, 
 
 // acc[o] += sum_k w[k] col[(o + k) rs] for the 16 rows o: a sliding window over NW + 15 rows.
 // The two states of a pack are two FP32 pairs (lo, hi); each pair takes one packed f32x2 FMA
-// with the tap weight duplicated in both halves (stored that way in the chunk table, read
-// through the read-only cache).
+// with the tap weight duplicated in both halves.
 template <int NW>
 __device__ __forceinline__ void tap_piece(float2 (&lo)[kTapOY], float2 (&hi)[kTapOY], const float4* col, int rs,
-                                          const float2* w) {
+                                          const float* w) {
   float2 w2[NW];
 #pragma unroll
-  for (int k = 0; k < NW; ++k) w2[k] = __ldg(w + k);
+  for (int k = 0; k < NW; ++k) {
+#if TBPM_TAPS_TABLE_SMEM
+    const float wk = w[k];
+#else
+    const float wk = __ldg(w + k);
+#endif
+    w2[k] = make_float2(wk, wk);
+  }
 #pragma unroll
   for (int j = 0; j < kTapOY + NW - 1; ++j) {
     const float4 v = col[j * rs];
@@ -96,11 +106,19 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
   const int RX = a.taps_rx, RY = a.taps_ry;
   const int TW = TX + 2 * RX, TH = kTapTY + 2 * RY, RS = NSUB * TW;
   float4* tile = smem;
-  // the chunk table stays in global memory: every warp reads the same piece at once (one
-  // broadcast L1 line), which keeps shared memory for two tiles per SM
-  const TapChunk* ch = a.taps;
   const int nch = a.taps_n0 + (NSUB == 2 ? a.taps_n1 : 0);
-  static_assert(sizeof(TapChunk) == 80, "chunk = 5 float4");
+  static_assert(sizeof(TapChunk) == 48, "chunk = 3 float4");
+#if TBPM_TAPS_TABLE_SMEM
+  TapChunk* ch = reinterpret_cast<TapChunk*>(smem + (size_t)TH * RS);
+  for (int i = threadIdx.x; i < 3 * nch; i += kTapThreads) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<float4*>(ch) + i);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst),
+                 "l"(reinterpret_cast<const float4*>(a.taps) + i)
+                 : "memory");
+  }
+#else
+  const TapChunk* ch = a.taps;
+#endif
 
   const int P = a.P;
   const int p = (int)(blockIdx.x % (unsigned)P);
@@ -140,20 +158,28 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
   for (int o = 0; o < kTapOY; ++o) lo[o] = hi[o] = make_float2(0.f, 0.f);
   const int c_lo = sub == 0 ? 0 : a.taps_n0, c_hi = sub == 0 ? a.taps_n0 : nch;
   for (int c = c_lo; c < c_hi; ++c) {
-    const int4 hd = __ldg(reinterpret_cast<const int4*>(ch + c));  // dx, dy0, ds, n
+#if TBPM_TAPS_TABLE_SMEM
+    const int4 hd = *reinterpret_cast<const int4*>(ch + c);  // dx, dy0, ds, n
+#else
+    const int4 hd = __ldg(reinterpret_cast<const int4*>(ch + c));
+#endif
     const float4* col = tile + (r0 + hd.y) * RS + hd.z * TW + RX + xl + hd.x;
-    const float2* w = ch[c].w;
+    const float* w = ch[c].w;
     switch (hd.w) {
       case 8: tap_piece<8>(lo, hi, col, RS, w); break;
-#if TBPM_TAPS_EXACT
+#if TBPM_TAPS_PIECES == 1
       case 7: tap_piece<7>(lo, hi, col, RS, w); break;
       case 6: tap_piece<6>(lo, hi, col, RS, w); break;
       case 5: tap_piece<5>(lo, hi, col, RS, w); break;
       case 3: tap_piece<3>(lo, hi, col, RS, w); break;
 #endif
+#if TBPM_TAPS_PIECES == 2
+      default: tap_piece<4>(lo, hi, col, RS, w); break;
+#else
       case 4: tap_piece<4>(lo, hi, col, RS, w); break;
       case 2: tap_piece<2>(lo, hi, col, RS, w); break;
       default: tap_piece<1>(lo, hi, col, RS, w); break;
+#endif
     }
   }
 
@@ -261,7 +287,7 @@ int64_t tap_grid(const RecurrenceArgs& a) {
 template <int NSUB>
 size_t tap_smem(int rx, int ry, int nch) {
   constexpr int TX = TapShape<NSUB>::TX;
-  return (size_t)(kTapTY + 2 * ry) * NSUB * (TX + 2 * rx) * 16;
+  return (size_t)(kTapTY + 2 * ry) * NSUB * (TX + 2 * rx) * 16 + (TBPM_TAPS_TABLE_SMEM ? (size_t)nch * sizeof(TapChunk) : 0);
 }
 
 }  // namespace
@@ -316,7 +342,8 @@ int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
   const int nsub = d.kind == TBPM_HONEYCOMB ? 2 : 1;
   const size_t z = lat->tap_t.size();
   std::vector<TapChunk> out;
-  int rx = 0, ry = 0;
+  int rx = 0, ry = 0, ry_taps = 0;
+  for (size_t k = 0; k < z; ++k) ry_taps = std::max(ry_taps, std::abs(lat->tap_off[4 * k + 1]));
   for (int sub = 0; sub < nsub; ++sub) {
     std::map<std::pair<int, int>, std::map<int, float>> runs;  // (dx, ds) -> dy -> weight
     for (size_t k = 0; k < z; ++k) {
@@ -337,16 +364,21 @@ int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
         c.dx = kv.first.first;
         c.ds = kv.first.second;
         const int left = hi - pos + 1;
-#if TBPM_TAPS_EXACT
+#if TBPM_TAPS_PIECES == 2
+        // zero-padded pieces of 8 or 4; one that would reach past the largest |dy| of any tap
+        // starts lower (its rows already covered weigh 0), so the halo stays that |dy|
+        c.n = left > 4 ? 8 : 4;
+        c.dy0 = std::min(pos, std::max(ry_taps - c.n + 1, -ry_taps));
+#elif TBPM_TAPS_PIECES == 1
         c.n = std::min(8, left);
+        c.dy0 = pos;
 #else
         c.n = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-#endif
         c.dy0 = pos;
+#endif
         for (int k = 0; k < c.n; ++k) {
           auto it = kv.second.find(c.dy0 + k);
-          const float wk = it == kv.second.end() ? 0.f : it->second;
-          c.w[k] = make_float2(wk, wk);
+          c.w[k] = (c.dy0 + k < pos || it == kv.second.end()) ? 0.f : it->second;
         }
         rx = std::max(rx, std::abs(c.dx));
         ry = std::max(ry, std::max(std::abs(c.dy0), std::abs(c.dy0 + c.n - 1)));

@@ -183,10 +183,10 @@ struct tbpm_ctx {
 
 // One piece of a column run of long-range taps for the matrix-free tap kernel: the taps
 // (dx, dy0 + k, ds), k < n (1 <= n <= 8), of one destination sublattice, with weights t_k/t
-// (0 where the run has a hole), each stored twice for packed f32x2 FMAs.
+// (0 where the run has a hole or the piece is padded).
 struct TapChunk {
   int dx, dy0, ds, n;
-  float2 w[8];
+  float w[8];
 };
 
 struct tbpm_lattice {
