@@ -45,7 +45,7 @@ WORKLOADS = {
     "dense61": wl.dense_honeycomb(61),
     "dense124": wl.dense_honeycomb(124),
     "dense235": wl.dense_honeycomb(235),
-    "dense235_small": wl.dense_honeycomb(235, n_steps=64, L=(1024, 1024)),   # profiling case
+    "dense235_small": wl.dense_honeycomb(235, n_steps=64, L=(1024, 2048)),   # profiling case
     "vacancy1024": wl.Workload("honeycomb1024x1024_vac1pct_W2_Nt256", wl.honeycomb(1024, 1024, t=-2.7, W=2.0,
                                                                                  vacancy_frac=0.01, path=wl.PATH_CSR),
                                n_states=1, n_moments=0, precision=wl.C64, n_steps=256, n_energies=16),

@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kT) k_build_ell_taps(Geom g, int64_t n, const 
         const int64_t j = hc ? 2 * (ty * g.Lx + tx) + (s ? 1 - tp.w : tp.w) : (tz * g.Ly + ty) * g.Lx + tx;
         cj = compact[j];
       }
-      ell[k * g.z + d] = (int32_t)cj;
+      if (ell) ell[k * g.z + d] = (int32_t)cj;
       if (cj >= 0) {
         rad += tabs[d];
         ++deg;
@@ -687,7 +687,10 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
     lat->n_sites = n_active;
     TBPM_TRY(dev_alloc(ctx, &lat->compact, g.n_full));
     TBPM_TRY(dev_alloc(ctx, &lat->full_of, n_active));
-    TBPM_TRY(dev_alloc(ctx, &lat->ell, (size_t)n_active * g.z));
+    // clean long-range lattices that the tap kernel serves build their ELL lists only when a
+    // pass needs them (complex128, one state, exports): at D_H ~ 230 they outweigh the states
+    const bool lazy_ell = lr && d.path == TBPM_PATH_AUTO && !vac && d.kind != TBPM_CUBIC;
+    if (!lazy_ell) TBPM_TRY(dev_alloc(ctx, &lat->ell, (size_t)n_active * g.z));
     if (lat->has_v) TBPM_TRY(dev_alloc(ctx, &lat->v64, n_active));
     k_compact<<<(unsigned)nchunks, kT, 0, ctx->stream>>>(g.n_full, d.seed, thr, offs, lat->compact, lat->full_of);
     TBPM_CK_LAUNCH(ctx);
@@ -726,6 +729,43 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
     TBPM_CK_LAUNCH(ctx);
   }
   return TBPM_OK;
+}
+
+// ELL lists of a long-range lattice built on first need (see build_lattice).
+static int ensure_ell(tbpm_ctx* ctx, tbpm_lattice* lat) {
+  if (lat->ell || lat->tap_t.empty()) return TBPM_OK;
+  const Geom& g = lat->geom;
+  const size_t z = lat->tap_t.size();
+  std::vector<double> tabs(z);
+  for (size_t k = 0; k < z; ++k) tabs[k] = fabs(lat->tap_t[k]);
+  const int nb = grid_for(ctx, lat->n_sites, kT);
+  int4* d_taps = nullptr;
+  double* d_tabs = nullptr;
+  Bounds3* part = nullptr;
+  int r = dev_alloc(ctx, &lat->ell, (size_t)lat->n_sites * g.z);
+  if (r == TBPM_OK) r = dev_alloc(ctx, &d_taps, z);
+  if (r == TBPM_OK) r = dev_alloc(ctx, &d_tabs, z);
+  if (r == TBPM_OK) r = dev_alloc(ctx, &part, (size_t)nb);
+  if (r == TBPM_OK) {
+    cudaMemcpyAsync(d_taps, lat->tap_off.data(), z * sizeof(int4), cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(d_tabs, tabs.data(), z * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+    k_build_ell_taps<<<nb, kT, 0, ctx->stream>>>(g, lat->n_sites, lat->full_of, lat->compact, d_taps, d_tabs,
+                                                  lat->desc.seed, lat->desc.W, lat->ell, nullptr, part);
+    ctx->launches++;
+    const cudaError_t e = cudaGetLastError();
+    const cudaError_t es = cudaStreamSynchronize(ctx->stream);  // the host tables must outlive the copies
+    if (e != cudaSuccess || es != cudaSuccess) {
+      set_error("ELL build: %s", cudaGetErrorString(e != cudaSuccess ? e : es));
+      r = TBPM_ECUDA;
+    }
+  }
+  for (void* q : {(void*)d_taps, (void*)d_tabs, (void*)part})
+    if (q) cudaFreeAsync(q, ctx->stream);
+  if (r != TBPM_OK && lat->ell) {
+    cudaFreeAsync(lat->ell, ctx->stream);
+    lat->ell = nullptr;
+  }
+  return r;
 }
 
 static int ensure_d64(tbpm_lattice* lat) {
@@ -860,6 +900,7 @@ int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, in
     }
   }
   if (nbr) {
+    TBPM_TRY(ensure_ell(ctx, const_cast<tbpm_lattice*>(lat)));
     if (lat->ell) {
       TBPM_CK(cudaMemcpyAsync(nbr, lat->ell, n * z * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
     } else {
@@ -998,7 +1039,6 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
   memset(a, 0, sizeof(*a));
   a->geom = lat->geom;
   a->path = lat->path;
-  a->ell = lat->ell;
   a->wrel = lat->wrel64 ? (pl.precision == TBPM_C128 ? (const void*)lat->wrel64 : (const void*)lat->wrel32) : nullptr;
   if (lat->chunks && pl.precision == TBPM_C64 && pl.Spad >= 2) {
     a->taps = lat->chunks;
@@ -1007,6 +1047,8 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
     a->taps_rx = lat->halo_x;
     a->taps_ry = lat->halo_y;
   }
+  if (!a->taps) TBPM_TRY(ensure_ell(ctx, lat));
+  a->ell = lat->ell;
   if (lat->has_v) {
     if (pl.precision == TBPM_C128) TBPM_TRY(ensure_d64(lat));
     a->diag = pl.precision == TBPM_C128 ? (const void*)lat->d64 : (const void*)lat->d32;

@@ -36,7 +36,7 @@ namespace {
 // run pieces: 2 = pieces of 8 and 4 taps (zero-padded), 1 = every length 1..8, 0 = lengths
 // 8, 4, 2, 1; and whether the chunk table is staged in shared memory (1) or read through L1
 #ifndef TBPM_TAPS_PIECES
-#define TBPM_TAPS_PIECES 2
+#define TBPM_TAPS_PIECES 0
 #endif
 #ifndef TBPM_TAPS_TABLE_SMEM
 #define TBPM_TAPS_TABLE_SMEM 1
@@ -131,18 +131,22 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
 
   // stage phi_n of the tile and its halo (wrapped on periodic sides, zero on open ones) with
   // asynchronous 16-byte copies, all in flight at once
-  const int total = TH * TW * NSUB;
-  for (int e = threadIdx.x; e < total; e += kTapThreads) {
+  // (one column (tx, s) per thread, walked down the rows: the column's wrap is computed once)
+  for (int e = threadIdx.x; e < NSUB * TW; e += kTapThreads) {
     const int s = NSUB == 2 ? (e & 1) : 0;
-    const int r = NSUB == 2 ? (e >> 1) : e;
-    const int tx = r % TW, ty = r / TW;
-    bool ok = true;
-    const int64_t gx = tap_wrap(x0 - RX + tx, Lx, a.geom.pbc_x, &ok);
-    const int64_t gy = tap_wrap(y0 - RY + ty, Ly, a.geom.pbc_y, &ok);
-    const float4* src = ok ? cur + ((gy * Lx + gx) * NSUB + s) * P + p : cur;
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + ty * RS + s * TW + tx);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
-                 : "memory");
+    const int tx = NSUB == 2 ? (e >> 1) : e;
+    bool okx = true;
+    const int64_t gx = tap_wrap(x0 - RX + tx, Lx, a.geom.pbc_x, &okx);
+    const float4* colsrc = cur + (gx * NSUB + s) * P + p;
+    const int64_t rstride = Lx * NSUB * P;
+    unsigned dst = (unsigned)__cvta_generic_to_shared(tile + s * TW + tx);
+    for (int ty = 0; ty < TH; ++ty, dst += (unsigned)(RS * sizeof(float4))) {
+      bool ok = okx;
+      const int64_t gy = tap_wrap(y0 - RY + ty, Ly, a.geom.pbc_y, &ok);
+      const float4* src = ok ? colsrc + gy * rstride : cur;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0)
+                   : "memory");
+    }
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_group 0;" ::: "memory");
