@@ -38,6 +38,9 @@ namespace {
 #ifndef TBPM_TAPS_PIECES
 #define TBPM_TAPS_PIECES 0
 #endif
+#ifndef TBPM_TAPS_PREFETCH
+#define TBPM_TAPS_PREFETCH 0
+#endif
 #ifndef TBPM_TAPS_TABLE_SMEM
 #define TBPM_TAPS_TABLE_SMEM 1
 #endif
@@ -157,6 +160,16 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
   const int sub = NSUB == 2 ? (lw & 1) : 0;
   const int xl = (NSUB == 2 ? (lw >> 1) : lw) * 32 + lane;
   const int r0 = RY + rb * kTapOY;          // tile row of this thread's first output row
+#if TBPM_TAPS_PREFETCH
+  // pull this thread's phi_{n-1} lines towards L2 while the taps run
+  if (!FIRST && x0 + xl < Lx) {
+#pragma unroll 4
+    for (int o = 0; o < kTapOY; ++o) {
+      const int64_t y = y0 + rb * kTapOY + o;
+      if (y < Ly) asm volatile("prefetch.global.L2 [%0];" ::"l"(po + ((y * Lx + x0 + xl) * NSUB + sub) * P + p));
+    }
+  }
+#endif
   float2 lo[kTapOY], hi[kTapOY];
 #pragma unroll
   for (int o = 0; o < kTapOY; ++o) lo[o] = hi[o] = make_float2(0.f, 0.f);

@@ -263,6 +263,21 @@ def test_polarization_and_charge_density_match_oracle(capi, ctx, prec):
     capi.tbpm_lattice_destroy(lat)
 
 
+def test_recreated_lattice_does_not_replay_a_destroyed_lattices_graph(capi, ctx):
+    """Moment passes are captured in CUDA graphs from their second call on.  A lattice destroyed
+    and created again (often at the same host address, with the same sizes and coefficients)
+    must run on its own tap table, not replay the old lattice's graph."""
+    desc = capi.lattice_desc(1, (70, 36), t=-2.7, cutoff=7.1, decay=DECAY)
+    runs = []
+    for _ in range(3):
+        lat = capi.tbpm_lattice_create(ctx, desc)
+        runs.append([gpu_moments(capi, ctx, lat, 2, 200, 0) for _ in range(3)])
+        capi.tbpm_lattice_destroy(lat)
+    for r in runs:
+        for m in r:
+            assert np.array_equal(m, runs[0][0])
+
+
 def test_unsupported_calls_and_invalid_descriptions(capi, ctx):
     lat, _ = make(capi, ctx, kind=1, L=(8, 8), cutoff=2.1)
     E = np.array([0.5])
