@@ -852,23 +852,6 @@ int tbpm_lattice_destroy(tbpm_lattice* lat) {
   if (!lat) return TBPM_OK;
   tbpm_ctx* ctx = lat->ctx;
   cudaSetDevice(ctx->device);
-  // captured moment-pass graphs hold this lattice's device pointers: drop them, so that a
-  // lattice created later at the same host address never replays them
-  const uint64_t me = (uint64_t)lat;
-  for (size_t i = 0; i < ctx->graphs.size();) {
-    if (ctx->graphs[i].key.size() > 5 && ctx->graphs[i].key[5] == me) {
-      cudaGraphExecDestroy(ctx->graphs[i].exec);
-      ctx->graphs.erase(ctx->graphs.begin() + i);
-    } else {
-      ++i;
-    }
-  }
-  for (size_t i = 0; i < ctx->graph_seen.size();) {
-    if (ctx->graph_seen[i].size() > 5 && ctx->graph_seen[i][5] == me)
-      ctx->graph_seen.erase(ctx->graph_seen.begin() + i);
-    else
-      ++i;
-  }
   free_lattice_mem(lat);
   cudaStreamSynchronize(lat->ctx->stream);
   delete lat;
@@ -1235,6 +1218,9 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
       return u;
     };
     const Geom& g = lat->geom;
+    // every device pointer the captured passes read must be part of the key: a graph replays
+    // only where those same addresses are allocated again (a lattice created anew at the same
+    // addresses holds the same data there); a missing one would replay freed memory
     const std::vector<uint64_t> key = {
         (uint64_t)ctx->ws_phi[0].p, (uint64_t)ctx->ws_phi[1].p, (uint64_t)ctx->ws_phi2[0].p,
         (uint64_t)ctx->ws_phi2[1].p, (uint64_t)d_mu, (uint64_t)lat, (uint64_t)lat->d32, (uint64_t)lat->d64,
@@ -1242,7 +1228,8 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
         (uint64_t)M, (uint64_t)fmode, (uint64_t)pl.precision, (uint64_t)pl.Spad, bits(a.thop), bits(a.diag_const),
         (uint64_t)g.Lx, (uint64_t)g.Ly, (uint64_t)g.Lz, (uint64_t)g.kind,
         (uint64_t)(g.pbc_x | (g.pbc_y << 1) | (g.pbc_z << 2)), (uint64_t)lat->path, (uint64_t)lat->n_sites,
-        (uint64_t)lat->chunks, (uint64_t)a.taps_rx, (uint64_t)a.taps_ry, (uint64_t)a.taps_n0, (uint64_t)a.taps_n1};
+        (uint64_t)lat->chunks, (uint64_t)a.taps_rx, (uint64_t)a.taps_ry, (uint64_t)a.taps_n0, (uint64_t)a.taps_n1,
+        (uint64_t)lat->wrel32, (uint64_t)lat->wrel64};
     tbpm_ctx::Graph* hit = nullptr;
     for (auto& e : ctx->graphs)
       if (e.key == key) hit = &e;
