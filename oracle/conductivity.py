@@ -30,7 +30,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .bessel import cheb_coefficients, truncation_order
-from .lattice import Lattice, SQUARE, HONEYCOMB, CUBIC
+from .lattice import Lattice, SQUARE, HONEYCOMB, CUBIC, long_range_bonds
 from .propagate import chebyshev_states, evolve_step
 from .quasi import qe_concurrent_e
 
@@ -57,7 +57,15 @@ def area_per_site(kind: int) -> float:
 
 
 def current_operator(lat: Lattice, direction: int) -> sp.csr_matrix:
-    """J_a as a sparse [n, n] complex matrix on the active sites."""
+    """J_a as a sparse [n, n] complex matrix on the active sites.  Long-range lattices: every
+    bond (i, j, image R) contributes -i t(r) (r_j + R - r_i)_a, its own bond vector."""
+    if getattr(lat, "cutoff", 0.0) > 0.0:
+        full_idx = np.flatnonzero(lat.active)
+        rows, cols, tv, dv = long_range_bonds(lat.kind, lat.L, lat.pbc, full_idx, lat.t, lat.cutoff, lat.decay,
+                                              with_disp=True)
+        J = sp.coo_matrix((-1j * tv * dv[:, direction], (rows, cols)), shape=(lat.n, lat.n)).tocsr()
+        J.sum_duplicates()
+        return J
     bv = bond_vectors(lat.kind)
     rows, cols, vals = [], [], []
     full_idx = np.flatnonzero(lat.active)

@@ -173,9 +173,10 @@ def period_vectors(kind: int, L) -> list:
     return [np.array([Lx, 0.0, 0.0]), np.array([0.0, Ly, 0.0]), np.array([0.0, 0.0, Lz if kind == CUBIC else 0.0])]
 
 
-def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay: float):
+def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay: float, with_disp: bool = False):
     """All bonds (i, j, t(r)) between the listed sites, by brute force over site pairs and
-    period images: 0 < |r_j + R - r_i| <= cutoff.  Returns compact rows, columns, values."""
+    period images: 0 < |r_j + R - r_i| <= cutoff.  Returns compact rows, columns, values (and,
+    with_disp, the bond vectors r_j + R - r_i, [n_bonds, 3])."""
     dims = 3 if kind == CUBIC else 2
     pos = site_positions(kind, L, full_idx)[:, :dims]
     per = [v[:dims] for v in period_vectors(kind, L)]
@@ -192,7 +193,7 @@ def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay
             ranges.append(range(-m, m + 1))
         else:
             ranges.append(range(0, 1))
-    rows, cols, vals = [], [], []
+    rows, cols, vals, disp = [], [], [], []
     n = pos.shape[0]
     c2 = cutoff * cutoff
     for n0 in ranges[0]:
@@ -209,8 +210,16 @@ def long_range_bonds(kind: int, L, pbc, full_idx, t: float, cutoff: float, decay
                     rows.append(ii + lo)
                     cols.append(jj)
                     vals.append(t * np.exp(-(r - 1.0) / decay))
+                    if with_disp:
+                        dv = np.zeros((ii.size, 3))
+                        for a in range(dims):
+                            dv[:, a] = pos[jj, a] + R[a] - pos[ii + lo, a]
+                        disp.append(dv)
     cat = lambda v, dt: np.concatenate(v).astype(dt) if v else np.zeros(0, dt)
-    return cat(rows, np.int64), cat(cols, np.int64), cat(vals, np.float64)
+    out = (cat(rows, np.int64), cat(cols, np.int64), cat(vals, np.float64))
+    if with_disp:
+        out = out + (np.concatenate(disp) if disp else np.zeros((0, 3)),)
+    return out
 
 
 def build_lattice(kind: int, L, t: float, W: float = 0.0, vacancy_frac: float = 0.0,

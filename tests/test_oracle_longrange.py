@@ -158,3 +158,47 @@ def test_vacancies_restrict_the_clean_hamiltonian_and_bounds_hold():
 def test_long_range_needs_a_decay_length():
     with pytest.raises(ValueError):
         olat.build_lattice(olat.SQUARE, (4, 4, 1), t=1.0, cutoff=2.0, decay=0.0)
+
+
+@pytest.mark.parametrize("kind,L,pbc", [(olat.HONEYCOMB, (5, 4, 1), (1, 1, 1)), (olat.HONEYCOMB, (6, 3, 1), (0, 1, 1)),
+                                        (olat.SQUARE, (5, 6, 1), (1, 0, 1)), (olat.CUBIC, (3, 4, 3), (1, 1, 1))])
+def test_current_operator_at_cutoff_one_is_the_nearest_neighbour_one(kind, L, pbc):
+    from oracle import conductivity as oec
+    nn = olat.build_lattice(kind, L, t=-1.3, W=0.7, seed=5, pbc=pbc)
+    lr = olat.build_lattice(kind, L, t=-1.3, W=0.7, seed=5, pbc=pbc, cutoff=1.2, decay=0.5)
+    for a in range(3 if kind == olat.CUBIC else 2):
+        assert abs(oec.current_operator(nn, a) - oec.current_operator(lr, a)).max() < 4e-15
+
+
+@pytest.mark.parametrize("L,cutoff", [((6, 5, 1), 3.3), ((3, 4, 1), 4.1)])
+def test_current_operator_is_the_band_velocity(L, cutoff):
+    """J_a = i[H, P_a] on Bloch states: J psi = (-dh/dk_a u)_s e^{i k.r}, with
+    dh/dk_a = sum_d t(|d|) i d_a e^{i k.d} the derivative of the lattice sum h(k)."""
+    from oracle import conductivity as oec
+    t, decay = -2.7, 0.7
+    lat = olat.build_lattice(olat.HONEYCOMB, L, t=t, cutoff=cutoff, decay=decay)
+    Lx, Ly, _ = L
+    Am = np.array([A1[:2], A2[:2]])
+    B = 2 * np.pi * np.linalg.inv(Am).T
+    full = np.arange(lat.n_full)
+    pos = olat.site_positions(olat.HONEYCOMB, lat.L, full)
+    s = full % 2
+    rng = np.random.default_rng(2)
+    R = int(cutoff) + 2
+    for mx, my in [(1, 2), (Lx - 1, 1), (0, 0)]:
+        k = np.zeros(3)
+        k[:2] = mx / Lx * B[0] + my / Ly * B[1]
+        for a in (0, 1):
+            dh = np.zeros((2, 2), np.complex128)
+            for s0, s1 in itertools.product((0, 1), (0, 1)):
+                for m, q in itertools.product(range(-R, R + 1), range(-R, R + 1)):
+                    d = m * A1 + q * A2 + (s1 - s0) * np.array([1.0, 0, 0])
+                    r = np.linalg.norm(d)
+                    if 1e-9 < r <= cutoff:
+                        dh[s0, s1] += _t(r, t, decay) * 1j * d[a] * np.exp(1j * (k @ d))
+            u = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+            psi = u[s] * np.exp(1j * (pos @ k))
+            want = (-(dh @ u))[s] * np.exp(1j * (pos @ k))
+            J = oec.current_operator(lat, a)
+            assert np.max(np.abs(J @ psi - want)) < 1e-12
+            assert abs(J - J.conj().T).max() < 1e-13
