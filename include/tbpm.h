@@ -93,8 +93,11 @@ typedef struct tbpm_lattice tbpm_lattice;
  * lands on a site another tap reaches adds to that bond; one that lands on the site itself
  * adds to the diagonal), open directions drop it.  The Gershgorin radius is the sum of |t(r)|
  * over the taps that reach active sites.  Such lattices run on the CSR/ELL path with
- * per-tap weights (path AUTO or CSR); the conductivity and optical-conductivity drivers
- * (current operator) and the serving loop reject them (TBPM_EUNSUPPORTED).
+ * per-tap weights (path CSR), or, with path AUTO and no vacancies on square and honeycomb
+ * lattices, on a matrix-free tap kernel for complex64 blocks of >= 2 states (the ELL lists are
+ * then built only when another pass needs them).  In the current operator (conductivity,
+ * optical conductivity) every tap carries its own bond vector.  The serving loop rejects
+ * long-range lattices (TBPM_EUNSUPPORTED).
  */
 typedef struct {
   int32_t kind;        /* TBPM_SQUARE / TBPM_HONEYCOMB / TBPM_CUBIC */

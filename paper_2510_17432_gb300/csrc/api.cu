@@ -639,6 +639,29 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
       w32[k] = (float)wrel[k];
     }
     const size_t z = wrel.size();
+    // current-operator weights t_k (r_j - r_i)_a per direction and sublattice; a honeycomb B site
+    // takes every tap mirrored, so its bond vectors are the negatives
+    std::vector<double> jw(6 * z);
+    const double h = sqrt(3.0) / 2.0;
+    for (size_t k = 0; k < z; ++k) {
+      const int* o = &lat->tap_off[4 * k];
+      double dv[3];
+      if (d.kind == TBPM_HONEYCOMB) {
+        dv[0] = 1.5 * (o[0] + o[1]) + o[3];
+        dv[1] = h * (o[0] - o[1]);
+        dv[2] = 0.0;
+      } else {
+        dv[0] = o[0];
+        dv[1] = o[1];
+        dv[2] = o[2];
+      }
+      for (int a = 0; a < 3; ++a) {
+        jw[(a * 2 + 0) * z + k] = lat->tap_t[k] * dv[a];
+        jw[(a * 2 + 1) * z + k] = (d.kind == TBPM_HONEYCOMB ? -1.0 : 1.0) * lat->tap_t[k] * dv[a];
+      }
+    }
+    TBPM_TRY(dev_alloc(ctx, &lat->jw, 6 * z));
+    TBPM_CK(cudaMemcpyAsync(lat->jw, jw.data(), 6 * z * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     TBPM_TRY(dev_alloc(ctx, &lat->wrel64, z));
     TBPM_TRY(dev_alloc(ctx, &lat->wrel32, z));
     TBPM_TRY(dev_alloc(ctx, &d_taps, z));
@@ -732,7 +755,7 @@ static int build_lattice(tbpm_ctx* ctx, tbpm_lattice* lat) {
 }
 
 // ELL lists of a long-range lattice built on first need (see build_lattice).
-static int ensure_ell(tbpm_ctx* ctx, tbpm_lattice* lat) {
+int tbpm::ensure_ell(tbpm_ctx* ctx, tbpm_lattice* lat) {
   if (lat->ell || lat->tap_t.empty()) return TBPM_OK;
   const Geom& g = lat->geom;
   const size_t z = lat->tap_t.size();
@@ -781,7 +804,7 @@ static int ensure_d64(tbpm_lattice* lat) {
 static void free_lattice_mem(tbpm_lattice* lat) {
   tbpm_ctx* ctx = lat->ctx;
   void* ps[] = {lat->d32, lat->d64, lat->v64, lat->ell, lat->compact, lat->full_of, lat->wrel32, lat->wrel64,
-                lat->chunks};
+                lat->chunks, lat->jw};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, ctx->stream);
 }
@@ -2128,10 +2151,7 @@ int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
     return TBPM_EINVAL;
   }
   tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
-  if (lat && lat->wrel64) {
-    set_error("tbpm_conductivity: the current operator is built for nearest-neighbour lattices only");
-    return TBPM_EUNSUPPORTED;
-  }
+  if (lat) TBPM_TRY(ensure_ell(ctx, lat));  // the current operator reads the ELL lists
   Plan pl;
   TBPM_TRY(make_plan(lat, req, &pl));
   TBPM_CK(cudaSetDevice(ctx->device));
@@ -2226,10 +2246,7 @@ int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tb
     set_error("tbpm_optical_conductivity: lattice is NULL");
     return TBPM_EINVAL;
   }
-  if (lat->wrel64) {
-    set_error("tbpm_optical_conductivity: the current operator is built for nearest-neighbour lattices only");
-    return TBPM_EUNSUPPORTED;
-  }
+  TBPM_TRY(ensure_ell(ctx, lat));  // the current operator reads the ELL lists
   const int dims = lat->desc.kind == TBPM_CUBIC ? 3 : 2;
   if (alpha < 0 || alpha >= dims || beta < 0 || beta >= dims) {
     set_error("directions must lie in [0, %d)", dims);

@@ -6,7 +6,8 @@
 //    so every bond i-j carries (J_alpha)_ij = -i H_ij (r_j - r_i)_alpha (hbar = e = 1).  Bond
 //    vectors are those of the library's lattices: unit-spaced square and cubic lattices; graphene
 //    with C-C distance 1, A -> B bonds (1,0), (-1/2,-sqrt3/2), (-1/2,sqrt3/2) in the fixed
-//    neighbour order, B -> A their negatives.  Periodic bonds use the nearest image.
+//    neighbour order, B -> A their negatives.  Periodic bonds use the nearest image.  On
+//    long-range lattices every tap carries its own bond vector (negated on the B sublattice).
 //  * Block inner products: out[s][a][b] = sum_i conj(A_a[i][s]) B_b[i][s] for nA x nB pairs of
 //    state blocks in one pass; each CTA owns a TA x TB tile of pairs and walks chunks of the
 //    site range, FP32 products (complex64 states) summed over 16 units per thread, folded into
@@ -42,6 +43,7 @@ struct CurArgs {
   int64_t n_sites;
   int P, logP;
   double kw[2][6];  // t (r_j - r_i)_alpha per sublattice and neighbour slot
+  const double* kwl;  // long-range lattices: the same per slot on the device, [2][z] (else null)
 };
 
 // y = J_alpha x for one block of states [n_sites][S].
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_current(CurArgs c, const void* xv,
     for (int d = 0; d < c.g.z; ++d) {
       const int64_t j = csr ? (int64_t)c.ell[i * c.g.z + d] : neighbour_full(c.g, i, d);
       if (j < 0) continue;
-      const R w = (R)c.kw[sub][d];
+      const R w = c.kwl ? (R)__ldg(c.kwl + sub * c.g.z + d) : (R)c.kw[sub][d];
       const PK x = ld(X + j * c.P + p);
 #pragma unroll
       for (int k = 0; k < SPT; ++k) {  // -i w (xr + i xi) = w xi - i w xr
@@ -307,6 +309,11 @@ int launch_current(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int S,
   c.logP = 0;
   while ((1 << c.logP) < c.P) ++c.logP;
   current_weights(lat->desc.kind, direction, lat->desc.t, c.kw);
+  c.kwl = lat->jw ? lat->jw + (size_t)direction * 2 * lat->geom.z : nullptr;
+  if (c.path == TBPM_PATH_CSR && !c.ell) {
+    set_error("current operator: ELL lists missing");
+    return TBPM_EINVAL;
+  }
   const int64_t n_units = lat->n_sites * c.P;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n_units + kThreads - 1) / kThreads,
                                                                (int64_t)ctx->num_sms * 8));

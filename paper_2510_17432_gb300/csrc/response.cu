@@ -172,6 +172,7 @@ struct XmyArgs {
   SiteGeom sg;
   const int32_t* ell;
   double kw[2][6];       // current operator weights t (r_j - r_i)_alpha
+  const double* kwl;     // long-range lattices: the same per slot on the device, [2][z] (else null)
   const double2* phase;  // density operator e^{i q.r_i}, or null for the current operator
   const void* Y;         // bb pair blocks [n][2 Sh], consecutive
   int64_t y_stride;      // elements (complex) between pair blocks
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_xmy(XmyArgs a) {
         for (int d = 0; d < a.sg.g.z; ++d) {
           const int64_t j = nb_of(a, i, d, coords);
           if (j < 0) continue;
-          const R w = (R)a.kw[sub][d];
+          const R w = a.kwl ? (R)__ldg(a.kwl + sub * a.sg.g.z + d) : (R)a.kw[sub][d];
           const T x = Y[j * S2 + Sh + s];
           vr += w * x.y;  // -i w x
           vi -= w * x.x;
@@ -430,7 +431,15 @@ int launch_xmy(tbpm_ctx* ctx, const tbpm_lattice* lat, int precision, int Sh, in
   XmyArgs a;
   a.sg = SiteGeom{lat->geom, lat->path == TBPM_PATH_CSR, lat->full_of};
   a.ell = lat->ell;
-  if (!phase) current_weights(lat->desc.kind, alpha, lat->desc.t, a.kw);
+  a.kwl = nullptr;
+  if (!phase) {
+    current_weights(lat->desc.kind, alpha, lat->desc.t, a.kw);
+    a.kwl = lat->jw ? lat->jw + (size_t)alpha * 2 * lat->geom.z : nullptr;
+    if (a.sg.csr && !a.ell) {
+      set_error("current operator: ELL lists missing");
+      return TBPM_EINVAL;
+    }
+  }
   a.phase = phase;
   a.Y = Y;
   a.y_stride = (int64_t)(pair_bytes / (precision == TBPM_C128 ? 16 : 8));

@@ -210,6 +210,7 @@ struct tbpm_lattice {
   double* wrel64 = nullptr;
   std::vector<int> tap_off;      // [z][4] (dx, dy, dz, ds) of each slot (long-range only)
   std::vector<double> tap_t;     // [z] t(r) of each slot (long-range only)
+  double* jw = nullptr;          // [3 directions][2 sublattices][z] t_k (r_j - r_i)_a of each slot
   // matrix-free tap kernel (clean long-range square / honeycomb lattices): column-run pieces
   // of destination sublattice 0 then 1 on the device, their counts and the tile halo
   TapChunk* chunks = nullptr;
@@ -289,6 +290,7 @@ int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bo
 // matrix-free tap kernel (csrc/taps.cu): chunk table of a clean long-range lattice, the moment
 // pass over it, and the size of its per-CTA partial sums
 int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat);
+int ensure_ell(tbpm_ctx* ctx, tbpm_lattice* lat);  // ELL lists of a long-range lattice, on first need
 int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);
 int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);  // recurrence only
 size_t taps_partials_bytes(const RecurrenceArgs& a);

@@ -278,15 +278,62 @@ def test_recreated_lattice_does_not_replay_a_destroyed_lattices_graph(capi, ctx)
             assert np.array_equal(m, runs[0][0])
 
 
-def test_unsupported_calls_and_invalid_descriptions(capi, ctx):
-    lat, _ = make(capi, ctx, kind=1, L=(8, 8), cutoff=2.1)
-    E = np.array([0.5])
-    with pytest.raises(capi.TbpmError):
-        capi.tbpm_conductivity(ctx, lat, capi.request(n_states=1, n_steps=4), 0, E, None, np.zeros((1, 1)))
-    with pytest.raises(capi.TbpmError):
-        capi.tbpm_optical_conductivity(ctx, lat, capi.request(n_states=1, n_steps=4), 0, 0, 0.0, 0.5, 1.0, 4, None,
-                                       np.zeros((1, 4), np.complex128))
+EC_CASES = [
+    ("honey9x8_c3.1_x_c128", dict(kind=1, L=(9, 8), W=1.0, cutoff=3.1), 0, 1, 2),
+    ("honey9x8_c3.1_y_c64", dict(kind=1, L=(9, 8), W=1.0, cutoff=3.1), 1, 0, 2),
+    ("square11x9_c2.9_open_x_c128", dict(kind=0, L=(11, 9), t=1.0, W=1.0, pbc=(0, 1, 1), cutoff=2.9, decay=0.6),
+     0, 1, 1),
+    ("honey10x8_c2.1_vac_y_c128", dict(kind=1, L=(10, 8), W=1.5, vac=0.04, cutoff=2.1), 1, 1, 1),
+]
+
+
+@pytest.mark.parametrize("form,b", [(0, 0), (2, 4), (1, 0)])
+@pytest.mark.parametrize("name,spec,direction,prec,S", EC_CASES, ids=[c[0] for c in EC_CASES])
+def test_conductivity_matches_oracle(capi, ctx, name, spec, direction, prec, S, form, b):
+    """EC in the three forms on long-range lattices: every tap carries its own bond vector in the
+    current operator (oracle: brute force over site pairs and images)."""
+    from oracle import conductivity as oec
+    lat, ol = make(capi, ctx, **spec)
+    E = ol.H0 + np.array([-0.6, 0.05, 0.4]) * (ol.E_max - ol.E_min) / 2
+    Nt = 15
+    C = np.zeros((S, E.size, Nt + 1), np.complex128)
+    sigma = np.zeros((S, E.size))
+    capi.tbpm_conductivity(ctx, lat, capi.request(n_states=S, precision=prec, form=form, n_steps=Nt, time_block=b,
+                                                  state_seed=12), direction, E, C, sigma)
+    psi = oprop.random_phase_states(ol, 12, S)
+    tol = {0: 3e-5, 1: 1e-10}[prec]
+    for s in range(S):
+        Cref, qe = oec.ec_correlation_sequential(ol, psi[s], E, Nt, direction)
+        sref = oec.conductivity(ol, psi[s], E, Cref, qe)
+        Dn = np.abs((qe.conj() @ psi[s]).real) / oec.area_per_site(ol.kind)
+        for k in range(E.size):
+            assert np.max(np.abs(C[s, k] - Cref[k])) / np.max(np.abs(Cref[k])) <= tol, ("C", s, k)
+            bound = Dn[k] * (np.pi / ol.half_width) * np.sum(np.abs(Cref[k]))
+            assert abs(sigma[s, k] - sref[k]) <= tol * bound, ("sigma", s, k)
     capi.tbpm_lattice_destroy(lat)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+@pytest.mark.parametrize("alpha,beta", [(0, 0), (0, 1)])
+def test_optical_conductivity_matches_oracle(capi, ctx, alpha, beta, prec):
+    lat, ol = make(capi, ctx, kind=1, L=(9, 8), W=1.0, cutoff=3.1)
+    S, Nt, nw = 2, 17, 25
+    mu = ol.H0 - 0.1 * (ol.E_max - ol.E_min) / 2
+    kT = 0.08 * (ol.E_max - ol.E_min) / 2
+    wmax = 1.2 * (ol.E_max - ol.E_min)
+    C = np.zeros((S, Nt + 1), np.complex128)
+    sig = np.zeros((S, nw), np.complex128)
+    capi.tbpm_optical_conductivity(ctx, lat, capi.request(n_states=S, precision=prec, form=2, n_steps=Nt,
+                                                          time_block=5, state_seed=6), alpha, beta, mu, kT, wmax, nw,
+                                   C, sig)
+    psi = oprop.random_phase_states(ol, 6, S)
+    for s in range(S):
+        Cref = R.oc_correlation_sequential(ol, psi[s], alpha, beta, mu, kT, Nt)
+        assert np.max(np.abs(C[s] - Cref)) / np.max(np.abs(Cref)) <= TOL_RESP[prec]
+    capi.tbpm_lattice_destroy(lat)
+
+
+def test_unsupported_calls_and_invalid_descriptions(capi, ctx):
     for kw in (dict(cutoff=2.0, decay=0.0), dict(cutoff=-1.0, decay=1.0), dict(cutoff=13.0, decay=1.0),
                dict(cutoff=0.5, decay=1.0), dict(cutoff=2.0, decay=1.0, path=1)):
         with pytest.raises(capi.TbpmError):
