@@ -81,6 +81,9 @@ def parse():
                    help="also time the optical conductivity on the workload's lattice (0-10 eV, 2048 frequencies)")
     p.add_argument("--oc-steps", type=int, default=256)
     p.add_argument("--requests", type=int, default=512)
+    p.add_argument("--forms", action="store_true",
+                   help="dense workloads: time QE, EC, OC, DP and CD in their sequential and concurrent forms")
+    p.add_argument("--forms-steps", type=int, default=512)
     p.add_argument("--seq-steps", type=int, default=0,
                    help="dense workloads: N_t of the D_H sweep against the sequential form (0 = the workload's)")
     p.add_argument("--log2-max-sites", type=int, default=20)
@@ -751,6 +754,53 @@ def dense_desc(capi, spec):
                              pbc=spec.pbc, path=spec.path, cutoff=spec.cutoff, decay=spec.decay)
 
 
+def dense_forms(capi, ctx, desc, S, Nt):
+    """Every quantity of the paper in its sequential and concurrent forms on the dense lattice
+    (Secs. IV-VIII measure these speedups on the D_H = 230 sample): wall time per call, same GPU."""
+    lat = capi.tbpm_lattice_create(ctx, desc)
+    info = capi.tbpm_lattice_info(lat)
+    n = info.n_sites
+    width = info.E_max - info.E_min
+    E = info.H0 + np.array([-0.5, -0.1, 0.2, 0.6]) * width / 2
+    mu, kT = info.H0, 0.05 * width / 2
+    om = np.linspace(0.0, width, 256)
+    res = {"n_steps": Nt, "states": S, "energies": E.size, "kT": kT}
+
+    def timed(fn):
+        capi.tbpm_sync(ctx)
+        t0 = time.perf_counter()
+        fn()
+        capi.tbpm_sync(ctx)
+        return time.perf_counter() - t0
+
+    def req(form, b=0, tau=0.0):
+        return capi.request(n_states=S, precision=capi.C64, form=form, n_steps=Nt, time_block=b, state_seed=1, tau=tau)
+
+    qe = np.zeros((E.size, S, n), np.complex64)
+    res["qe"] = {name: timed(lambda f=f: capi.tbpm_quasi_eigenstates(ctx, lat, req(f), E, qe))
+                 for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S),
+                                 ("concurrent_e", capi.CONCURRENT_E))}
+    sig = np.zeros((S, E.size))
+    res["ec"] = {name: timed(lambda f=f: capi.tbpm_conductivity(ctx, lat, req(f), 0, E, None, sig))
+                 for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S),
+                                 ("concurrent_m", capi.CONCURRENT_M))}
+    so = np.zeros((S, om.size), np.complex128)
+    res["oc"] = {name: timed(lambda f=f: capi.tbpm_optical_conductivity(ctx, lat, req(f), 0, 0, mu, kT, width,
+                                                                         om.size, None, so))
+                 for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S))}
+    res["dp"] = {name: timed(lambda f=f: capi.tbpm_polarization(ctx, lat, req(f), (0.3, 0.1, 0.0), mu, kT, om,
+                                                                 None, so))
+                 for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S))}
+    rho = np.zeros((S, n))
+    res["cd"] = {name: timed(lambda f=f: capi.tbpm_charge_density(ctx, lat, req(f), mu, kT, rho))
+                 for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S))}
+    for q in ("qe", "ec", "oc", "dp", "cd"):
+        seq = res[q]["sequential"]
+        res[q]["speedup"] = {k: seq / v for k, v in res[q].items() if k != "sequential"}
+    capi.tbpm_lattice_destroy(lat)
+    return res
+
+
 def run_dense(args, work):
     """Dense Hamiltonians (long-range hopping, D_H = 61 / 124 / 235; the stand-in for the paper's
     twisted bilayer graphene): the moment-based concurrent DOS over N_t steps of tau~ = pi (the
@@ -903,6 +953,9 @@ def run_dense(args, work):
                 "max_rel_dos_difference": float(np.max(np.abs(res["concurrent_m"][1] - res["sequential"][1])) /
                                                 np.max(np.abs(res["sequential"][1])))})
         out["dh_sweep"] = sweep
+
+    if rank == 0 and args.forms:
+        out["forms"] = dense_forms(capi, ctx, desc, S, args.forms_steps)
 
     if rank == 0 and not args.no_cpu and world == 1:
         try:
