@@ -8,10 +8,11 @@
 // step, more than the states themselves.  Here the taps are the same for every site, so no
 // index is stored: a CTA stages a halo'd tile of phi_n (one 16-byte pack = two complex64
 // states per site; 64 honeycomb or 128 square cells by 32 rows) in shared memory and each
-// thread computes 16 consecutive rows of one column of cells.  The taps of one destination sublattice, grouped by (dx, source
-// sublattice), form runs along y; a run piece of n <= 8 taps is applied to the 16 rows
-// as a sliding window, so each shared load feeds up to 4n FMAs and the pass is bound by
-// FP32 FMA issue rather than by HBM (2 (D_H - 1) FMAs per site-update against 24 bytes).
+// thread computes 16 consecutive rows of one column of cells.  The taps of one destination
+// sublattice, grouped by (dx, source sublattice), form runs along y; a run piece of n <= 8
+// taps is applied to the 16 rows as a sliding window, so each shared load feeds up to 4n FMAs
+// and the pass is bound by FP32 FMA issue rather than by HBM (2 (D_H - 1) FMAs per
+// site-update against 24 bytes).
 //
 // Reductions follow the other moment kernels: Neumaier-compensated FP32 per thread, an FP64
 // tree per CTA, per-CTA partials and a fixed-order sum by the last CTA to finish.
@@ -33,8 +34,12 @@ namespace {
 #define TBPM_TAPS_RB 2
 #endif
 
-// run pieces: 2 = pieces of 8 and 4 taps (zero-padded), 1 = every length 1..8, 0 = lengths
-// 8, 4, 2, 1; and whether the chunk table is staged in shared memory (1) or read through L1
+// build-time variants (measured on the D_H = 235 workload: 247 us per launch for the default
+// 0 against 251 us for 1 and 256 us for 2; 284 us with the table read through L1):
+//   TBPM_TAPS_PIECES      2 = pieces of 8 and 4 taps (zero-padded), 1 = every length 1..8,
+//                         0 = lengths 8, 4, 2, 1
+//   TBPM_TAPS_PREFETCH    1 = prefetch phi_{n-1} into L2 before the taps run
+//   TBPM_TAPS_TABLE_SMEM  1 = chunk table staged in shared memory, 0 = read through L1
 #ifndef TBPM_TAPS_PIECES
 #define TBPM_TAPS_PIECES 0
 #endif

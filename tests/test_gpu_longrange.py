@@ -310,12 +310,15 @@ def test_conductivity_matches_oracle(capi, ctx, name, spec, direction, prec, S, 
         ov = np.abs(qe.conj() @ psi[s])
         Dn = np.abs((qe.conj() @ psi[s]).real) / oec.area_per_site(ol.kind)
         for k in range(E.size):
-            # C(t, E) = <J psi(t)|J Psi(E)> / |<psi|Psi(E)>|: errors scale with the Cauchy-Schwarz
-            # bound of the inner product over the normalisation (small where the DOS is small)
+            # C(t, E) = <J psi(t)|J Psi(E)> / |<psi|Psi(E)>|: rounding errors scale with the
+            # Cauchy-Schwarz bound of the inner product, and the normalisation's relative error
+            # with its condition number |psi||Psi| / |<psi|Psi>| (large where the DOS is small)
             scale = np.linalg.norm(J @ psi[s]) * np.linalg.norm(J @ qe[k]) / ov[k]
-            assert np.max(np.abs(C[s, k] - Cref[k])) <= tol * scale, ("C", s, k)
-            bound = Dn[k] * (np.pi / ol.half_width) * (Nt + 1) * scale
-            assert abs(sigma[s, k] - sref[k]) <= tol * bound, ("sigma", s, k)
+            cond = np.linalg.norm(psi[s]) * np.linalg.norm(qe[k]) / ov[k]
+            err_bound = tol * (scale + np.max(np.abs(Cref[k])) * cond)
+            assert np.max(np.abs(C[s, k] - Cref[k])) <= err_bound, ("C", s, k)
+            bound = Dn[k] * (np.pi / ol.half_width) * (Nt + 1) * err_bound
+            assert abs(sigma[s, k] - sref[k]) <= bound, ("sigma", s, k)
     capi.tbpm_lattice_destroy(lat)
 
 
