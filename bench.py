@@ -794,6 +794,8 @@ def dense_forms(capi, ctx, desc, S, Nt):
     rho = np.zeros((S, n))
     res["cd"] = {name: timed(lambda f=f: capi.tbpm_charge_density(ctx, lat, req(f), mu, kT, rho))
                  for name, f in (("sequential", capi.SEQUENTIAL), ("concurrent_s", capi.CONCURRENT_S))}
+    b_opt, t_amxsy, t_axpy = capi.tbpm_block_autotune(ctx, lat, req(capi.CONCURRENT_S), Nt)
+    res["time_block"] = {"b_opt": b_opt, "t_amxsy_ms": t_amxsy, "t_axpy_ms": t_axpy}
     for q in ("qe", "ec", "oc", "dp", "cd"):
         seq = res[q]["sequential"]
         res[q]["speedup"] = {k: seq / v for k, v in res[q].items() if k != "sequential"}
