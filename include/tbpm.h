@@ -185,6 +185,14 @@ int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[8]);
  * launch per Chebyshev step.  Results are bit-identical with graphs on or off.  Phase timing
  * (tbpm_profile) runs the passes without graphs.  enable = 0 drops the cached graphs. */
 int tbpm_set_graphs(tbpm_ctx* ctx, int enable);
+/* Buffered time blocks (default on): the state-based and sequential forms (Sec. II.B, Eq. TE)
+ * keep the Chebyshev vectors phi_n of up to 32 consecutive terms in buffer slots and add
+ * sum_n c_n(j tau~) phi_n to every open accumulator of the block in one pass, instead of one
+ * accumulator update per term; C(t_j) = <psi|psi(t_j)> of the block then comes from one block
+ * inner product.  The arithmetic is the same sum in another order (results agree to rounding).
+ * The buffer takes up to 34 state blocks and shrinks with free memory; with fewer than 4 slots,
+ * or enable = 0, every term updates the accumulators in the recurrence pass itself. */
+int tbpm_set_block_buffering(tbpm_ctx* ctx, int enable);
 /* Memory control of the Fermi-Dirac filtered quantities (tbpm_optical_conductivity,
  * tbpm_polarization, tbpm_charge_density): their states are processed in passes of at most
  * max_states states (rounded down to a power of two; 0 = as many as fit in 85% of the free device

@@ -115,6 +115,7 @@ def load():
         "tbpm_set_pass_states": (C.c_int, [_P, C.c_int]),
         "tbpm_fusion_report": (C.c_int, [_P, C.POINTER(C.c_double)]),
         "tbpm_set_graphs": (C.c_int, [_P, C.c_int]),
+        "tbpm_set_block_buffering": (C.c_int, [_P, C.c_int]),
         "tbpm_truncation_order": (C.c_int64, [C.c_double]),
         "tbpm_block_counts": (C.c_int, [C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_int64)]),
         "tbpm_block_opt": (C.c_int64, [C.c_int64, C.c_double, C.c_double, C.c_double, C.c_int64]),
@@ -136,7 +137,7 @@ def exported_symbols():
             "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
-            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_fusion_report", "tbpm_set_graphs", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
+            "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_fusion_report", "tbpm_set_graphs", "tbpm_set_block_buffering", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
 
@@ -343,6 +344,10 @@ def tbpm_polarization(ctx, lat, req: Request, q, mu: float, kT: float, omegas: n
 
 def tbpm_set_graphs(ctx, enable: bool):
     _check(load().tbpm_set_graphs(ctx, int(bool(enable))))
+
+
+def tbpm_set_block_buffering(ctx, enable: bool):
+    _check(load().tbpm_set_block_buffering(ctx, int(bool(enable))))
 
 
 def tbpm_fusion_report(ctx) -> dict:

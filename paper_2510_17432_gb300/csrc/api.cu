@@ -433,7 +433,7 @@ int tbpm_destroy(tbpm_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->ws_phi[0], &ctx->ws_phi[1], &ctx->ws_psi, &ctx->ws_acc, &ctx->ws_partials,
                     &ctx->ws_counter, &ctx->ws_mu, &ctx->ws_table, &ctx->ws_aux, &ctx->ws_out,
                     &ctx->ws_energies, &ctx->ws_recon, &ctx->ws_phi2[0], &ctx->ws_phi2[1],
-                    &ctx->ws_fused_partials, &ctx->ws_qe, &ctx->ws_qe_coef, &ctx->ws_xdot,
+                    &ctx->ws_fused_partials, &ctx->ws_qe, &ctx->ws_qe_coef, &ctx->ws_xdot, &ctx->ws_blk, &ctx->ws_blk_coef,
                     &ctx->ws_jpsi, &ctx->ws_ec, &ctx->ws_fermi};
   for (DevBuf* b : bufs) release(ctx, *b);
   cudaStreamSynchronize(ctx->stream);
@@ -475,6 +475,16 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     return TBPM_EINVAL;
   }
   ctx->fusion = enable;
+  return TBPM_OK;
+}
+
+int tbpm_set_block_buffering(tbpm_ctx* ctx, int enable) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_set_block_buffering: ctx is NULL");
+    return TBPM_EINVAL;
+  }
+  ctx->buffer_blocks = enable != 0;
   return TBPM_OK;
 }
 
@@ -1330,7 +1340,7 @@ void block_coefficients(double tau, double shift, int bb, std::vector<double>* c
 int64_t block_cap(const Plan& pl, int64_t n_steps) {
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  const int64_t by_mem = (int64_t)std::max<double>(1.0, 0.8 * (double)free_b / (double)pl.state_bytes - 4.0);
+  const int64_t by_mem = (int64_t)std::max<double>(1.0, 0.8 * (double)free_b / (double)pl.state_bytes - 4.0 - 34.0);
   return std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(by_mem, 256), n_steps));
 }
 
@@ -1377,10 +1387,50 @@ int measure_pass_costs(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req
     cudaEventElapsedTime(&ms0, e[0], e[1]);
     cudaEventElapsedTime(&ms1, e[1], e[2]);
   }
-  for (auto& x : e) cudaEventDestroy(x);
-  TBPM_TRY(r);
   *t_amxsy = ms0 / reps;
   *t_axpy = std::max(1e-6, (double)(ms1 - ms0) / reps / k_acc);
+  // buffered blocks: a step is the recurrence into a buffer slot plus its share of the flush's
+  // slot reads; an accumulator update is the flush's extra cost per accumulator and term
+  const int Tm = 8;
+  if (r == TBPM_OK && ctx->buffer_blocks && k_acc >= 2 &&
+      ensure(ctx, ctx->ws_blk, pl.state_bytes * (size_t)Tm) == TBPM_OK &&
+      ensure(ctx, ctx->ws_blk_coef, sizeof(double) * 2 * (size_t)Tm * k_acc) == TBPM_OK) {
+    TBPM_CK(cudaMemsetAsync(ctx->ws_blk_coef.p, 0, sizeof(double) * 2 * (size_t)Tm * k_acc, ctx->stream));
+    TBPM_CK(cudaMemsetAsync(ctx->ws_blk.p, 0, pl.state_bytes * (size_t)Tm, ctx->stream));
+    float m[3] = {0.f, 0.f, 0.f};
+    for (int pass = 0; pass < 2 && r == TBPM_OK; ++pass) {
+      g.b = 0;
+      g.j_lo = 0;
+      g.r.next = ctx->ws_blk.p;
+      cudaEventRecord(e[0], ctx->stream);
+      for (int i = 0; i < reps && r == TBPM_OK; ++i) r = launch_accum_step(ctx, g, pl.precision, ACC_REGULAR);
+      cudaEventRecord(e[1], ctx->stream);
+      for (int i = 0; i < reps && r == TBPM_OK; ++i)
+        r = launch_block_flush(ctx, g.r, pl.precision, ctx->ws_blk.p, Tm, ctx->ws_acc.p, 1,
+                               (const double*)ctx->ws_blk_coef.p);
+      cudaEventRecord(e[2], ctx->stream);
+      for (int i = 0; i < reps && r == TBPM_OK; ++i)
+        r = launch_block_flush(ctx, g.r, pl.precision, ctx->ws_blk.p, Tm, ctx->ws_acc.p, k_acc,
+                               (const double*)ctx->ws_blk_coef.p);
+      cudaEvent_t e3;
+      cudaEventCreate(&e3);
+      cudaEventRecord(e3, ctx->stream);
+      if (r == TBPM_OK && cudaEventSynchronize(e3) == cudaSuccess) {
+        cudaEventElapsedTime(&m[0], e[0], e[1]);
+        cudaEventElapsedTime(&m[1], e[1], e[2]);
+        cudaEventElapsedTime(&m[2], e[2], e3);
+      }
+      cudaEventDestroy(e3);
+    }
+    g.r.next = nullptr;
+    if (r == TBPM_OK) {
+      const double rec = m[0] / reps, f1 = m[1] / reps, fk = m[2] / reps;
+      *t_amxsy = rec + f1 / Tm;
+      *t_axpy = std::max(1e-6, (fk - f1) / ((double)(k_acc - 1) * Tm));
+    }
+  }
+  for (auto& x : e) cudaEventDestroy(x);
+  TBPM_TRY(r);
   return TBPM_OK;
 }
 
@@ -1456,6 +1506,82 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
   g.psi = corr ? ctx->ws_psi.p : nullptr;
   g.C = corr ? d_C : nullptr;
   g.C_len = C_len;
+
+  // Buffered accumulation: the recurrence writes phi_n into a window of T buffer slots, and
+  // every T terms one flush adds sum_t c_t(j) phi_t to every accumulator of the block (each
+  // accumulator crosses HBM once per T terms instead of once per term); C(t_j) = <psi|acc_j>
+  // for the whole block comes from one block inner product at its end.  Slots 0 and 1 carry the
+  // two latest vectors of the previous window, slot 2 + k holds term n0 + k.
+  int T = 0;
+  if (ctx->buffer_blocks) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const int64_t fit = (int64_t)(0.5 * (double)free_b / (double)pl.state_bytes) - 2;
+    const int Nb_full = *std::max_element(nper_full.begin(), nper_full.end());
+    T = (int)std::min<int64_t>(std::min<int64_t>(qe_flush_max_terms(), fit), (int64_t)Nb_full);
+  }
+  if (T >= 4) {
+    TBPM_TRY(ensure(ctx, ctx->ws_blk, pl.state_bytes * (size_t)(T + 2)));
+    // coefficient tables with the terms past N(j tau~) set to zero, full block then last block
+    std::vector<double> cz;
+    auto zeroed = [&](const std::vector<double>& cf, const std::vector<int>& np, int bb) {
+      const int Nb = *std::max_element(np.begin(), np.end());
+      const size_t base = cz.size();
+      cz.insert(cz.end(), cf.begin(), cf.begin() + (size_t)Nb * bb * 2);
+      for (int n = 0; n < Nb; ++n)
+        for (int j = 0; j < bb; ++j)
+          if (n >= np[j]) cz[base + ((size_t)n * bb + j) * 2] = cz[base + ((size_t)n * bb + j) * 2 + 1] = 0.0;
+      return base;
+    };
+    const size_t off_full = zeroed(coef_full, nper_full, (int)b);
+    const size_t off_last = last_len ? zeroed(coef_last, nper_last, (int)last_len) : 0;
+    TBPM_TRY(ensure(ctx, ctx->ws_blk_coef, cz.size() * sizeof(double)));
+    TBPM_CK(cudaMemcpyAsync(ctx->ws_blk_coef.p, cz.data(), cz.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    TBPM_CK(cudaStreamSynchronize(ctx->stream));
+    char* slots = (char*)ctx->ws_blk.p;
+    auto slot = [&](int k) { return (void*)(slots + (size_t)k * pl.state_bytes); };
+    AccumArgs gr = g;
+    gr.b = 0;
+    gr.j_lo = 0;
+    gr.j_done = -1;
+    gr.first_term = 0;
+    int64_t start = 0;
+    while (start < n_steps) {
+      const int bb = (int)std::min<int64_t>(b, n_steps - start);
+      const std::vector<int>& nper = (bb == b) ? nper_full : nper_last;
+      const double* cf = (const double*)ctx->ws_blk_coef.p + ((bb == b) ? off_full : off_last);
+      const int Nb = *std::max_element(nper.begin(), nper.end());
+      TBPM_CK(cudaMemsetAsync(ctx->ws_acc.p, 0, pl.state_bytes * (size_t)bb, ctx->stream));
+      TBPM_CK(cudaMemcpyAsync(slot(2), ctx->ws_phi[0].p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      int n0 = 0;
+      auto slot_of = [&](int m) { return m >= n0 ? slot(2 + (m - n0)) : (m == n0 - 1 ? slot(1) : slot(0)); };
+      for (int n = 1; n < Nb; ++n) {
+        if (n - n0 == T) {
+          TBPM_TRY(launch_block_flush(ctx, gr.r, pl.precision, slot(2), T, ctx->ws_acc.p, bb,
+                                      cf + (size_t)n0 * bb * 2));
+          TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+          TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+          n0 = n;
+        }
+        gr.r.cur = slot_of(n - 1);
+        gr.r.prev_out = n >= 2 ? slot_of(n - 2) : slot_of(n - 1);  // not read by the first step
+        gr.r.next = slot_of(n);
+        TBPM_TRY(launch_accum_step(ctx, gr, pl.precision, n == 1 ? ACC_FIRST : ACC_REGULAR));
+      }
+      TBPM_TRY(launch_block_flush(ctx, gr.r, pl.precision, slot(2), Nb - n0, ctx->ws_acc.p, bb,
+                                  cf + (size_t)n0 * bb * 2));
+      if (corr)
+        TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, lat->n_sites, ctx->ws_psi.p, 1, ctx->ws_acc.p, bb, d_C,
+                             C_len, 0, 1, start + 1));
+      if (hook) TBPM_TRY(hook(start, bb, ctx->ws_acc.p));
+      const char* last = (const char*)ctx->ws_acc.p + (size_t)(bb - 1) * pl.state_bytes;
+      TBPM_CK(cudaMemcpyAsync(ctx->ws_phi[0].p, last, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      start += bb;
+    }
+    return TBPM_OK;
+  }
+
   int64_t start = 0;
   while (start < n_steps) {
     const int bb = (int)std::min<int64_t>(b, n_steps - start);

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_accum_stencil(AccumArgs gargs) 
 #pragma unroll
           for (int w = 0; w < 2 * SPT; ++w) o.v[w] = d * ph.v[w] + th * h.v[w] - pv.v[w];
         }
-        st(po + own, o);
+        st((a.next ? reinterpret_cast<PK*>(a.next) : po) + own, o);
       }
       for (int j = jlo; j < jb; ++j) {
         const R cr = (R)__ldg(gargs.coef + 2 * j), ci = (R)__ldg(gargs.coef + 2 * j + 1);
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kThreads) k_accum_step(AccumArgs g) {
 #pragma unroll
         for (int k = 0; k < 2 * SPT; ++k) o.v[k] = d * ph.v[k] + th * h.v[k] - pv.v[k];
       }
-      st(po + off, o);
+      st((a.next ? reinterpret_cast<PK*>(a.next) : po) + off, o);
     }
     for (int j = g.j_lo; j < g.b; ++j) {
       const R cr = (R)__ldg(g.coef + 2 * j), ci = (R)__ldg(g.coef + 2 * j + 1);
@@ -657,6 +657,55 @@ __global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, 
         const R c = cs[t][e];
 #pragma unroll
         for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] += c * x.v[k];
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < kQeEB; ++e)
+      if (e < ne) st(Q + (int64_t)(e0 + e) * stride_packs + u, acc[e]);
+  }
+}
+
+// Buffered time-block accumulation: acc_j += sum_{t < T} c_t(j) phi_t for the open
+// accumulators of a time block, with T buffered Chebyshev vectors phi_t (consecutive state
+// blocks) and complex coefficients c_t(j) = coef[(t * nb + j) * 2 + {0, 1}] (zero once term t is
+// past N(j tau~)).  Each accumulator is read and written once per T terms instead of once per
+// term.  grid: (accumulator tiles of kQeEB, unit blocks).
+template <typename R, int SPT>
+__global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int T, int64_t stride_packs, void* accv,
+                                                          int nb, const double* coef, int64_t n_units) {
+  using PK = Pack<R, SPT>;
+  __shared__ R cr[kQeMaxT][kQeEB], ci[kQeMaxT][kQeEB];
+  const int e0 = blockIdx.x * kQeEB;
+  const int ne = min(kQeEB, nb - e0);
+  for (int i = threadIdx.x; i < T * kQeEB; i += kThreads) {
+    const int t = i / kQeEB, e = i - t * kQeEB;
+    const bool ok = e < ne;
+    cr[t][e] = ok ? (R)coef[((int64_t)t * nb + e0 + e) * 2] : R(0);
+    ci[t][e] = ok ? (R)coef[((int64_t)t * nb + e0 + e) * 2 + 1] : R(0);
+  }
+  __syncthreads();
+  const PK* Phi = reinterpret_cast<const PK*>(phiv);
+  PK* Q = reinterpret_cast<PK*>(accv);
+  for (int64_t u = (int64_t)blockIdx.y * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.y * kThreads) {
+    PK acc[kQeEB];
+#pragma unroll
+    for (int e = 0; e < kQeEB; ++e) {
+      if (e < ne) acc[e] = ld(Q + (int64_t)(e0 + e) * stride_packs + u);
+      else
+#pragma unroll
+        for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] = R(0);
+    }
+    for (int t = 0; t < T; ++t) {
+      const PK x = ld(Phi + (int64_t)t * stride_packs + u);
+#pragma unroll
+      for (int e = 0; e < kQeEB; ++e) {
+        const R a = cr[t][e], b = ci[t][e];
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          const R xr = x.v[2 * q], xi = x.v[2 * q + 1];
+          acc[e].v[2 * q] += a * xr - b * xi;
+          acc[e].v[2 * q + 1] += a * xi + b * xr;
+        }
       }
     }
 #pragma unroll
@@ -815,6 +864,33 @@ int launch_qe_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const
   int64_t stride = n_units;
   int64_t nu = n_units;
   void* args[] = {(void*)&phi, &T, &stride, &qe, &nE, (void*)&coef, &n0, &nu};
+  cudaError_t e = cudaLaunchKernel(fn, dim3(etiles, ublocks), dim3(kThreads), args, 0, ctx->stream);
+  ctx->launches++;
+  if (e != cudaSuccess) {
+    set_error("kernel launch: %s", cudaGetErrorString(e));
+    return TBPM_ECUDA;
+  }
+  return TBPM_OK;
+}
+
+int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* acc,
+                       int nb, const double* coef) {
+  if (T < 1 || T > kQeMaxT || nb < 1) {
+    set_error("block flush of %d terms into %d accumulators", T, nb);
+    return TBPM_EINVAL;
+  }
+  const int spt = spt_of(precision, a.S);
+  const int64_t n_units = a.n_sites * a.P;
+  const int etiles = (nb + kQeEB - 1) / kQeEB;
+  const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * 8 / etiles);
+  const int ublocks = (int)std::min<int64_t>(std::min<int64_t>(want, (n_units + kThreads - 1) / kThreads), 65535);
+  void* fn;
+  if (precision == TBPM_C128) fn = (void*)k_block_flush<double, 1>;
+  else if (spt == 2) fn = (void*)k_block_flush<float, 2>;
+  else fn = (void*)k_block_flush<float, 1>;
+  int64_t stride = n_units;
+  int64_t nu = n_units;
+  void* args[] = {(void*)&phi, &T, &stride, &acc, &nb, (void*)&coef, &nu};
   cudaError_t e = cudaLaunchKernel(fn, dim3(etiles, ublocks), dim3(kThreads), args, 0, ctx->stream);
   ctx->launches++;
   if (e != cudaSuccess) {

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
         out.z -= pv.z;
         out.w -= pv.w;
       }
-      po[off] = out;
+      (a.next ? reinterpret_cast<float4*>(a.next) : po)[off] = out;
       if constexpr (MOM) {
         A0.add(ph.x * ph.x + ph.y * ph.y);
         R0.add(out.x * ph.x + out.y * ph.y);

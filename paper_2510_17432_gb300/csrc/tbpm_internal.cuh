@@ -152,7 +152,9 @@ struct tbpm_ctx {
   int64_t launches = 0;
   // cached workspaces (grow-only, stream-ordered allocations)
   tbpm::DevBuf ws_phi[2], ws_psi, ws_acc, ws_partials, ws_counter, ws_mu, ws_table, ws_aux, ws_out,
-      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi;
+      ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi, ws_blk, ws_blk_coef;
+  // time blocks buffer up to 32 Chebyshev vectors and flush them into the accumulators at once
+  bool buffer_blocks = true;
   int fusion = 5;  // temporal-fusion mode of the moment pass (5 = four-step row sweep; -1 = autotuned)
   // autotuned fusion modes: key (kind, Lx, Ly, Lz, pbc bits, path, Spad, precision, disorder) -> mode
   std::vector<std::pair<std::vector<int64_t>, int>> fusion_choice;
@@ -234,6 +236,7 @@ struct RecurrenceArgs {
   // states
   const void* cur;     // phi_n      [n_sites][S]
   void* prev_out;      // phi_{n-1} in, phi_{n+1} out
+  void* next;          // accumulation passes: phi_{n+1} goes here instead (null: into prev_out)
   // lattice
   Geom geom;
   int path;
@@ -295,6 +298,10 @@ int launch_taps_moment(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);
 int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first);  // recurrence only
 size_t taps_partials_bytes(const RecurrenceArgs& a);
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
+// acc_j += sum_{t<T} c_t(j) phi_t over T consecutive buffered state blocks phi and nb
+// consecutive accumulators; coef [T][nb] complex (csrc/cheb.cu)
+int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* acc,
+                       int nb, const double* coef);
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
