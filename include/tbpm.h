@@ -191,7 +191,8 @@ int tbpm_set_graphs(tbpm_ctx* ctx, int enable);
  * accumulator update per term; C(t_j) = <psi|psi(t_j)> of the block then comes from one block
  * inner product.  The arithmetic is the same sum in another order (results agree to rounding).
  * The buffer takes up to 34 state blocks and shrinks with free memory; with fewer than 4 slots,
- * or enable = 0, every term updates the accumulators in the recurrence pass itself. */
+ * the sequential form (b = 1), or enable = 0, every term updates the accumulators in the
+ * recurrence pass itself. */
 int tbpm_set_block_buffering(tbpm_ctx* ctx, int enable);
 /* Memory control of the Fermi-Dirac filtered quantities (tbpm_optical_conductivity,
  * tbpm_polarization, tbpm_charge_density): their states are processed in passes of at most

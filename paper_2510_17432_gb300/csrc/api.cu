@@ -1437,7 +1437,10 @@ int measure_pass_costs(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req
 // b_opt = argmin_b C(b) with measured costs (Sec. II.B), capped by memory.
 int choose_block(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t n_steps,
                  int64_t* b, double* t_amxsy, double* t_axpy) {
-  const int64_t cap = block_cap(pl, n_steps);
+  int64_t cap = block_cap(pl, n_steps);
+  // buffered blocks: one flush serves 16 accumulators per pass over the buffer; past that every
+  // further 16 re-read the buffer, which the linear cost model does not see
+  if (ctx->buffer_blocks) cap = std::min<int64_t>(cap, 16);
   double ta = 0, tx = 0;
   TBPM_TRY(measure_pass_costs(ctx, lat, req, pl, (int)std::min<int64_t>(cap, 8), &ta, &tx));
   if (t_amxsy) *t_amxsy = ta;
@@ -1513,7 +1516,7 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
   // for the whole block comes from one block inner product at its end.  Slots 0 and 1 carry the
   // two latest vectors of the previous window, slot 2 + k holds term n0 + k.
   int T = 0;
-  if (ctx->buffer_blocks) {
+  if (ctx->buffer_blocks && b >= 2) {  // the sequential form keeps its fused one-accumulator pass
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const int64_t fit = (int64_t)(0.5 * (double)free_b / (double)pl.state_bytes) - 2;
