@@ -699,12 +699,14 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
       const PK x = ld(Phi + (int64_t)t * stride_packs + u);
 #pragma unroll
       for (int e = 0; e < kQeEB; ++e) {
-        const R a = cr[t][e], b = ci[t][e];
+        if (e < ne) {  // uniform: a tile of fewer accumulators does no work for the rest
+          const R a = cr[t][e], b = ci[t][e];
 #pragma unroll
-        for (int q = 0; q < SPT; ++q) {
-          const R xr = x.v[2 * q], xi = x.v[2 * q + 1];
-          acc[e].v[2 * q] += a * xr - b * xi;
-          acc[e].v[2 * q + 1] += a * xi + b * xr;
+          for (int q = 0; q < SPT; ++q) {
+            const R xr = x.v[2 * q], xi = x.v[2 * q + 1];
+            acc[e].v[2 * q] += a * xr - b * xi;
+            acc[e].v[2 * q + 1] += a * xi + b * xr;
+          }
         }
       }
     }
