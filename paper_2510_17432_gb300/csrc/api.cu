@@ -1395,8 +1395,12 @@ int measure_pass_costs(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req
   if (r == TBPM_OK && ctx->buffer_blocks && k_acc >= 2 &&
       ensure(ctx, ctx->ws_blk, pl.state_bytes * (size_t)Tm) == TBPM_OK &&
       ensure(ctx, ctx->ws_blk_coef, sizeof(double) * 2 * (size_t)Tm * k_acc) == TBPM_OK) {
-    TBPM_CK(cudaMemsetAsync(ctx->ws_blk_coef.p, 0, sizeof(double) * 2 * (size_t)Tm * k_acc, ctx->stream));
-    TBPM_CK(cudaMemsetAsync(ctx->ws_blk.p, 0, pl.state_bytes * (size_t)Tm, ctx->stream));
+    if (cudaMemsetAsync(ctx->ws_blk_coef.p, 0, sizeof(double) * 2 * (size_t)Tm * k_acc, ctx->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(ctx->ws_blk.p, 0, pl.state_bytes * (size_t)Tm, ctx->stream) != cudaSuccess) {
+      set_error("measure_pass_costs: %s", cudaGetErrorString(cudaGetLastError()));
+      r = TBPM_ECUDA;
+    }
     float m[3] = {0.f, 0.f, 0.f};
     for (int pass = 0; pass < 2 && r == TBPM_OK; ++pass) {
       g.b = 0;
