@@ -63,7 +63,10 @@ def test_buffered_blocks_match_oracle_and_unbuffered(capi, ctx, name, spec, prec
         capi.tbpm_set_block_buffering(ctx, False)
         Cu = _corr(capi, ctx, lat, S, Nt, prec, form, b)
         capi.tbpm_set_block_buffering(ctx, True)
-        assert np.array_equal(Cb, Cb2)
+        if b > 0 or form == capi.SEQUENTIAL:  # b = 0 is chosen from measured pass times per call
+            assert np.array_equal(Cb, Cb2)
+        else:
+            assert np.max(np.abs(Cb - Cb2)) <= 2 * TOL[prec]
         for s in range(S):
             assert np.max(np.abs(Cb[s] - refs[s])) / abs(refs[s][0]) <= TOL[prec], (form, b, s)
             assert np.max(np.abs(Cb[s] - Cu[s])) / abs(refs[s][0]) <= 2 * TOL[prec], (form, b, s)
