@@ -670,6 +670,11 @@ __global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, 
 // blocks) and complex coefficients c_t(j) = coef[(t * nb + j) * 2 + {0, 1}] (zero once term t is
 // past N(j tau~)).  Each accumulator is read and written once per T terms instead of once per
 // term.  grid: (accumulator tiles of kQeEB, unit blocks).
+#ifndef TBPM_FLUSH_UNROLL
+#define TBPM_FLUSH_UNROLL 4
+#endif
+constexpr int kFlushUnroll = TBPM_FLUSH_UNROLL;
+
 template <typename R, int SPT>
 __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int T, int64_t stride_packs, void* accv,
                                                           int nb, const double* coef, int64_t n_units) {
@@ -695,7 +700,8 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
 #pragma unroll
         for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] = R(0);
     }
-    for (int t = 0; t < T; ++t) {
+#pragma unroll (kFlushUnroll)
+    for (int t = 0; t < T; ++t) {  // unrolled so that several buffer loads are in flight
       const PK x = ld(Phi + (int64_t)t * stride_packs + u);
 #pragma unroll
       for (int e = 0; e < kQeEB; ++e) {
