@@ -1816,6 +1816,39 @@ int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
     TBPM_TRY(base_args(ctx, lat, pl, &g.r, 3));
     g.b = 0;
     g.j_done = -1;
+    // buffered: the recurrence fills a window of up to 32 slots and one block inner product
+    // gives the window's moments against all kets (each ket read once per window, not per term);
+    // slots 0 and 1 carry the previous window's last two vectors, slot 2 + a holds term n0 + a
+    int T = 0;
+    if (ctx->buffer_blocks) {
+      size_t free_b = 0, total_b = 0;
+      cudaMemGetInfo(&free_b, &total_b);
+      const int64_t fit = (int64_t)(0.5 * (double)free_b / (double)pl.state_bytes) - 2;
+      T = (int)std::min<int64_t>(std::min<int64_t>(qe_flush_max_terms(), fit), Nn);
+    }
+    if (T >= 4) {
+      TBPM_TRY(ensure(ctx, ctx->ws_blk, pl.state_bytes * (size_t)(T + 2)));
+      char* slots = (char*)ctx->ws_blk.p;
+      auto slot = [&](int64_t k) { return (void*)(slots + (size_t)k * pl.state_bytes); };
+      int64_t n0 = 0;
+      auto slot_of = [&](int64_t t) { return t >= n0 ? slot(2 + (t - n0)) : (t == n0 - 1 ? slot(1) : slot(0)); };
+      TBPM_CK(cudaMemcpyAsync(slot(2), ctx->ws_jpsi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      for (int64_t k = 1; k < Nn; ++k) {
+        if (k - n0 == T) {
+          TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, slot(2), T, kets, nE, m, (int64_t)nE * Nn, 1, Nn, n0));
+          TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+          TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+          n0 = k;
+        }
+        g.r.cur = slot_of(k - 1);
+        g.r.prev_out = k >= 2 ? slot_of(k - 2) : slot_of(k - 1);  // not read by the first step
+        g.r.next = slot_of(k);
+        TBPM_TRY(launch_accum_step(ctx, g, pl.precision, k == 1 ? ACC_FIRST : ACC_REGULAR));
+      }
+      TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, slot(2), (int)(Nn - n0), kets, nE, m, (int64_t)nE * Nn, 1,
+                           Nn, n0));
+      g.r.next = nullptr;
+    } else {
     TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_phi[0].p, 1, kets, nE, m, (int64_t)nE * Nn, 0, Nn, 0));
     for (int64_t k = 0; k + 1 < Nn; ++k) {
       g.r.cur = ctx->ws_phi[k & 1].p;
@@ -1823,6 +1856,7 @@ int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
       TBPM_TRY(launch_accum_step(ctx, g, pl.precision, k == 0 ? ACC_FIRST : ACC_REGULAR));
       TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, ctx->ws_phi[(k + 1) & 1].p, 1, kets, nE, m,
                            (int64_t)nE * Nn, 0, Nn, k + 1));
+    }
     }
     phase_end(ctx, tok);
     const int n_table = (int)Nn + 8;
