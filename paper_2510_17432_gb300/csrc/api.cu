@@ -1927,6 +1927,40 @@ int apply_series_bufs(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, void* b0
   g.b = 1;
   g.j_lo = 0;
   g.j_done = -1;
+  // buffered: terms go into a window of up to 32 slots and one flush adds sum_n a_n T_n phi to
+  // the output per window (the same bookkeeping as the buffered time blocks)
+  int T = 0;
+  if (ctx->buffer_blocks) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const int64_t fit = (int64_t)(0.5 * (double)free_b / (double)pc.state_bytes) - 2;
+    T = (int)std::min<int64_t>(std::min<int64_t>(qe_flush_max_terms(), fit), (int64_t)n_terms);
+  }
+  if (T >= 4) {
+    TBPM_TRY(ensure(ctx, ctx->ws_blk, pc.state_bytes * (size_t)(T + 2)));
+    char* slots = (char*)ctx->ws_blk.p;
+    auto slot = [&](int k) { return (void*)(slots + (size_t)k * pc.state_bytes); };
+    int n0 = 0;
+    auto slot_of = [&](int t) { return t >= n0 ? slot(2 + (t - n0)) : (t == n0 - 1 ? slot(1) : slot(0)); };
+    TBPM_CK(cudaMemsetAsync(out, 0, pc.state_bytes, ctx->stream));
+    TBPM_CK(cudaMemcpyAsync(slot(2), b0, pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    g.b = 0;
+    for (int n = 1; n < n_terms; ++n) {
+      if (n - n0 == T) {
+        TBPM_TRY(launch_block_flush(ctx, g.r, pc.precision, slot(2), T, out, 1, coef + 2 * (size_t)n0));
+        TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        n0 = n;
+      }
+      g.r.cur = slot_of(n - 1);
+      g.r.prev_out = n >= 2 ? slot_of(n - 2) : slot_of(n - 1);  // not read by the first step
+      g.r.next = slot_of(n);
+      TBPM_TRY(launch_accum_step(ctx, g, pc.precision, n == 1 ? ACC_FIRST : ACC_REGULAR));
+    }
+    TBPM_TRY(launch_block_flush(ctx, g.r, pc.precision, slot(2), n_terms - n0, out, 1, coef + 2 * (size_t)n0));
+    release(ctx, ctx->ws_blk);  // the callers' next step sizes its blocks by the free memory
+    return TBPM_OK;
+  }
   void* buf[2] = {b0, b1};
   for (int n = 0; n < n_terms; ++n) {
     const int mode = (n == n_terms - 1) ? ACC_NOSPMV : (n == 0 ? ACC_FIRST : ACC_REGULAR);
