@@ -119,3 +119,16 @@ def test_kramers_kronig_on_a_lorentzian():
         assert abs(im[k] - om[k] / (om[k] ** 2 + g ** 2)) < 1e-7
     with pytest.raises(ValueError):
         R.kramers_kronig_imag(np.array([0.1, 0.2, 0.4]), np.ones(3))
+
+
+def test_oc_correlation_equals_lehmann_form_on_a_long_range_lattice():
+    """The Kubo correlation of the optical conductivity on a long-range lattice (each bond its own
+    vector in the current operator) against the eigen-decomposition form."""
+    lat = olat.build_lattice(olat.HONEYCOMB, (5, 4, 1), t=-2.7, W=0.8, seed=21, cutoff=3.1, decay=0.5)
+    psi = oprop.random_phase_states(lat, 2, 1)[0]
+    mu, kT, Nt = 0.3, 0.4, 12
+    ts = np.arange(Nt + 1) * (np.pi / 2) / lat.half_width
+    for a, b in ((0, 0), (0, 1), (1, 1)):
+        C = R.oc_correlation_sequential(lat, psi, a, b, mu, kT, Nt)
+        L_ = R.lehmann_correlation(lat, psi, oec.current_operator(lat, a), oec.current_operator(lat, b), mu, kT, ts)
+        assert np.max(np.abs(C - L_)) < 1e-12 * max(1.0, np.max(np.abs(L_)))
