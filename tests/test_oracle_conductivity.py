@@ -54,3 +54,15 @@ def test_correlation_forms_and_exact_diagonalisation():
         for k in range(E.size):
             ref = np.vdot(Jpsi, eiHt @ (J @ qe[k])) / abs(np.vdot(psi, qe[k]))
             assert abs(Cs[k, j] - ref) < 1e-11
+
+
+@pytest.mark.parametrize("kind,L,cutoff", [(lattice.HONEYCOMB, (5, 4, 1), 3.1), (lattice.SQUARE, (6, 5, 1), 2.9),
+                                           (lattice.CUBIC, (4, 3, 3), 1.8)])
+def test_long_range_current_operator_is_commutator_on_open_lattices(kind, L, cutoff):
+    """Without periodic images every bond vector is r_j - r_i, so J_a = i[H, P_a] exactly."""
+    lat = lattice.build_lattice(kind, L, t=-1.3, W=0.8, seed=2, pbc=(0, 0, 0), cutoff=cutoff, decay=0.6)
+    H = lat.H.toarray()
+    for direction in range(3 if kind == lattice.CUBIC else 2):
+        J = ec.current_operator(lat, direction).toarray()
+        P = -np.diag(positions(lat)[:, direction])
+        assert np.max(np.abs(J - 1j * (H @ P - P @ H))) < 1e-13
