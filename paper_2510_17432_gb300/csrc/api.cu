@@ -1080,6 +1080,7 @@ int base_args(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pl, RecurrenceArgs* 
     a->taps_n1 = lat->n_chunks[1];
     a->taps_rx = lat->halo_x;
     a->taps_ry = lat->halo_y;
+    a->taps_exact = lat->tap_exact ? 1 : 0;
   }
   if (!a->taps) TBPM_TRY(ensure_ell(ctx, lat));
   a->ell = lat->ell;
@@ -1262,6 +1263,7 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
         (uint64_t)g.Lx, (uint64_t)g.Ly, (uint64_t)g.Lz, (uint64_t)g.kind,
         (uint64_t)(g.pbc_x | (g.pbc_y << 1) | (g.pbc_z << 2)), (uint64_t)lat->path, (uint64_t)lat->n_sites,
         (uint64_t)lat->chunks, (uint64_t)a.taps_rx, (uint64_t)a.taps_ry, (uint64_t)a.taps_n0, (uint64_t)a.taps_n1,
+        (uint64_t)a.taps_exact,
         (uint64_t)lat->wrel32, (uint64_t)lat->wrel64};
     tbpm_ctx::Graph* hit = nullptr;
     for (auto& e : ctx->graphs)

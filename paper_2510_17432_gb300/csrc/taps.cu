@@ -36,13 +36,8 @@ namespace {
 
 // build-time variants (measured on the D_H = 235 workload: 247 us per launch for the default
 // 0 against 251 us for 1 and 256 us for 2; 284 us with the table read through L1):
-//   TBPM_TAPS_PIECES      2 = pieces of 8 and 4 taps (zero-padded), 1 = every length 1..8,
-//                         0 = lengths 8, 4, 2, 1
 //   TBPM_TAPS_PREFETCH    1 = prefetch phi_{n-1} into L2 before the taps run
 //   TBPM_TAPS_TABLE_SMEM  1 = chunk table staged in shared memory, 0 = read through L1
-#ifndef TBPM_TAPS_PIECES
-#define TBPM_TAPS_PIECES 0
-#endif
 #ifndef TBPM_TAPS_PREFETCH
 #define TBPM_TAPS_PREFETCH 0
 #endif
@@ -107,7 +102,9 @@ __device__ __forceinline__ void tap_piece(float2 (&lo)[kTapOY], float2 (&hi)[kTa
 
 // MOM: fuse the moment sums (moment pass); without it the kernel is the plain recurrence step
 // that the accumulation passes pair with an accumulate-only pass.
-template <int NSUB, bool FIRST, bool MOM>
+// EXACT: run pieces of every length 1..8 (fewer, longer pieces; best below D_H ~ 180), else
+// pieces of 8, 4, 2 and 1 taps (fewer kernel variants in the dispatch; best at D_H = 235)
+template <int NSUB, bool FIRST, bool MOM, bool EXACT>
 __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(RecurrenceArgs a) {
   constexpr int TX = TapShape<NSUB>::TX;
   extern __shared__ float4 smem[];
@@ -187,21 +184,24 @@ __global__ void __launch_bounds__(kTapThreads, kTapMinBlocks) k_taps_moment(Recu
 #endif
     const float4* col = tile + (r0 + hd.y) * RS + hd.z * TW + RX + xl + hd.x;
     const float* w = ch[c].w;
-    switch (hd.w) {
-      case 8: tap_piece<8>(lo, hi, col, RS, w); break;
-#if TBPM_TAPS_PIECES == 1
-      case 7: tap_piece<7>(lo, hi, col, RS, w); break;
-      case 6: tap_piece<6>(lo, hi, col, RS, w); break;
-      case 5: tap_piece<5>(lo, hi, col, RS, w); break;
-      case 3: tap_piece<3>(lo, hi, col, RS, w); break;
-#endif
-#if TBPM_TAPS_PIECES == 2
-      default: tap_piece<4>(lo, hi, col, RS, w); break;
-#else
-      case 4: tap_piece<4>(lo, hi, col, RS, w); break;
-      case 2: tap_piece<2>(lo, hi, col, RS, w); break;
-      default: tap_piece<1>(lo, hi, col, RS, w); break;
-#endif
+    if constexpr (EXACT) {
+      switch (hd.w) {
+        case 8: tap_piece<8>(lo, hi, col, RS, w); break;
+        case 7: tap_piece<7>(lo, hi, col, RS, w); break;
+        case 6: tap_piece<6>(lo, hi, col, RS, w); break;
+        case 5: tap_piece<5>(lo, hi, col, RS, w); break;
+        case 4: tap_piece<4>(lo, hi, col, RS, w); break;
+        case 3: tap_piece<3>(lo, hi, col, RS, w); break;
+        case 2: tap_piece<2>(lo, hi, col, RS, w); break;
+        default: tap_piece<1>(lo, hi, col, RS, w); break;
+      }
+    } else {
+      switch (hd.w) {
+        case 8: tap_piece<8>(lo, hi, col, RS, w); break;
+        case 4: tap_piece<4>(lo, hi, col, RS, w); break;
+        case 2: tap_piece<2>(lo, hi, col, RS, w); break;
+        default: tap_piece<1>(lo, hi, col, RS, w); break;
+      }
     }
   }
 
@@ -328,13 +328,17 @@ static int launch_taps(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first, bool 
     set_error("tap kernel: grid %lld or shared memory %zu out of range", (long long)grid, smem);
     return TBPM_EUNSUPPORTED;
   }
-  void* fn;
-  if (mom)
-    fn = hc ? (first ? (void*)k_taps_moment<2, true, true> : (void*)k_taps_moment<2, false, true>)
-            : (first ? (void*)k_taps_moment<1, true, true> : (void*)k_taps_moment<1, false, true>);
-  else
-    fn = hc ? (first ? (void*)k_taps_moment<2, true, false> : (void*)k_taps_moment<2, false, false>)
-            : (first ? (void*)k_taps_moment<1, true, false> : (void*)k_taps_moment<1, false, false>);
+  // [exact][honeycomb][first][moments]
+  static void* const fns[2][2][2][2] = {
+      {{{(void*)k_taps_moment<1, false, false, false>, (void*)k_taps_moment<1, false, true, false>},
+        {(void*)k_taps_moment<1, true, false, false>, (void*)k_taps_moment<1, true, true, false>}},
+       {{(void*)k_taps_moment<2, false, false, false>, (void*)k_taps_moment<2, false, true, false>},
+        {(void*)k_taps_moment<2, true, false, false>, (void*)k_taps_moment<2, true, true, false>}}},
+      {{{(void*)k_taps_moment<1, false, false, true>, (void*)k_taps_moment<1, false, true, true>},
+        {(void*)k_taps_moment<1, true, false, true>, (void*)k_taps_moment<1, true, true, true>}},
+       {{(void*)k_taps_moment<2, false, false, true>, (void*)k_taps_moment<2, false, true, true>},
+        {(void*)k_taps_moment<2, true, false, true>, (void*)k_taps_moment<2, true, true, true>}}}};
+  void* fn = fns[a.taps_exact ? 1 : 0][hc ? 1 : 0][first ? 1 : 0][mom ? 1 : 0];
   TBPM_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   RecurrenceArgs aa = a;
   void* args[] = {&aa};
@@ -353,19 +357,19 @@ int launch_taps_step(tbpm_ctx* ctx, const RecurrenceArgs& a, bool first) { retur
 
 // Column-run pieces of the taps of every destination sublattice.  Sublattice 1 of the honeycomb
 // takes each tap mirrored, (-dx, -dy, 1-ds), as the ELL builder does.  A run of one (dx, ds)
-// spans its lowest to highest dy (holes weigh 0) and is cut into pieces of 8 taps and then of
-// 4, 2 and 1 (or one piece of the 1..7 that remain), so the tile halo is the largest |dx| and
-// |dy| of any tap.  Lattices
-// whose tile would not fit shared memory, cubic lattices and lattices with vacancies keep the
-// ELL path only.
+// spans its lowest to highest dy (holes weigh 0) and is cut into pieces of 8 taps and then one
+// piece of the 1..7 that remain (below 180 taps per site, measured faster there: 141 against
+// 152 us at D_H = 61) or pieces of 4, 2 and 1 (247 against 251 us at D_H = 235), so the tile
+// halo is the largest |dx| and |dy| of any tap.  Lattices whose tile would not fit shared
+// memory, cubic lattices and lattices with vacancies keep the ELL path only.
 int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
   const tbpm_lattice_desc& d = lat->desc;
   if (lat->tap_t.empty() || d.kind == TBPM_CUBIC || d.vacancy_frac > 0.0) return TBPM_OK;
   const int nsub = d.kind == TBPM_HONEYCOMB ? 2 : 1;
   const size_t z = lat->tap_t.size();
+  const bool exact = z < 180;
   std::vector<TapChunk> out;
-  int rx = 0, ry = 0, ry_taps = 0;
-  for (size_t k = 0; k < z; ++k) ry_taps = std::max(ry_taps, std::abs(lat->tap_off[4 * k + 1]));
+  int rx = 0, ry = 0;
   for (int sub = 0; sub < nsub; ++sub) {
     std::map<std::pair<int, int>, std::map<int, float>> runs;  // (dx, ds) -> dy -> weight
     for (size_t k = 0; k < z; ++k) {
@@ -386,18 +390,8 @@ int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
         c.dx = kv.first.first;
         c.ds = kv.first.second;
         const int left = hi - pos + 1;
-#if TBPM_TAPS_PIECES == 2
-        // zero-padded pieces of 8 or 4; one that would reach past the largest |dy| of any tap
-        // starts lower (its rows already covered weigh 0), so the halo stays that |dy|
-        c.n = left > 4 ? 8 : 4;
-        c.dy0 = std::min(pos, std::max(ry_taps - c.n + 1, -ry_taps));
-#elif TBPM_TAPS_PIECES == 1
-        c.n = std::min(8, left);
+        c.n = exact ? std::min(8, left) : (left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1);
         c.dy0 = pos;
-#else
-        c.n = left >= 8 ? 8 : left >= 4 ? 4 : left >= 2 ? 2 : 1;
-        c.dy0 = pos;
-#endif
         for (int k = 0; k < c.n; ++k) {
           auto it = kv.second.find(c.dy0 + k);
           c.w[k] = (c.dy0 + k < pos || it == kv.second.end()) ? 0.f : it->second;
@@ -418,6 +412,7 @@ int build_tap_chunks(tbpm_ctx* ctx, tbpm_lattice* lat) {
   }
   lat->halo_x = rx;
   lat->halo_y = ry;
+  lat->tap_exact = exact;
   TBPM_CK(cudaMallocAsync((void**)&lat->chunks, out.size() * sizeof(TapChunk), ctx->stream));
   TBPM_CK(cudaMemcpyAsync(lat->chunks, out.data(), out.size() * sizeof(TapChunk), cudaMemcpyHostToDevice,
                           ctx->stream));

@@ -218,6 +218,7 @@ struct tbpm_lattice {
   TapChunk* chunks = nullptr;
   int n_chunks[2] = {0, 0};
   int halo_x = 0, halo_y = 0;
+  bool tap_exact = false;        // run pieces of every length 1..8 (else 8, 4, 2, 1)
   int64_t* compact = nullptr;  // [n_full] compact index or -1 (CSR path only)
   int64_t* full_of = nullptr;  // [n_sites] full index of each compact site (CSR path only)
 };
@@ -244,7 +245,7 @@ struct RecurrenceArgs {
   const void* wrel;    // per-slot weights t_k/t (float* or double*), or null (every bond t)
   // matrix-free tap kernel (complex64, >= 2 states): chunk table, counts, halo, partial sums
   const TapChunk* taps;
-  int taps_n0, taps_n1, taps_rx, taps_ry;
+  int taps_n0, taps_n1, taps_rx, taps_ry, taps_exact;
   double* tap_partials;
   const void* diag;    // per-site D_i (float* or double*), or null when the lattice is clean
   double diag_const;   // D when diag == null
