@@ -34,8 +34,8 @@ namespace {
 #define TBPM_TAPS_RB 2
 #endif
 
-// build-time variants (measured on the D_H = 235 workload: 247 us per launch for the default
-// 0 against 251 us for 1 and 256 us for 2; 284 us with the table read through L1):
+// build-time variants (on the D_H = 235 workload the table read through L1 took 284 us per
+// launch against 256 us staged in shared memory; the prefetch is off by default):
 //   TBPM_TAPS_PREFETCH    1 = prefetch phi_{n-1} into L2 before the taps run
 //   TBPM_TAPS_TABLE_SMEM  1 = chunk table staged in shared memory, 0 = read through L1
 #ifndef TBPM_TAPS_PREFETCH
