@@ -56,6 +56,16 @@ KERNEL_SRCS = {
     "k_fused_cols": ("fused.cu",),
     "k_fused_rows": ("fused.cu",),
 }
+# Chebyshev steps per launch and kernel of each fusion mode of the moment pass
+FUSION_STEPS = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2}
+FUSION_KERNELS = {1: "k_fused_cols (4 Chebyshev steps per pass, 2-D tiles)",
+                  2: "k_fused_cols (2 Chebyshev steps per pass, 2-D tiles)",
+                  3: "k_fused_rows<128> (2 Chebyshev steps per pass, row sweep)",
+                  4: "k_fused_rows<256> (2 Chebyshev steps per pass, row sweep)",
+                  5: "k_fused_rowsK<128, 4> (4 Chebyshev steps per pass, row sweep)",
+                  6: "k_fused_rowsK<256, 4> (4 Chebyshev steps per pass, row sweep)",
+                  7: "k_fused_rowsK<256, 2> (2 Chebyshev steps per pass, row sweep)"}
+FUSION_TRAFFIC_FAMILY = {}
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -86,7 +96,15 @@ def parse():
     p.add_argument("--forms-steps", type=int, default=512)
     p.add_argument("--seq-steps", type=int, default=0,
                    help="dense workloads: N_t of the D_H sweep against the sequential form (0 = the workload's)")
-    p.add_argument("--log2-max-sites", type=int, default=20)
+    p.add_argument("--log2-max-sites", type=int, default=24)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
+    p.add_argument("--serving-requests", type=int, default=512,
+                   help="requests of the serving leg (reduced to fit --serving-budget-s, stated in the line)")
+    p.add_argument("--serving-budget-s", type=float, default=150.0)
+    p.add_argument("--no-largest", action="store_true",
+                   help="skip the 1.015e9-site honeycomb leg (S = 4, M = 8192) of the default line")
+    p.add_argument("--prof-steps", type=int, default=2,
+                   help="steps of the separate profiled pass that times the dominant kernel")
     p.add_argument("--load", type=float, default=0.8, help="arrival rate as a fraction of measured capacity")
     return p.parse_args()
 
@@ -341,10 +359,10 @@ def run_gpu(args, work):
         step_device()
     barrier()
 
+    # timed region: the product's own configuration (CUDA graphs on, no phase events)
     clocks = Clocks(local)
     clocks.start()
     launches0 = capi.tbpm_launch_count(ctx)
-    capi.tbpm_profile(ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     ev0.record(stream)
@@ -353,13 +371,26 @@ def run_gpu(args, work):
     ev1.record(stream)
     barrier()
     dev_ms = ev0.elapsed_time(ev1)
-    prof = capi.tbpm_profile_read(ctx)
-    capi.tbpm_profile(ctx, False)
     launches = capi.tbpm_launch_count(ctx) - launches0
     clk = clocks.stop()
     dev_ms = reduce_max(pg, dev_ms, dev)
     ms_per_step = dev_ms / args.steps
     value = whole_job_rate(site_updates, world, ms_per_step / 1e3)
+
+    # separate profiled pass (phase events on the library stream; graphs off while profiling):
+    # the dominant kernel's average launch time and the phase shares of a step
+    prof_steps = max(1, args.prof_steps)
+    capi.tbpm_profile(ctx, True)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    pe0.record(stream)
+    for _ in range(prof_steps):
+        step_device()
+    pe1.record(stream)
+    barrier()
+    prof_ms = pe0.elapsed_time(pe1)
+    prof = capi.tbpm_profile_read(ctx)
+    capi.tbpm_profile(ctx, False)
 
     # parity of this run's output against the oracle is covered by the tests; sanity here
     D = d_D.cpu().numpy()
@@ -381,18 +412,24 @@ def run_gpu(args, work):
     e2e = {"value": whole_job_rate(site_updates, world, e2e_s), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
 
-    # ---- roofline of the dominant kernel, from the live events.  Algorithmic bytes: 24 B per
-    # site-update (read phi_n, read phi_{n-1}, write phi_{n+1}, complex64) + 4 B per site with disorder.
-    per_site_step = 3.0 * elem * info.n_sites * S + ((elem / 2) * info.n_sites if spec.W != 0.0 else 0.0)
-    total_alg = per_site_step * (M // 2) * args.steps
-    if prof["fused_launches"] > 0:
-        steps_per_launch = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2}[args.fusion]
-        kname = (f"k_fused_cols ({steps_per_launch} Chebyshev steps per pass, complex64 state pairs)"
-                 if args.fusion in (1, 2) else
-                 f"k_fused_rows ({steps_per_launch} Chebyshev steps per pass, row sweep)")
+    # ---- roofline of the dominant kernel, from the profiled pass's events.  Unfused one-step
+    # pass: 24 B per site-update (read phi_n, read phi_{n-1}, write phi_{n+1}, complex64) + 4 B
+    # per site of D_i with disorder.  Fused K-step pass: each state block crosses HBM four times
+    # per launch (read phi_{n-1}, phi_n; write phi_{n+K-1}, phi_{n+K}) + D_i once: those are the
+    # launch's algorithmic bytes and `frac` is an HBM fraction; the 24 B-per-site-update figure
+    # of the same launch is reported beside it as frac_unfused_equiv.
+    diag_bytes = (elem / 2) * info.n_sites if spec.W != 0.0 else 0.0
+    per_site_step = 3.0 * elem * info.n_sites * S + diag_bytes
+    fused_launch = prof["fused_launches"] > 0
+    if fused_launch:
+        steps_per_launch = FUSION_STEPS[args.fusion]
+        kname = FUSION_KERNELS[args.fusion]
         per_launch_ms = prof["fused_ms"] / prof["fused_launches"]
         traffic_key = (f"k_fused_cols{steps_per_launch}/{work.name}" if args.fusion in (1, 2)
-                       else f"k_fused_rows{steps_per_launch}/{work.name}")
+                       else f"{FUSION_TRAFFIC_FAMILY.get(args.fusion, 'k_fused_rows')}{steps_per_launch}/{work.name}")
+        bytes_per_launch = 4.0 * elem * info.n_sites * S + diag_bytes
+        bytes_model = ("fused K-step pass: 4 state-block crossings per launch (read phi_{n-1}, phi_n; write "
+                       "phi_{n+K-1}, phi_{n+K}) of N x S x 8 B" + (" + D_i 4 B per site" if diag_bytes else ""))
     else:
         steps_per_launch = 1
         kname = (f"k_moment_stencil<{wl.KIND_NAMES[spec.kind]}, "
@@ -400,25 +437,32 @@ def run_gpu(args, work):
                     "complex64 x1 per thread>" if prec == capi.C64 else "complex128>"))
         per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
         traffic_key = f"k_moment_stencil/{work.name}"
-    bytes_per_launch = per_site_step * steps_per_launch
+        bytes_per_launch = per_site_step
+        bytes_model = "one-step pass: 24 B per site-update (complex64) + D_i 4 B per site"
+    unfused_equiv = per_site_step * steps_per_launch
     achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
     peak, peak_kind = measured_hbm_peak()
     traffic = kernel_traffic(traffic_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_kind, "kernel": kname,
-                "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
-                "recurrence_algorithmic_gbs": total_alg / (prof["recurrence_ms"] / 1e3) / 1e9,
-                "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
+                "algorithmic_bytes_per_launch": bytes_per_launch, "bytes_model": bytes_model,
+                "avg_launch_us": per_launch_ms * 1e3,
+                "site_updates_per_launch": steps_per_launch * info.n_sites * S,
+                "frac_unfused_equiv": unfused_equiv / (per_launch_ms / 1e3) / 1e9 / peak,
+                "timing": f"CUDA events around the moment passes on the library stream, separate profiled pass "
+                          f"of {prof_steps} step(s) after the timed region",
+                "recurrence_share_of_step": prof["recurrence_ms"] / prof_ms}
     if traffic:
         roofline["dram_gbs"] = traffic / (per_launch_ms / 1e3) / 1e9
         roofline["dram_frac"] = roofline["dram_gbs"] / peak
+        roofline["traffic_over_algorithmic"] = traffic / bytes_per_launch
 
-    recon_ms = prof["recon_ms"] / args.steps
+    recon_ms = prof["recon_ms"] / prof_steps
     Mp = (M + 63) // 64 * 64
     rows_pad = (nE + 127) // 128 * 128
     NP = 16 if 3 * S <= 16 else (32 if 3 * S <= 32 else 48)
     mma_flops = 2.0 * rows_pad * 3 * Mp * NP * (1 if S <= 16 else 2)
-    recon = {"ms_per_step": recon_ms, "launches_per_step": prof["recon_launches"] / args.steps,
+    recon = {"ms_per_step": recon_ms, "launches_per_step": prof["recon_launches"] / prof_steps,
              "path": args.recon,
              "mma_tflops": (mma_flops / (recon_ms / 1e3) / 1e12) if args.recon == "tensor" and recon_ms > 0 else None}
     out = {
@@ -488,6 +532,15 @@ def run_gpu(args, work):
             "site_updates_per_s_sequential": seq_su / res["sequential"][0],
             "site_updates_per_s_concurrent": conc_su / res["concurrent_m"][0],
             "max_rel_dos_difference": diff}
+
+    if rank == 0 and not args.no_serving and work is wl.GRAPHENE_2048:
+        out["serving"] = serving_leg(capi, ctx, args, args.serving_requests, args.serving_budget_s)
+
+    if rank == 0 and not args.no_largest and work is wl.GRAPHENE_2048:
+        try:
+            out["largest_config"] = largest_leg(capi, ctx, args)
+        except Exception as exc:  # the headline number stands; say why this leg is missing
+            out["largest_config"] = {"workload": wl.GRAPHENE_22528.name, "failed": f"{exc!r}"[:300]}
 
     if rank == 0 and not args.no_cpu and world == 1:
         try:
@@ -713,12 +766,14 @@ def request_work(r):
     return (r.n_moments // 2) * n * r.n_states
 
 
-def run_serving(args):
+def serving_leg(capi, ctx, args, n_requests: int, budget_s: float | None = None) -> dict:
+    """The request stream of the serving configuration: Poisson arrivals of DOS / LDOS requests
+    (square, honeycomb or simple-cubic lattices, 2^12..2^log2_max sites, W ~ U[0,2]t, M ~ U{256..8192},
+    S ~ U{1..16} or LDOS at 32 sites) at `--load` x the capacity measured by a closed-loop probe,
+    served by one server (continuous batching into the persistent kernel).  With a time budget the
+    stream is cut to the first requests whose work fits it at that rate (stated in the result)."""
     import threading
-    from paper_2510_17432_gb300 import capi
 
-    rank, world, local = dist_env()
-    ctx = capi.tbpm_create(local)
     E = wl.uniform_energy_grid(1024, -8.2, 8.2)
     recon = capi.RECON_TENSOR if args.recon == "tensor" else capi.RECON_FP64
 
@@ -741,10 +796,19 @@ def run_serving(args):
     cap_su = sum(request_work(r) for r in probe) / (time.perf_counter() - t0)
     capi.tbpm_server_destroy(srv)
 
-    base = wl.serving_stream(args.requests, 1.0, log2_max=args.log2_max_sites)
-    mean_work = sum(request_work(r) for r in base) / len(base)
+    full = wl.serving_stream(n_requests, 1.0, log2_max=args.log2_max_sites)
+    mean_work = sum(request_work(r) for r in full) / len(full)
     rate = args.load * cap_su / mean_work
-    stream = wl.serving_stream(args.requests, rate, log2_max=args.log2_max_sites)
+    stream = wl.serving_stream(n_requests, rate, log2_max=args.log2_max_sites)
+    cut = len(stream)
+    if budget_s:
+        work = 0.0
+        for i, r in enumerate(stream):
+            work += request_work(r)
+            if max(r.arrival_s, work / (args.load * cap_su)) > budget_s:
+                cut = max(16, i)
+                break
+    stream = stream[:cut]
     srv = capi.tbpm_server_create(ctx, recon=recon)
     tickets = [None] * len(stream)
     start = time.perf_counter()
@@ -768,19 +832,84 @@ def run_serving(args):
     makespan = time.perf_counter() - start
     stats = capi.tbpm_server_stats(srv)
     capi.tbpm_server_destroy(srv)
-    capi.tbpm_destroy(ctx)
     lat = np.array(lat)
     total_su = sum(request_work(r) for r in stream)
-    print(json.dumps({
-        "metric": "serving latency (submit to DOS on host) and throughput", "requests": len(stream),
+    sizes = [r.lattice.n_full for r in stream]
+    return {
+        "requests": len(stream), "requests_planned": n_requests,
+        "cut": (None if cut == n_requests else
+                f"first {cut} of the {n_requests} arrivals: their work at {args.load} x capacity fills the "
+                f"{budget_s:.0f} s time budget of this leg; same distribution, same arrival process"),
         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
         "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "latency": "submit to DOS copied into the caller's host buffer",
         "throughput_site_updates_per_s": total_su / makespan, "makespan_s": makespan,
         "arrival_rate_per_s": rate, "load": args.load, "capacity_site_updates_per_s": cap_su,
-        "kernel_launches": stats["launches"], "batched_kernel_gpu_s": stats["gpu_us"] / 1e6, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"serving stream: {len(stream)} Poisson arrivals, square/honeycomb/cubic, "
-                               f"2^12..2^{args.log2_max_sites} sites, W~U[0,2]t, M~U{{256..8192}}, "
-                               "S~U{1..16} or LDOS at 32 sites", "reconstruction": args.recon}}))
+        "sites_min": int(min(sizes)), "sites_max": int(max(sizes)),
+        "kernel_launches": stats["launches"], "batched_kernel_gpu_s": stats["gpu_us"] / 1e6,
+        "workload": f"Poisson arrivals, square/honeycomb/cubic, 2^12..2^{args.log2_max_sites} sites, W~U[0,2]t, "
+                    "M~U{256..8192}, S~U{1..16} or LDOS at 32 sites, complex64, Jackson DOS on 1024 energies",
+        "reconstruction": args.recon}
+
+
+def run_serving(args):
+    from paper_2510_17432_gb300 import capi
+
+    rank, world, local = dist_env()
+    ctx = capi.tbpm_create(local)
+    res = serving_leg(capi, ctx, args, args.requests)
+    capi.tbpm_destroy(ctx)
+    print(json.dumps({"metric": "serving latency (submit to DOS on host) and throughput", "n_gpus": 1,
+                      "dtype": "f32", "data": "synthetic", **res}))
+
+
+def largest_leg(capi, ctx, args) -> dict:
+    """The 1.015e9-site honeycomb (22528 x 22528 cells, V in [-0.5, 0.5] eV, 4 complex64 states,
+    8192 moments, Jackson DOS on 8192 energies): one timed spectrum through tbpm_dos_device after
+    a short warm-up request on the same lattice."""
+    import torch
+
+    work = wl.GRAPHENE_22528
+    spec = work.lattice
+    desc = capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, seed=spec.seed, pbc=spec.pbc, path=spec.path)
+    t0 = time.perf_counter()
+    lat = capi.tbpm_lattice_create(ctx, desc)
+    capi.tbpm_sync(ctx)
+    build_s = time.perf_counter() - t0
+    info = capi.tbpm_lattice_info(lat)
+    S, M, nE = work.n_states, work.n_moments, 8192
+    E = wl.uniform_energy_grid(nE, info.H0 - info.half_width, info.H0 + info.half_width)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_E = torch.tensor(E, device=dev, dtype=torch.float64)
+    d_D = torch.empty((S, nE), device=dev, dtype=torch.float64)
+    recon = capi.RECON_TENSOR if args.recon == "tensor" else capi.RECON_FP64
+    warm = capi.request(n_states=S, precision=work.precision, n_moments=64, state_seed=1,
+                        dos_method=capi.DOS_JACKSON, recon=recon)
+    capi.tbpm_dos_device(ctx, lat, warm, d_E, nE, d_D)
+    req = capi.request(n_states=S, precision=work.precision, n_moments=M, state_seed=1,
+                       dos_method=capi.DOS_JACKSON, recon=recon)
+    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
+    capi.tbpm_sync(ctx)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = capi.tbpm_launch_count(ctx)
+    e0.record(stream)
+    capi.tbpm_dos_device(ctx, lat, req, d_E, nE, d_D)
+    e1.record(stream)
+    capi.tbpm_sync(ctx)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sec = e0.elapsed_time(e1) / 1e3
+    D = d_D.cpu().numpy()
+    capi.tbpm_lattice_destroy(lat)
+    su = (M // 2) * info.n_sites * S
+    return {"workload": work.name, "sites": info.n_sites, "states": S, "moments": M, "energies": nE,
+            "steps": 1, "warmup": "one 64-moment request on the same lattice",
+            "seconds_per_spectrum": sec, "site_updates_per_s": su / sec, "launches": capi.tbpm_launch_count(ctx) - l0,
+            "lattice_build_s": build_s, "finite": bool(np.all(np.isfinite(D))), "clocks": clk,
+            "timing": "CUDA events on the library stream around one tbpm_dos_device call (graphs on)"}
 
 
 def dense_desc(capi, spec):

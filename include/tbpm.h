@@ -324,7 +324,8 @@ int tbpm_server_stats(tbpm_server* srv, int64_t out[7]);
  * which every GPU that loads the library holds until the process exits.
  *
  * Matrix-free stencil lattices only (no vacancies).  Arguments:
- *   kind, L[3], pbc[3]  lattice as in tbpm_lattice_desc (L[2] ignored unless cubic)
+ *   kind, L, pbc        lattice as in tbpm_lattice_desc; L[2] and pbc[2] are read only for
+ *                       the cubic lattice, so 2-D callers may pass two-entry arrays
  *   t_scaled            t / |H|
  *   d_diag              device [N] rescaled on-site terms (V_i - H0)/|H| (float for C64,
  *                       double for C128), or NULL to use diag_const for every site

@@ -995,7 +995,7 @@ extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int3
   }
   g.pbc_x = pbc[0] != 0;
   g.pbc_y = pbc[1] != 0;
-  g.pbc_z = pbc[2] != 0;
+  g.pbc_z = kind == TBPM_CUBIC ? pbc[2] != 0 : 1;  // a 2-D caller may pass a two-entry pbc array
   g.z = kind == TBPM_SQUARE ? 4 : kind == TBPM_HONEYCOMB ? 3 : 6;
   g.row_sites = kind == TBPM_HONEYCOMB ? 2 * g.Lx : g.Lx;
   g.n_rows = g.Ly * g.Lz;

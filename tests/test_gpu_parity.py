@@ -362,3 +362,46 @@ def test_graph_replay_is_bit_identical(capi, ctx, spec, S, prec):
     for o in outs:
         assert np.array_equal(o, ref)
     capi.tbpm_lattice_destroy(lat)
+
+
+# ---------------------------------------------------------------- headline moment counts, every moment
+
+_ORACLE_CACHE = {}
+
+
+def oracle_moments_cached(key, ol, seed, s, M):
+    """Oracle moments of state s (plain definition), kept across the fusion modes of one case."""
+    k = (key, seed, s, M)
+    if k not in _ORACLE_CACHE:
+        psi = oprop.random_phase_states(ol, seed, s + 1)[s]
+        _ORACLE_CACHE[k] = oprop.moments(ol, psi, psi, M)
+    return _ORACLE_CACHE[k]
+
+
+HEADLINE_CASES = [
+    # the benchmark's state block and moment count on a lattice wide and tall enough for many
+    # bands and row segments of the fused sweep (2047 fused steps)
+    ("honey512x384_S8_M4096", dict(kind=1, L=(512, 384), t=-2.7, W=0.0), 8, 4096, (0, 7)),
+    # the 1e9-site workload's state block, moment count and disorder (4095 steps)
+    ("honey200x150_W1_S4_M8192", dict(kind=1, L=(200, 150), t=-2.7, W=1.0), 4, 8192, (0, 3)),
+]
+
+
+@pytest.mark.parametrize("mode", [0, 5])
+@pytest.mark.parametrize("name,spec,S,M,check", HEADLINE_CASES, ids=[c[0] for c in HEADLINE_CASES])
+def test_headline_moment_counts_match_oracle(capi, ctx, name, spec, S, M, check, mode):
+    """Every one of the M moments of two states at the benchmark's M = 4096 (S = 8) and the
+    1e9-site workload's M = 8192 (S = 4), complex64 states with FP64 reductions, through the
+    one-step pass (mode 0) and the default four-step fused pass (mode 5): max_n |dmu_n| / |mu_0|
+    <= 1e-5 against the oracle's plain FP64 moments."""
+    lat, ol = make(capi, ctx, **spec)
+    capi.tbpm_set_fusion(ctx, mode)
+    try:
+        mu = gpu_moments(capi, ctx, lat, S, M, 0, seed=2)
+    finally:
+        capi.tbpm_set_fusion(ctx, 5)
+    capi.tbpm_lattice_destroy(lat)
+    for s in check:
+        ref = oracle_moments_cached(name, ol, 2, s, M)
+        err = np.max(np.abs(mu[s] - ref)) / abs(ref[0])
+        assert err <= 1e-5, (s, err)

@@ -10,6 +10,8 @@ import time
 import numpy as np
 import pytest
 
+from oracle import lattice as olat, propagate as oprop, spectra as ospec
+
 pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-5, 1: 1e-11}
@@ -71,6 +73,44 @@ def test_served_results_match_direct_api(capi, ctx):
             ref = direct_dos(capi, ctx, ld, rk, E)
             err = np.max(np.abs(D - ref)) / np.max(np.abs(ref))
             assert err <= TOL[rk["precision"]], (name, err)
+    finally:
+        capi.tbpm_server_destroy(srv)
+
+
+def oracle_dos(lk, rk, E):
+    """The oracle's Jackson DOS of the oracle's moments for one served request."""
+    lk = dict(lk)
+    kind, L = lk.pop("kind"), tuple(lk.pop("L"))
+    ol = olat.build_lattice(kind, L + (1,) * (3 - len(L)), t=lk.get("t", 1.0), W=lk.get("W", 0.0),
+                            vacancy_frac=lk.get("vacancy_frac", 0.0), seed=lk.get("seed", 0))
+    if "sites" in rk:
+        psi = oprop.site_states(ol, rk["sites"])
+    else:
+        psi = oprop.random_phase_states(ol, rk.get("state_seed", 1), rk["n_states"])
+    M = rk["n_moments"]
+    return np.stack([ospec.dos_jackson(oprop.moments(ol, p, p, M), E, ol.H0, ol.half_width) for p in psi])
+
+
+@pytest.mark.parametrize("recon", ["fp64", "tensor"])
+def test_served_results_match_oracle(capi, ctx, recon):
+    """Every served DOS (square, honeycomb, cubic, vacancies, LDOS, complex64 and complex128, 1 to
+    16 states) against the oracle's Jackson DOS of the oracle's moments: max_E |dD| / max_E D <=
+    1e-5 for complex64, 1e-11 for complex128 with the FP64 reconstruction (1e-5 through the
+    bf16 x3 tensor-core reconstruction)."""
+    E = energies()
+    srv = capi.tbpm_server_create(ctx, recon=capi.RECON_TENSOR if recon == "tensor" else capi.RECON_FP64)
+    try:
+        tickets = [(name, lk, rk, capi.tbpm_submit(srv, capi.lattice_desc(**lk), capi.request(**rk), E))
+                   for name, lk, rk in CASES]
+        for name, lk, rk, t in tickets:
+            S = len(rk["sites"]) if "sites" in rk else rk["n_states"]
+            D = np.zeros((S, E.size))
+            capi.tbpm_wait(srv, t, D)
+            ref = oracle_dos(lk, rk, E)
+            tol = TOL[rk["precision"]] if recon == "fp64" else 1e-5
+            for s in range(S):
+                err = np.max(np.abs(D[s] - ref[s])) / np.max(np.abs(ref[s]))
+                assert err <= tol, (name, s, err)
     finally:
         capi.tbpm_server_destroy(srv)
 

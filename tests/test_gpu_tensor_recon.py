@@ -58,3 +58,27 @@ def test_tensor_reconstruction_matches_oracle(capi, ctx):
         ref = ospec.dos_jackson(mu, E, ol.H0, ol.half_width)
         assert np.max(np.abs(Dt[s] - ref)) / np.max(ref) <= 1e-5
     capi.tbpm_lattice_destroy(lat)
+
+
+def test_tensor_reconstruction_at_benchmark_shape(capi, ctx):
+    """The benchmark's reconstruction shape: M = 4096 moments, 8192 midpoint energies over the
+    band, 8 states.  The bf16 x3 split error grows with M, so this is the size that matters:
+    against the FP64 reconstruction of the same moments at every energy, and against the
+    oracle's Jackson DOS of the oracle's moments (complex128 moments, so that only the
+    reconstruction differs) on every 16th energy."""
+    L, S, M, nE = (48, 40), 8, 4096, 8192
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(1, L, t=-2.7, W=1.0, seed=0x7B1A5))
+    ol = olat.build_lattice(1, L + (1,), t=-2.7, W=1.0, seed=0x7B1A5)
+    k = np.arange(nE)
+    E = ol.H0 + ol.half_width * (-1.0 + (2.0 * k + 1.0) / nE)
+    Dt = dos(capi, ctx, lat, S, M, E, capi.RECON_TENSOR, prec=1)
+    Df = dos(capi, ctx, lat, S, M, E, capi.RECON_FP64, prec=1)
+    capi.tbpm_lattice_destroy(lat)
+    for s in range(S):
+        assert np.max(np.abs(Dt[s] - Df[s])) / np.max(np.abs(Df[s])) <= 1e-5, s
+    psi = oprop.random_phase_states(ol, 9, S)
+    sub = E[::16]
+    for s in (0, S - 1):
+        mu = oprop.moments(ol, psi[s], psi[s], M)
+        ref = ospec.dos_jackson(mu, sub, ol.H0, ol.half_width)
+        assert np.max(np.abs(Dt[s, ::16] - ref)) / np.max(ref) <= 1e-5, s
