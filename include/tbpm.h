@@ -157,7 +157,9 @@ int tbpm_destroy(tbpm_ctx* ctx);
 const char* tbpm_last_error(void);
 /* The context's cudaStream_t, returned as void*, for event timing by the caller. */
 void* tbpm_stream(tbpm_ctx* ctx);
-/* Block until all work enqueued on the context's stream has finished. */
+/* Block until all work enqueued on the context's stream has finished.  Returns TBPM_ETIMEOUT
+ * (once) when a bounded device wait of a fused moment pass expired since the last check; the
+ * synchronous tbpm_moments and tbpm_dos report it the same way. */
 int tbpm_sync(tbpm_ctx* ctx);
 /* Number of kernels the library has launched on this context since creation. */
 int64_t tbpm_launch_count(const tbpm_ctx* ctx);
@@ -168,9 +170,13 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
  * 3, 4 = 2 steps per pass by a row sweep (bands of cells, rows of phi_n streamed through a
  * shared-memory ring one row ahead, each further step one row behind the previous; 128- and
  * 256-thread CTAs); 5, 6 = the row sweep with 4 steps per pass (128- and 256-thread CTAs);
- * 7 = the 2-step sweep in the same code as 5 and 6.  Default 5, the fastest measured on GB300
- * (honeycomb 2048 x 2048, 8 states: 1.87x the one-step pass).  Results of different modes agree
- * within the complex64 tolerance, not bit for bit; each mode is deterministic. */
+ * 7 = the 2-step sweep in the same code as 5 and 6; 8, 9, 10 = 4 steps per pass by a
+ * register-resident sweep (each thread keeps the recurrence levels of its cell in registers and
+ * exchanges only the x-neighbours through shared memory, one barrier per row; rows of phi_n and
+ * phi_{n-1} arrive by TMA bulk copies; 128-, 192- and 256-thread CTAs; a lattice narrower than
+ * one band takes mode 5).  Default 5.  -1 = the fastest of modes 0, 4, 5 and 8 timed on the
+ * request's lattice shape.  Results of different modes agree within the complex64 tolerance, not
+ * bit for bit; each mode is deterministic.  Modes outside -1..10 are rejected with TBPM_EINVAL. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
 /* mode -1 = autotuned: the first moment request on a lattice shape (kind, sizes, boundaries,
  * path, padded S, precision, disorder) with at least 128 moments times 24 steps of each of modes

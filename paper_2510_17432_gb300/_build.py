@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtbpm.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "cheb.cu", "conduct.cu", "fused.cu", "recon.cu", "recon_tc.cu", "response.cu", "serve.cu",
-           "taps.cu"]
+           "sweep.cu", "taps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                 "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

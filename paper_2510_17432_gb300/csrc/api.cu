@@ -422,6 +422,7 @@ int tbpm_create(tbpm_ctx** out, int device) {
     return TBPM_ECUDA;
   }
   ctx->pinned_cap = 4096;
+  memset(ctx->pinned, 0, ctx->pinned_cap);
   *out = ctx;
   return TBPM_OK;
 }
@@ -459,7 +460,7 @@ int tbpm_sync(tbpm_ctx* ctx) {
     return TBPM_EINVAL;
   }
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+  return sweep_status(ctx);  // a fused sweep's bounded wait that expired since the last check
 }
 
 int64_t tbpm_launch_count(const tbpm_ctx* ctx) { return ctx ? ctx->launches : -1; }
@@ -470,8 +471,8 @@ int tbpm_set_fusion(tbpm_ctx* ctx, int enable) {
     set_error("tbpm_set_fusion: ctx is NULL");
     return TBPM_EINVAL;
   }
-  if (enable < -1 || enable > 7) {
-    set_error("tbpm_set_fusion: mode %d unknown (-1..7)", enable);
+  if (enable < -1 || enable > 10) {
+    set_error("tbpm_set_fusion: mode %d unknown (-1..10)", enable);
     return TBPM_EINVAL;
   }
   ctx->fusion = enable;
@@ -1146,7 +1147,7 @@ int choose_fusion(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, con
   cudaEvent_t e0, e1;
   TBPM_CK(cudaEventCreate(&e0));
   TBPM_CK(cudaEventCreate(&e1));
-  const int modes[] = {0, 4, 5};
+  const int modes[] = {0, 4, 5, 8};
   double best_ms = 1e300;
   ctx->fusion_timings.clear();
   // 24 steps per mode after 8 warm-up steps (multiples of every mode's steps per pass)
@@ -2177,7 +2178,7 @@ int tbpm_moments(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* r
   TBPM_TRY(run_moments(ctx, lat, req, pl, M, (double*)ctx->ws_mu.p));
   TBPM_TRY(copy_rows(ctx, mu, (double*)ctx->ws_mu.p, pl.S, 2 * (size_t)M, cudaMemcpyDeviceToHost));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+  return sweep_status(ctx);
 }
 
 int tbpm_correlation_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_C) {
@@ -2255,7 +2256,7 @@ int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, 
   TBPM_TRY(run_dos(ctx, lat, req, pl, dE, nE, dD));
   TBPM_CK(cudaMemcpyAsync(D, dD, sizeof(double) * nE * pl.S, cudaMemcpyDeviceToHost, ctx->stream));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
-  return TBPM_OK;
+  return sweep_status(ctx);
 }
 
 // Adjacency operator y_i = sum_{j in nbr(i)} x_j through the hot-path recurrence kernel

@@ -943,7 +943,7 @@ bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad) {
          g.Lx >= fused::V1::WX && g.Ly >= fused::V1::WY;
 }
 
-int fused_steps(int variant) { return (variant == 1 || variant == 5 || variant == 6) ? 4 : 2; }
+int fused_steps(int variant) { return (variant == 1 || (variant >= 5 && variant != 7)) ? 4 : 2; }
 
 template <class C, bool D, bool O>
 static cudaError_t set_smem_attr() {
@@ -1004,6 +1004,13 @@ static int launch_variant(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurren
 // One fused pass: steps step0 .. step0+K-1 from (prev_in, cur_in) into (prev_out, cur_out).
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant) {
+  if (variant >= 8 && variant <= 10) {
+    // the register sweep copies whole band rows; a lattice narrower than a band takes mode 5
+    const int band = (variant == 8 ? 128 : variant == 9 ? 192 : 256) / (ra.S / 2);
+    if (lat->geom.Lx >= band)
+      return launch_sweep_pass(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0, variant);
+    variant = 5;
+  }
   if (variant == 5) return launch_rowsK<128, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 6) return launch_rowsK<256, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
   if (variant == 7) return launch_rowsK<256, 2>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);

@@ -1,0 +1,553 @@
+// Register-resident row sweep: K Chebyshev steps per pass over HBM on the honeycomb stencil,
+// complex64 state pairs, with the moment inner products of every step fused in.
+//
+// The recurrence phi_{n+1} = 2 H~ phi_n - phi_{n-1} (App. B) on the honeycomb couples
+//   A(x,y) <- B(x,y), B(x-1,y), B(x,y-1)        B(x,y) <- A(x,y), A(x+1,y), A(x,y+1)
+// so a thread that owns one cell (both sites) and one state pair finds every neighbour in its
+// own registers except B(x-1,y) and A(x+1,y), which belong to the threads of the adjacent cells
+// of the same row.  A CTA owns a band of CW cells (K/2 halo cells on each side) and a segment of
+// rows (K/2 halo rows below and above) and sweeps it upwards as a wavefront: at sweep position r
+// level L = 1..K forms phi_{n+L} at row r - (L-1) from
+//   * level L-1 at rows r-L, r-L+1, r-L+2 of the same cell: registers (the thread formed them in
+//     this and the two previous positions),
+//   * level L-1 at row r-L+1 of the adjacent cells: a shared-memory exchange row written in the
+//     previous position (double-buffered, so one barrier per position suffices),
+//   * level L-2 at row r-L+1 of the same cell: registers.
+// Level 0 (phi_n) and phi_{n-1} arrive row by row through 1-D TMA bulk copies (cp.async.bulk,
+// one elected thread, an mbarrier per ring slot) into a ring NSLOT rows deep; a band row is
+// contiguous in the [N][S] layout, so one copy per state block (two where a periodic band wraps).
+// Levels K-1 and K go to HBM, so per K steps each state block crosses HBM four times: read
+// phi_{n-1}, phi_n, write phi_{n+K-1}, phi_{n+K}.
+//
+// Moments (cost halving of Eq. cheby_prod): for every level, <phi_{n+L-1}|phi_{n+L-1}> and
+// <phi_{n+L}|phi_{n+L-1}> over the segment's interior, summed in FP32 over at most 32 units per
+// thread, then FP32 lane trees per state pair, FP64 warp slots, FP64 block partials and a
+// fixed-order FP64 sum by the last CTA: deterministic for a given launch shape.
+//
+// Every mbarrier wait is bounded by a wall-clock budget; on expiry the CTA records an error code
+// in the caller's status word, stops sweeping, waits (bounded) for its copies in flight and still
+// takes part in the grid reduction so that the completion counter stays consistent.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "tbpm_internal.cuh"
+
+namespace tbpm {
+namespace sweep {
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per mbarrier wait
+
+template <int NT_, int K_, int NSLOT_>
+struct Cfg {
+  static constexpr int NT = NT_, K = K_, H = K_ / 2, NSLOT = NSLOT_;
+  static constexpr int NV = 6 * K;     // per level: {|a|^2, Re<n|a>, Im<n|a>} x 2 states
+  static constexpr int FOLD = 16;      // positions per FP32 partial (32 unit terms per thread)
+  static constexpr int MINB = NT <= 128 ? 3 : NT <= 192 ? 2 : 1;
+  static constexpr int BAR_BYTES = ((NSLOT * 8 + 15) / 16) * 16;
+  // ring slot: [P zero][phi_n row: 2 NT units][P zero][phi_{n-1} row: 2 NT units]
+  static int slot_units(int P) { return 4 * NT + 2 * P; }
+  // exchange row: [A plane: NT units][P zero][B plane: NT units]
+  static int xrow_units(int P) { return 2 * NT + P; }
+  static size_t smem(int P) {
+    return (size_t)BAR_BYTES + 16 * ((size_t)NSLOT * slot_units(P) + (size_t)2 * (K - 1) * xrow_units(P)) +
+           8 * (size_t)(NT / 32) * P * NV;
+  }
+};
+
+struct Args {
+  const float4* prev_in;  // phi_{n-1}
+  const float4* cur_in;   // phi_n
+  float4* prev_out;       // phi_{n+K-1}
+  float4* cur_out;        // phi_{n+K}
+  const float* diag;      // rescaled D_i or null
+  float dc2, th2;         // 2 D (clean lattice), 2 t/|H|
+  int64_t Lx, Ly;
+  int pbc_x, pbc_y;
+  int P, logP, S;
+  int CW, BX, SY;         // band cells, interior cells, rows per segment
+  int nbx, nsy;
+  double* partials;       // [grid][P][NV]
+  unsigned* counter;
+  double* mu;
+  int M;
+  int step0;
+  int* status;            // host-visible status word: nonzero = a bounded wait expired
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (!mbar_try(bar, parity))
+    if (globaltimer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+// 1-D bulk copy global -> shared, completion counted in bytes on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// d own + th (n1 + n2 + n3) - pv for one complex64 pair
+__device__ __forceinline__ float4 level_update(float d, float4 own, float th, float4 n1, float4 n2, float4 n3,
+                                               float4 pv) {
+  float4 r;
+  r.x = fmaf(d, own.x, fmaf(th, (n1.x + n2.x) + n3.x, -pv.x));
+  r.y = fmaf(d, own.y, fmaf(th, (n1.y + n2.y) + n3.y, -pv.y));
+  r.z = fmaf(d, own.z, fmaf(th, (n1.z + n2.z) + n3.z, -pv.z));
+  r.w = fmaf(d, own.w, fmaf(th, (n1.w + n2.w) + n3.w, -pv.w));
+  return r;
+}
+
+// acc[0..5] += {|a|^2, Re<n|a>, Im... } for the two states of a pair: <phi_j|phi_j> and
+// <phi_{j+1}|phi_j> with a = phi_j, n = phi_{j+1} (the bra is conjugated)
+__device__ __forceinline__ void moment_terms(float* acc, float4 a, float4 n) {
+  acc[0] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0]));
+  acc[1] = fmaf(n.x, a.x, fmaf(n.y, a.y, acc[1]));
+  acc[2] = fmaf(n.x, a.y, fmaf(-n.y, a.x, acc[2]));
+  acc[3] = fmaf(a.z, a.z, fmaf(a.w, a.w, acc[3]));
+  acc[4] = fmaf(n.z, a.z, fmaf(n.w, a.w, acc[4]));
+  acc[5] = fmaf(n.z, a.w, fmaf(-n.w, a.z, acc[5]));
+}
+
+template <int NT_, int K_, int NSLOT_, bool HAS_DIAG, bool OPEN>
+__global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_moments(Args a) {
+  using C = Cfg<NT_, K_, NSLOT_>;
+  constexpr int NT = C::NT, K = C::K, H = C::H, NSLOT = C::NSLOT, NV = C::NV;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned ticket;
+  const int P = a.P, logP = a.logP, CW = a.CW;
+  const int SU = 4 * NT + 2 * P, XU = 2 * NT + P;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
+  float4* ring = reinterpret_cast<float4*>(smraw + C::BAR_BYTES);  // [NSLOT][SU]
+  float4* xb = ring + NSLOT * SU;                                   // [K-1][2][XU]
+  double* red = reinterpret_cast<double*>(xb + 2 * (K - 1) * XU);   // [warps][P][NV]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  for (int i = tid; i < NSLOT * SU + 2 * (K - 1) * XU; i += NT) ring[i] = zero;
+  for (int i = tid; i < (NT / 32) * P * NV; i += NT) red[i] = 0.0;
+  if (tid == 0) {
+    for (int s = 0; s < NSLOT; ++s) mbar_init(smem_u32(bars + s), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // the zero pads written through the generic proxy must be ordered before the bulk copies
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+
+  const int bx = blockIdx.x % a.nbx, sy = blockIdx.x / a.nbx;
+  const int64_t x0 = (int64_t)bx * a.BX;
+  const int64_t ys = (int64_t)sy * a.SY;
+  const int64_t ye = ys + a.SY < a.Ly ? ys + a.SY : a.Ly;
+  const int64_t r0 = ys - H;          // first sweep position = first level-0 row
+  const int64_t rlast = ye + H - 1;   // last level-0 row any exact value needs
+  const int64_t r_end = ye + K - 2;   // level K reaches row ye - 1 here
+  const int64_t row_units = 2 * a.Lx * P;
+
+  // this thread's cell and pair
+  const int c = tid >> logP, p = tid & (P - 1);
+  int64_t x = x0 - H + c;
+  bool ghx = false;
+  if (x < 0 || x >= a.Lx) {
+    if (OPEN && !a.pbc_x) ghx = true;
+    else x = ((x % a.Lx) + a.Lx) % a.Lx;
+  }
+  const bool intx = c >= H && c < CW - H && x0 + c - H < a.Lx;
+  const int64_t colA = 2 * x * P + p;
+  const int uA = 2 * (c << logP) + p;  // unit of A(c, pair p) in a ring row; B is + P
+  const int wA = tid, wB = NT + P + tid;
+
+  // row index in the lattice, or -1 outside it (open y) or beyond the rows that are needed
+  auto grow = [&](int64_t r) -> int64_t {
+    if (r > rlast) return -1;
+    if (r >= 0 && r < a.Ly) return r;
+    if (OPEN && !a.pbc_y) return -1;
+    return ((r % a.Ly) + a.Ly) % a.Ly;
+  };
+
+  // producer (thread 0): level-0 row j of both state blocks into its ring slot
+  auto issue = [&](int64_t j) {
+    const int slot = (int)((j - r0) % NSLOT);
+    const uint32_t bar = smem_u32(bars + slot);
+    const int64_t gy = grow(j);
+    if (gy < 0) {
+      mbar_arrive(bar);
+      return;
+    }
+    // pieces of the band [x0 - H, x0 - H + CW) that lie in the lattice (wrapping when periodic)
+    int cs[4], ns[4];
+    int64_t gs[4];
+    int np = 0;
+    if (!a.pbc_x) {
+      const int64_t lo = H - x0 > 0 ? H - x0 : 0;
+      const int64_t hi = a.Lx - x0 + H < CW ? a.Lx - x0 + H : CW;
+      if (lo < hi) {
+        cs[0] = (int)lo;
+        gs[0] = x0 - H + lo;
+        ns[0] = (int)(hi - lo);
+        np = 1;
+      }
+    } else {
+      int cc = 0;
+      while (cc < CW && np < 4) {
+        const int64_t g = (((x0 - H + cc) % a.Lx) + a.Lx) % a.Lx;
+        const int n = (int)(CW - cc < a.Lx - g ? CW - cc : a.Lx - g);
+        cs[np] = cc;
+        gs[np] = g;
+        ns[np] = n;
+        ++np;
+        cc += n;
+      }
+    }
+    uint32_t bytes = 0;
+    for (int k = 0; k < np; ++k) bytes += 2u * (uint32_t)ns[k] * 2u * (uint32_t)P * 16u;
+    mbar_arrive_tx(bar, bytes);
+    float4* sn = ring + slot * SU + P;
+    float4* sp = ring + slot * SU + 2 * NT + 2 * P;
+    for (int k = 0; k < np; ++k) {
+      const int64_t src = gy * row_units + gs[k] * 2 * P;
+      const uint32_t nb = (uint32_t)ns[k] * 2u * (uint32_t)P * 16u;
+      bulk_g2s(smem_u32(sn + cs[k] * 2 * P), a.cur_in + src, nb, bar);
+      bulk_g2s(smem_u32(sp + cs[k] * 2 * P), a.prev_in + src, nb, bar);
+    }
+  };
+  if (tid == 0)
+    for (int k = 0; k < NSLOT; ++k) issue(r0 + k);
+
+  auto diag_row = [&](int64_t r) -> float2 {
+    if (!HAS_DIAG) return make_float2(a.dc2, a.dc2);
+    const int64_t gy = grow(r);
+    if (gy < 0 || ghx) return make_float2(0.f, 0.f);
+    const float2 d = __ldg(reinterpret_cast<const float2*>(a.diag + 2 * (gy * a.Lx + x)));
+    return make_float2(2.f * d.x, 2.f * d.y);
+  };
+
+  // registers: level l = 1 .. K-1 at the rows formed in the last three positions (slot =
+  // position % 3); level 0 (phi_n) is read from the ring, which keeps row j until position j + 1
+  float4 RA[K][3], RB[K][3];
+#pragma unroll
+  for (int l = 0; l < K; ++l)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) RA[l][s] = RB[l][s] = zero;
+  float2 dh[K];  // 2 D of rows r, r-1, .., r-K+1
+#pragma unroll
+  for (int l = 0; l < K; ++l) dh[l] = make_float2(0.f, 0.f);
+  float2 dn1 = diag_row(r0), dn2 = diag_row(r0 + 1);
+  float acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  int folded = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      float t = acc[v];
+      for (int off = 16; off >= P; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+      if (lane < P) red[(warp * P + lane) * NV + v] += (double)t;
+      acc[v] = 0.f;
+    }
+  };
+  // ring row of level-0 row j (phi_n part; phi_{n-1} part at + 2 NT + P), or null when row j
+  // holds no data (outside the lattice, beyond the needed rows, before the segment's first row)
+  auto ring_row = [&](int64_t j) -> const float4* {
+    if (j < r0 || grow(j) < 0) return nullptr;
+    return ring + (int)((j - r0) % NSLOT) * SU + P;
+  };
+  auto ld = [&](const float4* row, int u) -> float4 { return row ? row[u] : zero; };
+
+  bool timed_out = !mbar_wait(smem_u32(bars + 0), 0);  // this thread's waits; OR-reduced per position
+  const float th = a.th2;
+  bool aborted = false;
+  int64_t r_done = r0 - 1;  // last position completed
+
+  for (int64_t rb = r0; rb <= r_end && !aborted; rb += 3) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int64_t r = rb + u;
+      if (r > r_end || aborted) break;
+      const int s0 = u, s1 = (u + 2) % 3, s2 = (u + 1) % 3;  // ages 0, 1, 2
+      {  // level-0 row r+1 must have landed
+        const int64_t j = r + 1;
+        const int slot = (int)((j - r0) % NSLOT);
+        const uint32_t par = (uint32_t)(((j - r0) / NSLOT) & 1);
+        if (!mbar_wait(smem_u32(bars + slot), par)) timed_out = true;
+      }
+      const float4* Rm = ring_row(r - 1);
+      const float4* R0 = ring_row(r);
+      const float4* Rp = ring_row(r + 1);
+#pragma unroll
+      for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
+      dh[0] = dn1;
+      dn1 = dn2;
+      dn2 = diag_row(r + 2);
+#pragma unroll
+      for (int L = 1; L <= K; ++L) {
+        const int64_t q = r - (L - 1);
+        const bool ghost = OPEN && (ghx || grow(q) < 0);
+        float4 ownA, ownB, bxm, axp, bym, ayp, pvA, pvB;
+        if (L == 1) {
+          ownA = ld(R0, uA);
+          ownB = ld(R0, uA + P);
+          bxm = ld(R0, uA - P);
+          axp = ld(R0, uA + 2 * P);
+          bym = ld(Rm, uA + P);
+          ayp = ld(Rp, uA);
+          pvA = ld(R0, 2 * NT + P + uA);
+          pvB = ld(R0, 2 * NT + P + uA + P);
+        } else {
+          const float4* Xin = xb + ((L - 2) * 2 + (int)((r - 1) & 1)) * XU;
+          ownA = RA[L - 1][s1];
+          ownB = RB[L - 1][s1];
+          bxm = Xin[wB - P];
+          axp = Xin[wA + P];
+          bym = RB[L - 1][s2];
+          ayp = RA[L - 1][s0];
+          if (L == 2) {
+            pvA = ld(Rm, uA);
+            pvB = ld(Rm, uA + P);
+          } else {
+            pvA = RA[L - 2][s2];
+            pvB = RB[L - 2][s2];
+          }
+        }
+        float4 nA = level_update(dh[L - 1].x, ownA, th, ownB, bxm, bym, pvA);
+        float4 nB = level_update(dh[L - 1].y, ownB, th, ownA, axp, ayp, pvB);
+        if (ghost) {
+          nA = zero;
+          nB = zero;
+        }
+        if (L < K) {
+          RA[L][s0] = nA;
+          RB[L][s0] = nB;
+          float4* Xout = xb + ((L - 1) * 2 + (int)(r & 1)) * XU;
+          Xout[wA] = nA;
+          Xout[wB] = nB;
+        }
+        if (intx && q >= ys && q < ye) {
+          if (L >= K - 1) {
+            float4* dst = (L == K - 1) ? a.prev_out : a.cur_out;
+            const int64_t off = q * row_units + colA;
+            __stcs(dst + off, nA);
+            __stcs(dst + off + P, nB);
+          }
+          moment_terms(acc + (L - 1) * 6, ownA, nA);
+          moment_terms(acc + (L - 1) * 6, ownB, nB);
+        }
+      }
+      if (++folded == C::FOLD) {
+        folded = 0;
+        fold();
+      }
+      // one barrier per position; it also tells every thread whether any wait expired
+      if (__syncthreads_or(timed_out ? 1 : 0)) {
+        aborted = true;
+        break;
+      }
+      r_done = r;
+      // row r-1 has been read for the last time: refill its slot with row r - 1 + NSLOT
+      if (tid == 0 && r - 1 >= r0) issue(r - 1 + NSLOT);
+    }
+  }
+  if (aborted && tid == 0) {
+    // copies in flight into this CTA's shared memory must land before it exits: rows
+    // r_done + 2 .. r_done - 1 + NSLOT were issued and never waited for (bounded waits)
+    bool err_wait = false;
+    const int64_t last_issued = r_done - 1 >= r0 ? r_done - 1 + NSLOT : r0 + NSLOT - 1;
+    for (int64_t j = r_done + 2; j <= last_issued; ++j) {
+      const int slot = (int)((j - r0) % NSLOT);
+      const uint32_t par = (uint32_t)(((j - r0) / NSLOT) & 1);
+      if (!mbar_wait(smem_u32(bars + slot), par)) err_wait = true;
+    }
+    atomicExch(a.status, err_wait ? 2 : 1);
+  }
+  fold();
+  __syncthreads();
+  for (int qv = tid; qv < P * NV; qv += NT) {  // warps in order
+    const int pp = qv / NV, v = qv - pp * NV;
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[(w * P + pp) * NV + v];
+    a.partials[(size_t)blockIdx.x * P * NV + qv] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) ticket = atomicAdd(a.counter, 1u);
+  __syncthreads();
+  if (ticket != gridDim.x - 1) return;
+  __threadfence();
+  const int nval = K * a.S * 3;
+  for (int v = warp; v < nval; v += NT / 32) {
+    const int k = v / (a.S * 3), rem = v - k * a.S * 3, s = rem / 3, comp = rem - s * 3;
+    const int pr = s >> 1, sub = s & 1;
+    const int idx = k * 6 + sub * 3 + comp;
+    double sum = 0.0;
+    for (int t = lane; t < (int)gridDim.x; t += 32) sum += __ldcg(a.partials + ((size_t)t * P + pr) * NV + idx);
+    for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) {
+      const int j = a.step0 + k;
+      double* ms = a.mu + (size_t)s * a.M * 2;
+      if (comp == 0) {
+        ms[4 * j] = 2.0 * sum - ms[0];
+        ms[4 * j + 1] = -ms[1];
+      } else if (comp == 1) {
+        ms[4 * j + 2] = 2.0 * sum - ms[2];
+      } else {
+        ms[4 * j + 3] = 2.0 * sum - ms[3];
+      }
+    }
+  }
+  if (tid == 0) *a.counter = 0u;
+}
+
+}  // namespace sweep
+
+template <int NT, int K, int NSLOT, bool D, bool O>
+static cudaError_t set_sweep_smem() {
+  return cudaFuncSetAttribute(sweep::k_sweep_moments<NT, K, NSLOT, D, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sweep::Cfg<NT, K, NSLOT>::smem(16));
+}
+
+template <int NT, int K, int NSLOT>
+static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                        const void* cur_in, void* prev_out, void* cur_out, int step0) {
+  using namespace sweep;
+  using Cf = Cfg<NT, K, NSLOT>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    cudaError_t e[4] = {set_sweep_smem<NT, K, NSLOT, false, false>(), set_sweep_smem<NT, K, NSLOT, false, true>(),
+                        set_sweep_smem<NT, K, NSLOT, true, false>(), set_sweep_smem<NT, K, NSLOT, true, true>()};
+    for (cudaError_t x : e)
+      if (x != cudaSuccess) attr = x;
+  });
+  TBPM_CK(attr);
+  if (ctx->pinned_cap < 256) {
+    set_error("context has no pinned status word");
+    return TBPM_ECUDA;
+  }
+  Args a;
+  memset(&a, 0, sizeof(a));
+  a.prev_in = (const float4*)prev_in;
+  a.cur_in = (const float4*)cur_in;
+  a.prev_out = (float4*)prev_out;
+  a.cur_out = (float4*)cur_out;
+  a.diag = (const float*)ra.diag;
+  a.dc2 = ra.dc2f;
+  a.th2 = ra.th2f;
+  a.Lx = lat->geom.Lx;
+  a.Ly = lat->geom.Ly;
+  a.pbc_x = lat->geom.pbc_x;
+  a.pbc_y = lat->geom.pbc_y;
+  a.P = ra.S / 2;
+  a.logP = 0;
+  while ((1 << a.logP) < a.P) ++a.logP;
+  a.S = ra.S;
+  a.CW = NT / a.P;
+  a.BX = a.CW - 2 * Cf::H;
+  if (a.BX < 1) {
+    set_error("fused sweep: band too narrow for %d states", a.S);
+    return TBPM_EUNSUPPORTED;
+  }
+  a.nbx = (int)((a.Lx + a.BX - 1) / a.BX);
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_moments<NT, K, NSLOT, false, false>, NT,
+                                                      Cf::smem(4)) != cudaSuccess || per_sm < 1) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  // segments per band: the count whose CTAs fill the resident slots best over whole waves, weighed
+  // by the sweep positions each segment adds (K/2 halo rows at each end, K - 1 to drain)
+  const int64_t slots = (int64_t)ctx->num_sms * per_sm;
+  const int64_t max_nsy = std::max<int64_t>(1, std::min<int64_t>(a.Ly / 4, 8 * slots / a.nbx + 1));
+  int64_t nsy = 1;
+  double best = -1.0;
+  for (int64_t k = 1; k <= max_nsy; ++k) {
+    const int64_t sy = (a.Ly + k - 1) / k;
+    const int64_t ctas = a.nbx * ((a.Ly + sy - 1) / sy);
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots) * (double)sy / (double)(sy + 2 * K);
+    if (eff > best + 1e-9) {
+      best = eff;
+      nsy = k;
+    }
+  }
+  a.SY = (int)((a.Ly + nsy - 1) / nsy);
+  a.nsy = (int)((a.Ly + a.SY - 1) / a.SY);
+  a.mu = ra.mu;
+  a.M = ra.M;
+  a.step0 = step0;
+  a.status = reinterpret_cast<int*>(ctx->pinned + kSweepStatusSlot);
+  const int64_t grid = (int64_t)a.nbx * a.nsy;
+  TBPM_TRY(ensure(ctx, ctx->ws_fused_partials, sizeof(double) * Cf::NV * (size_t)a.P * (size_t)grid));
+  a.partials = (double*)ctx->ws_fused_partials.p;
+  a.counter = ra.counter;
+  const bool open = !(a.pbc_x && a.pbc_y);
+  const dim3 gr((unsigned)grid), bl(NT);
+  const size_t sm = Cf::smem(a.P);
+  if (a.diag) {
+    if (open) k_sweep_moments<NT, K, NSLOT, true, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_sweep_moments<NT, K, NSLOT, true, false><<<gr, bl, sm, ctx->stream>>>(a);
+  } else {
+    if (open) k_sweep_moments<NT, K, NSLOT, false, true><<<gr, bl, sm, ctx->stream>>>(a);
+    else k_sweep_moments<NT, K, NSLOT, false, false><<<gr, bl, sm, ctx->stream>>>(a);
+  }
+  TBPM_CK_LAUNCH(ctx);
+  return TBPM_OK;
+}
+
+// One register-resident sweep pass: steps step0 .. step0+K-1 from (prev_in, cur_in) into
+// (prev_out, cur_out).  Variant 8: 128 threads; 9: 192 threads; 10: 256 threads (K = 4).
+int launch_sweep_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                      const void* cur_in, void* prev_out, void* cur_out, int step0, int variant) {
+  if (variant == 9) return launch_sweep<192, 4, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+  if (variant == 10) return launch_sweep<256, 4, 4>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+  return launch_sweep<128, 4, 5>(ctx, lat, ra, prev_in, cur_in, prev_out, cur_out, step0);
+}
+
+int sweep_status(tbpm_ctx* ctx) {
+  int* st = reinterpret_cast<int*>(ctx->pinned + kSweepStatusSlot);
+  const int v = *st;
+  if (v != 0) {
+    *st = 0;
+    set_error("fused sweep: a bounded wait for a row copy expired (code %d)", v);
+    return TBPM_ETIMEOUT;
+  }
+  return TBPM_OK;
+}
+
+}  // namespace tbpm

@@ -318,6 +318,12 @@ int launch_qe_coefficients_phase_only(tbpm_ctx* ctx, const double* energies, int
 
 // temporal fusion (csrc/fused.cu)
 bool fused_applicable(const tbpm_lattice* lat, int precision, int Spad);
+// register-resident sweep (variants 8-10, csrc/sweep.cu); its bounded waits report through the
+// int status word at ctx->pinned + kSweepStatusSlot (zeroed at context creation)
+constexpr int kSweepStatusSlot = 16;
+int launch_sweep_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                      const void* cur_in, void* prev_out, void* cur_out, int step0, int variant);
+int sweep_status(tbpm_ctx* ctx);  // TBPM_ETIMEOUT (and clears the word) after an expired wait
 int fused_steps(int variant);
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant);

@@ -313,7 +313,7 @@ FUSED_CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
 @pytest.mark.parametrize("name,spec,S,M", FUSED_CASES, ids=[c[0] for c in FUSED_CASES])
 def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode):
     lat, ol = make(capi, ctx, **spec)
@@ -331,8 +331,8 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
 
 
 def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
-    """Mode -1 times modes 0, 4, 5 on the request's lattice shape and uses the fastest; the moments
-    agree with the one-step pass within the complex64 tolerance."""
+    """Mode -1 times modes 0, 4, 5, 8 on the request's lattice shape and uses the fastest; the
+    moments agree with the one-step pass within the complex64 tolerance."""
     lat, ol = make(capi, ctx, kind=1, L=(256, 200), t=-2.7, W=0.5)
     capi.tbpm_set_fusion(ctx, -1)
     ma = gpu_moments(capi, ctx, lat, 8, 160, 0)
@@ -340,7 +340,7 @@ def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
     capi.tbpm_set_fusion(ctx, 0)
     m0 = gpu_moments(capi, ctx, lat, 8, 160, 0)
     capi.tbpm_set_fusion(ctx, 5)
-    assert set(rep) == {0, 4, 5} and all(v > 0 for v in rep.values())
+    assert set(rep) == {0, 4, 5, 8} and all(v > 0 for v in rep.values())
     assert np.max(np.abs(ma - m0)) <= 1e-6
     capi.tbpm_lattice_destroy(lat)
 
@@ -387,13 +387,14 @@ HEADLINE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("mode", [0, 5])
+@pytest.mark.parametrize("mode", [0, 5, 8])
 @pytest.mark.parametrize("name,spec,S,M,check", HEADLINE_CASES, ids=[c[0] for c in HEADLINE_CASES])
 def test_headline_moment_counts_match_oracle(capi, ctx, name, spec, S, M, check, mode):
     """Every one of the M moments of two states at the benchmark's M = 4096 (S = 8) and the
     1e9-site workload's M = 8192 (S = 4), complex64 states with FP64 reductions, through the
-    one-step pass (mode 0) and the default four-step fused pass (mode 5): max_n |dmu_n| / |mu_0|
-    <= 1e-5 against the oracle's plain FP64 moments."""
+    one-step pass (mode 0) and the four-step fused passes (mode 5: shared-memory level rings,
+    mode 8: register-resident sweep with TMA row copies): max_n |dmu_n| / |mu_0| <= 1e-5 against
+    the oracle's plain FP64 moments."""
     lat, ol = make(capi, ctx, **spec)
     capi.tbpm_set_fusion(ctx, mode)
     try:
