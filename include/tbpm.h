@@ -180,11 +180,11 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);
 /* mode -1 = autotuned: the first moment request on a lattice shape (kind, sizes, boundaries,
  * path, padded S, precision, disorder) with at least 128 moments times 24 steps of each of modes
- * 0, 4 and 5 on scratch buffers and keeps the fastest for that shape in the context.  Results of
- * different modes agree within the complex64 tolerance, not bit for bit.
- * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode 0..7, -1 = not
- * timed). */
-int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[8]);
+ * 0, 4, 5 and 8 on scratch buffers and keeps the fastest for that shape in the context.  Results
+ * of different modes agree within the complex64 tolerance, not bit for bit.
+ * tbpm_fusion_report: ms per step of each mode in the last autotune (index = mode 0..15, -1 = not
+ * timed); the caller's array holds 16 doubles. */
+int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[16]);
 /* CUDA graphs for the moment pass (default on): a moment request whose pass sequence (buffers,
  * lattice, sizes, fusion mode) repeats a previous one is captured into a CUDA graph on its
  * second occurrence and replayed from the third on, so a small lattice no longer pays one host

@@ -352,9 +352,9 @@ def tbpm_set_block_buffering(ctx, enable: bool):
 
 def tbpm_fusion_report(ctx) -> dict:
     """ms per step of each fusion mode timed by the last autotune (mode -> ms)."""
-    out = (C.c_double * 8)()
+    out = (C.c_double * 16)()
     _check(load().tbpm_fusion_report(ctx, out))
-    return {m: out[m] for m in range(8) if out[m] >= 0.0}
+    return {m: out[m] for m in range(16) if out[m] >= 0.0}
 
 
 def tbpm_set_pass_states(ctx, max_states: int):

@@ -505,15 +505,15 @@ int tbpm_set_graphs(tbpm_ctx* ctx, int enable) {
   return TBPM_OK;
 }
 
-int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[8]) {
+int tbpm_fusion_report(tbpm_ctx* ctx, double ms_per_step[16]) {
   clear_error();
   if (!ctx || !ms_per_step) {
     set_error("tbpm_fusion_report: invalid argument");
     return TBPM_EINVAL;
   }
-  for (int m = 0; m < 8; ++m) ms_per_step[m] = -1.0;
+  for (int m = 0; m < 16; ++m) ms_per_step[m] = -1.0;
   for (auto& t : ctx->fusion_timings)
-    if (t.first >= 0 && t.first < 8) ms_per_step[t.first] = t.second;
+    if (t.first >= 0 && t.first < 16) ms_per_step[t.first] = t.second;
   return TBPM_OK;
 }
 
