@@ -55,17 +55,21 @@ KERNEL_SRCS = {
     "k_moment_stencil": ("cheb.cu", "stencil.cuh"),
     "k_fused_cols": ("fused.cu",),
     "k_fused_rows": ("fused.cu",),
+    "k_sweep": ("sweep.cu",),
 }
 # Chebyshev steps per launch and kernel of each fusion mode of the moment pass
-FUSION_STEPS = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2}
+FUSION_STEPS = {1: 4, 2: 2, 3: 2, 4: 2, 5: 4, 6: 4, 7: 2, 8: 4, 9: 4, 10: 4}
 FUSION_KERNELS = {1: "k_fused_cols (4 Chebyshev steps per pass, 2-D tiles)",
                   2: "k_fused_cols (2 Chebyshev steps per pass, 2-D tiles)",
                   3: "k_fused_rows<128> (2 Chebyshev steps per pass, row sweep)",
                   4: "k_fused_rows<256> (2 Chebyshev steps per pass, row sweep)",
                   5: "k_fused_rowsK<128, 4> (4 Chebyshev steps per pass, row sweep)",
                   6: "k_fused_rowsK<256, 4> (4 Chebyshev steps per pass, row sweep)",
-                  7: "k_fused_rowsK<256, 2> (2 Chebyshev steps per pass, row sweep)"}
-FUSION_TRAFFIC_FAMILY = {}
+                  7: "k_fused_rowsK<256, 2> (2 Chebyshev steps per pass, row sweep)",
+                  8: "k_sweep_moments<128, 4> (4 Chebyshev steps per pass, register sweep, TMA rows)",
+                  9: "k_sweep_moments<192, 4> (4 Chebyshev steps per pass, register sweep, TMA rows)",
+                  10: "k_sweep_moments<256, 4> (4 Chebyshev steps per pass, register sweep, TMA rows)"}
+FUSION_TRAFFIC_FAMILY = {8: "k_sweep", 9: "k_sweep", 10: "k_sweep"}
 TRAFFIC = os.path.join(ROOT, "profiles", "roofline_traffic.json")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -85,7 +89,7 @@ def parse():
     p.add_argument("--fusion", type=int, default=5,
                    help="moment-pass fusion mode: 0 = one step per pass, 1 = 4-step tiles, 2 = 2-step tiles, "
                         "3/4 = 2-step row sweep, 5/6 = 4-step row sweep, 7 = 2-step sweep (K-step code), "
-                        "-1 = autotuned")
+                        "8/9/10 = 4-step register sweep (128/192/256 threads), -1 = autotuned")
     p.add_argument("--serving", action="store_true", help="serving stream: Poisson arrivals, p50/p99 latency")
     p.add_argument("--oc", action="store_true",
                    help="also time the optical conductivity on the workload's lattice (0-10 eV, 2048 frequencies)")

@@ -179,13 +179,15 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   const int64_t r_end = ye + K - 2;   // level K reaches row ye - 1 here
   const int64_t row_units = 2 * a.Lx * P;
 
-  // this thread's cell and pair
+  // this thread's cell and pair.  The band [x0 - H, x0 - H + CW) and the rows r0 .. r_end lie
+  // within one period of the lattice on either side (the host requires Lx >= CW, Ly > H), so a
+  // single wrap brings any coordinate back into it.
   const int c = tid >> logP, p = tid & (P - 1);
   int64_t x = x0 - H + c;
   bool ghx = false;
   if (x < 0 || x >= a.Lx) {
     if (OPEN && !a.pbc_x) ghx = true;
-    else x = ((x % a.Lx) + a.Lx) % a.Lx;
+    else x = x < 0 ? x + a.Lx : x - a.Lx;
   }
   const bool intx = c >= H && c < CW - H && x0 + c - H < a.Lx;
   const int64_t colA = 2 * x * P + p;
@@ -197,57 +199,57 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
     if (r > rlast) return -1;
     if (r >= 0 && r < a.Ly) return r;
     if (OPEN && !a.pbc_y) return -1;
-    return ((r % a.Ly) + a.Ly) % a.Ly;
+    return r < 0 ? r + a.Ly : r - a.Ly;
   };
 
-  // producer (thread 0): level-0 row j of both state blocks into its ring slot
-  auto issue = [&](int64_t j) {
-    const int slot = (int)((j - r0) % NSLOT);
+  // producer (thread 0): the band's pieces inside the lattice are the same for every row (at
+  // most two: one wrap when periodic); rows are issued in order, slot after slot
+  int pc0 = 0, pn0 = 0, pc1 = 0, pn1 = 0;
+  int64_t pg0 = 0, pg1 = 0;
+  if (!a.pbc_x) {
+    const int64_t lo = H - x0 > 0 ? H - x0 : 0;
+    const int64_t hi = a.Lx - x0 + H < CW ? a.Lx - x0 + H : CW;
+    if (lo < hi) {
+      pc0 = (int)lo;
+      pg0 = x0 - H + lo;
+      pn0 = (int)(hi - lo);
+    }
+  } else {
+    pg0 = x0 - H < 0 ? x0 - H + a.Lx : x0 - H;
+    pn0 = (int)(a.Lx - pg0 < CW ? a.Lx - pg0 : CW);
+    pc1 = pn0;
+    pg1 = 0;
+    pn1 = CW - pn0;
+  }
+  const uint32_t piece_bytes0 = (uint32_t)pn0 * 2u * (uint32_t)P * 16u;
+  const uint32_t piece_bytes1 = (uint32_t)pn1 * 2u * (uint32_t)P * 16u;
+  int64_t next_row = r0;
+  int next_slot = 0;
+  auto issue_next = [&]() {
+    const int64_t j = next_row;
+    const int slot = next_slot;
+    ++next_row;
+    next_slot = next_slot + 1 == NSLOT ? 0 : next_slot + 1;
     const uint32_t bar = smem_u32(bars + slot);
     const int64_t gy = grow(j);
-    if (gy < 0) {
+    if (gy < 0 || pn0 == 0) {
       mbar_arrive(bar);
       return;
     }
-    // pieces of the band [x0 - H, x0 - H + CW) that lie in the lattice (wrapping when periodic)
-    int cs[4], ns[4];
-    int64_t gs[4];
-    int np = 0;
-    if (!a.pbc_x) {
-      const int64_t lo = H - x0 > 0 ? H - x0 : 0;
-      const int64_t hi = a.Lx - x0 + H < CW ? a.Lx - x0 + H : CW;
-      if (lo < hi) {
-        cs[0] = (int)lo;
-        gs[0] = x0 - H + lo;
-        ns[0] = (int)(hi - lo);
-        np = 1;
-      }
-    } else {
-      int cc = 0;
-      while (cc < CW && np < 4) {
-        const int64_t g = (((x0 - H + cc) % a.Lx) + a.Lx) % a.Lx;
-        const int n = (int)(CW - cc < a.Lx - g ? CW - cc : a.Lx - g);
-        cs[np] = cc;
-        gs[np] = g;
-        ns[np] = n;
-        ++np;
-        cc += n;
-      }
-    }
-    uint32_t bytes = 0;
-    for (int k = 0; k < np; ++k) bytes += 2u * (uint32_t)ns[k] * 2u * (uint32_t)P * 16u;
-    mbar_arrive_tx(bar, bytes);
+    mbar_arrive_tx(bar, 2u * (piece_bytes0 + piece_bytes1));
     float4* sn = ring + slot * SU + P;
     float4* sp = ring + slot * SU + 2 * NT + 2 * P;
-    for (int k = 0; k < np; ++k) {
-      const int64_t src = gy * row_units + gs[k] * 2 * P;
-      const uint32_t nb = (uint32_t)ns[k] * 2u * (uint32_t)P * 16u;
-      bulk_g2s(smem_u32(sn + cs[k] * 2 * P), a.cur_in + src, nb, bar);
-      bulk_g2s(smem_u32(sp + cs[k] * 2 * P), a.prev_in + src, nb, bar);
+    const int64_t src0 = gy * row_units + pg0 * 2 * P;
+    bulk_g2s(smem_u32(sn + pc0 * 2 * P), a.cur_in + src0, piece_bytes0, bar);
+    bulk_g2s(smem_u32(sp + pc0 * 2 * P), a.prev_in + src0, piece_bytes0, bar);
+    if (pn1 > 0) {
+      const int64_t src1 = gy * row_units + pg1 * 2 * P;
+      bulk_g2s(smem_u32(sn + pc1 * 2 * P), a.cur_in + src1, piece_bytes1, bar);
+      bulk_g2s(smem_u32(sp + pc1 * 2 * P), a.prev_in + src1, piece_bytes1, bar);
     }
   };
   if (tid == 0)
-    for (int k = 0; k < NSLOT; ++k) issue(r0 + k);
+    for (int k = 0; k < NSLOT; ++k) issue_next();
 
   auto diag_row = [&](int64_t r) -> float2 {
     if (!HAS_DIAG) return make_float2(a.dc2, a.dc2);
@@ -281,13 +283,14 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       acc[v] = 0.f;
     }
   };
-  // ring row of level-0 row j (phi_n part; phi_{n-1} part at + 2 NT + P), or null when row j
-  // holds no data (outside the lattice, beyond the needed rows, before the segment's first row)
-  auto ring_row = [&](int64_t j) -> const float4* {
-    if (j < r0 || grow(j) < 0) return nullptr;
-    return ring + (int)((j - r0) % NSLOT) * SU + P;
-  };
+  // ring rows of level-0 rows r-1, r, r+1 at the current position (phi_n part; the phi_{n-1}
+  // part follows at + 2 NT + P), or null where a row holds no data (outside the lattice, beyond
+  // the needed rows, before the segment's first row); slots advance one per position
+  auto ring_at = [&](int slot, bool valid) -> const float4* { return valid ? ring + slot * SU + P : nullptr; };
   auto ld = [&](const float4* row, int u) -> float4 { return row ? row[u] : zero; };
+  int slot_m1 = NSLOT - 1, slot_0 = 0, slot_p1 = 1 % NSLOT;
+  bool val_m1 = false, val_0 = grow(r0) >= 0;
+  uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
 
   bool timed_out = !mbar_wait(smem_u32(bars + 0), 0);  // this thread's waits; OR-reduced per position
   const float th = a.th2;
@@ -300,15 +303,11 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       const int64_t r = rb + u;
       if (r > r_end || aborted) break;
       const int s0 = u, s1 = (u + 2) % 3, s2 = (u + 1) % 3;  // ages 0, 1, 2
-      {  // level-0 row r+1 must have landed
-        const int64_t j = r + 1;
-        const int slot = (int)((j - r0) % NSLOT);
-        const uint32_t par = (uint32_t)(((j - r0) / NSLOT) & 1);
-        if (!mbar_wait(smem_u32(bars + slot), par)) timed_out = true;
-      }
-      const float4* Rm = ring_row(r - 1);
-      const float4* R0 = ring_row(r);
-      const float4* Rp = ring_row(r + 1);
+      if (!mbar_wait(smem_u32(bars + slot_p1), wait_par)) timed_out = true;  // level-0 row r+1
+      const bool val_p1 = grow(r + 1) >= 0;
+      const float4* Rm = ring_at(slot_m1, val_m1);
+      const float4* R0 = ring_at(slot_0, val_0);
+      const float4* Rp = ring_at(slot_p1, val_p1);
 #pragma unroll
       for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
       dh[0] = dn1;
@@ -379,18 +378,22 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       }
       r_done = r;
       // row r-1 has been read for the last time: refill its slot with row r - 1 + NSLOT
-      if (tid == 0 && r - 1 >= r0) issue(r - 1 + NSLOT);
+      if (tid == 0 && r - 1 >= r0) issue_next();
+      slot_m1 = slot_0;
+      slot_0 = slot_p1;
+      slot_p1 = slot_p1 + 1 == NSLOT ? 0 : slot_p1 + 1;
+      if (slot_p1 == 0) wait_par ^= 1u;
+      val_m1 = val_0;
+      val_0 = val_p1;
     }
   }
   if (aborted && tid == 0) {
     // copies in flight into this CTA's shared memory must land before it exits: rows
-    // r_done + 2 .. r_done - 1 + NSLOT were issued and never waited for (bounded waits)
+    // r_done + 2 .. next_row - 1 were issued and never waited for (bounded waits)
     bool err_wait = false;
-    const int64_t last_issued = r_done - 1 >= r0 ? r_done - 1 + NSLOT : r0 + NSLOT - 1;
-    for (int64_t j = r_done + 2; j <= last_issued; ++j) {
-      const int slot = (int)((j - r0) % NSLOT);
-      const uint32_t par = (uint32_t)(((j - r0) / NSLOT) & 1);
-      if (!mbar_wait(smem_u32(bars + slot), par)) err_wait = true;
+    for (int64_t j = r_done + 2 > r0 ? r_done + 2 : r0; j < next_row; ++j) {
+      const int64_t k = j - r0;
+      if (!mbar_wait(smem_u32(bars + (int)(k % NSLOT)), (uint32_t)((k / NSLOT) & 1))) err_wait = true;
     }
     atomicExch(a.status, err_wait ? 2 : 1);
   }
