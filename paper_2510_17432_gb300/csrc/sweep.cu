@@ -40,6 +40,11 @@ namespace sweep {
 
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per mbarrier wait
 
+// Source of the bulk copies for rows that hold no data (outside an open lattice, beyond the rows
+// a segment needs): two state-block rows of 2 NT units for NT <= 256.  Zero-initialised when the
+// module loads and never written, so every ring read is a plain shared load.
+static __device__ __align__(16) float4 g_zero_rows[2 * 256];
+
 template <int NT_, int K_, int NSLOT_>
 struct Cfg {
   static constexpr int NT = NT_, K = K_, H = K_ / 2, NSLOT = NSLOT_;
@@ -123,15 +128,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// d own + th (n1 + n2 + n3) - pv for one complex64 pair
+// d own + th (n1 + n2 + n3) - pv for one complex64 pair, as two packed f32x2 halves (one state each)
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 half_update(float2 d, float2 own, float2 th, float2 n1, float2 n2, float2 n3,
+                                              float2 pv) {
+  const float2 h = __fadd2_rn(__fadd2_rn(n1, n2), n3);
+  return __ffma2_rn(d, own, __ffma2_rn(th, h, make_float2(-pv.x, -pv.y)));
+}
 __device__ __forceinline__ float4 level_update(float d, float4 own, float th, float4 n1, float4 n2, float4 n3,
                                                float4 pv) {
-  float4 r;
-  r.x = fmaf(d, own.x, fmaf(th, (n1.x + n2.x) + n3.x, -pv.x));
-  r.y = fmaf(d, own.y, fmaf(th, (n1.y + n2.y) + n3.y, -pv.y));
-  r.z = fmaf(d, own.z, fmaf(th, (n1.z + n2.z) + n3.z, -pv.z));
-  r.w = fmaf(d, own.w, fmaf(th, (n1.w + n2.w) + n3.w, -pv.w));
-  return r;
+  const float2 d2 = make_float2(d, d), t2 = make_float2(th, th);
+  const float2 l = half_update(d2, lo2(own), t2, lo2(n1), lo2(n2), lo2(n3), lo2(pv));
+  const float2 h = half_update(d2, hi2(own), t2, hi2(n1), hi2(n2), hi2(n3), hi2(pv));
+  return make_float4(l.x, l.y, h.x, h.y);
 }
 
 // acc[0..5] += {|a|^2, Re<n|a>, Im... } for the two states of a pair: <phi_j|phi_j> and
@@ -176,8 +186,13 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   const int64_t ye = ys + a.SY < a.Ly ? ys + a.SY : a.Ly;
   const int64_t r0 = ys - H;          // first sweep position = first level-0 row
   const int64_t rlast = ye + H - 1;   // last level-0 row any exact value needs
-  const int64_t r_end = ye + K - 2;   // level K reaches row ye - 1 here
+  const int ny = (int)(ye - ys);
+  const int npos = ny + K - 1 + H;    // positions r0 .. ye + K - 2 (level K reaches row ye - 1)
   const int64_t row_units = 2 * a.Lx * P;
+  // level-0 rows that hold data, as local indices i = row - r0: [v_lo, v_hi]
+  const bool open_y = OPEN && !a.pbc_y;
+  const int v_lo = (open_y && r0 < 0) ? (int)(-r0) : 0;
+  const int v_hi = (int)(((open_y && rlast > a.Ly - 1) ? a.Ly - 1 : rlast) - r0);
 
   // this thread's cell and pair.  The band [x0 - H, x0 - H + CW) and the rows r0 .. r_end lie
   // within one period of the lattice on either side (the host requires Lx >= CW, Ly > H), so a
@@ -194,16 +209,17 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   const int uA = 2 * (c << logP) + p;  // unit of A(c, pair p) in a ring row; B is + P
   const int wA = tid, wB = NT + P + tid;
 
-  // row index in the lattice, or -1 outside it (open y) or beyond the rows that are needed
-  auto grow = [&](int64_t r) -> int64_t {
-    if (r > rlast) return -1;
+  // row index in the lattice of local row i, or -1 where the row holds no data
+  auto grow = [&](int i) -> int64_t {
+    if (i < v_lo || i > v_hi) return -1;
+    const int64_t r = r0 + i;
     if (r >= 0 && r < a.Ly) return r;
-    if (OPEN && !a.pbc_y) return -1;
     return r < 0 ? r + a.Ly : r - a.Ly;
   };
 
   // producer (thread 0): the band's pieces inside the lattice are the same for every row (at
-  // most two: one wrap when periodic); rows are issued in order, slot after slot
+  // most two: one wrap when periodic); rows are issued in order, slot after slot; a row without
+  // data is filled with zeros from g_zero_rows
   int pc0 = 0, pn0 = 0, pc1 = 0, pn1 = 0;
   int64_t pg0 = 0, pg1 = 0;
   if (!a.pbc_x) {
@@ -223,39 +239,46 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   }
   const uint32_t piece_bytes0 = (uint32_t)pn0 * 2u * (uint32_t)P * 16u;
   const uint32_t piece_bytes1 = (uint32_t)pn1 * 2u * (uint32_t)P * 16u;
-  int64_t next_row = r0;
+  const uint32_t zero_bytes = 2u * NT * 16u;
+  int next_row = 0;  // local index of the next row to issue
   int next_slot = 0;
+  // rows 0 .. npos are read (row r+1 at the last position); none beyond is issued, so no copy is
+  // in flight when the CTA finishes its sweep
   auto issue_next = [&]() {
-    const int64_t j = next_row;
+    if (next_row > npos) return;
+    const int j = next_row;
     const int slot = next_slot;
     ++next_row;
     next_slot = next_slot + 1 == NSLOT ? 0 : next_slot + 1;
     const uint32_t bar = smem_u32(bars + slot);
+    const uint32_t sn = smem_u32(ring + slot * SU + P);
+    const uint32_t sp = smem_u32(ring + slot * SU + 2 * NT + 2 * P);
     const int64_t gy = grow(j);
-    if (gy < 0 || pn0 == 0) {
-      mbar_arrive(bar);
+    if (gy < 0) {
+      mbar_arrive_tx(bar, 2u * zero_bytes);
+      bulk_g2s(sn, g_zero_rows, zero_bytes, bar);
+      bulk_g2s(sp, g_zero_rows, zero_bytes, bar);
       return;
     }
     mbar_arrive_tx(bar, 2u * (piece_bytes0 + piece_bytes1));
-    float4* sn = ring + slot * SU + P;
-    float4* sp = ring + slot * SU + 2 * NT + 2 * P;
     const int64_t src0 = gy * row_units + pg0 * 2 * P;
-    bulk_g2s(smem_u32(sn + pc0 * 2 * P), a.cur_in + src0, piece_bytes0, bar);
-    bulk_g2s(smem_u32(sp + pc0 * 2 * P), a.prev_in + src0, piece_bytes0, bar);
+    bulk_g2s(sn + 32u * pc0 * P, a.cur_in + src0, piece_bytes0, bar);
+    bulk_g2s(sp + 32u * pc0 * P, a.prev_in + src0, piece_bytes0, bar);
     if (pn1 > 0) {
       const int64_t src1 = gy * row_units + pg1 * 2 * P;
-      bulk_g2s(smem_u32(sn + pc1 * 2 * P), a.cur_in + src1, piece_bytes1, bar);
-      bulk_g2s(smem_u32(sp + pc1 * 2 * P), a.prev_in + src1, piece_bytes1, bar);
+      bulk_g2s(sn + 32u * pc1 * P, a.cur_in + src1, piece_bytes1, bar);
+      bulk_g2s(sp + 32u * pc1 * P, a.prev_in + src1, piece_bytes1, bar);
     }
   };
   if (tid == 0)
     for (int k = 0; k < NSLOT; ++k) issue_next();
 
-  auto diag_row = [&](int64_t r) -> float2 {
+  const float* drow = HAS_DIAG ? a.diag + 2 * x : nullptr;
+  auto diag_row = [&](int i) -> float2 {
     if (!HAS_DIAG) return make_float2(a.dc2, a.dc2);
-    const int64_t gy = grow(r);
+    const int64_t gy = grow(i);
     if (gy < 0 || ghx) return make_float2(0.f, 0.f);
-    const float2 d = __ldg(reinterpret_cast<const float2*>(a.diag + 2 * (gy * a.Lx + x)));
+    const float2 d = __ldg(reinterpret_cast<const float2*>(drow + 2 * gy * a.Lx));
     return make_float2(2.f * d.x, 2.f * d.y);
   };
 
@@ -266,10 +289,10 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   for (int l = 0; l < K; ++l)
 #pragma unroll
     for (int s = 0; s < 3; ++s) RA[l][s] = RB[l][s] = zero;
-  float2 dh[K];  // 2 D of rows r, r-1, .., r-K+1
+  float2 dh[K];  // 2 D of rows r, r-1, .., r-K+1 (disordered lattices)
 #pragma unroll
   for (int l = 0; l < K; ++l) dh[l] = make_float2(0.f, 0.f);
-  float2 dn1 = diag_row(r0), dn2 = diag_row(r0 + 1);
+  float2 dn1 = diag_row(0), dn2 = diag_row(1);
   float acc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.f;
@@ -283,52 +306,52 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       acc[v] = 0.f;
     }
   };
-  // ring rows of level-0 rows r-1, r, r+1 at the current position (phi_n part; the phi_{n-1}
-  // part follows at + 2 NT + P), or null where a row holds no data (outside the lattice, beyond
-  // the needed rows, before the segment's first row); slots advance one per position
-  auto ring_at = [&](int slot, bool valid) -> const float4* { return valid ? ring + slot * SU + P : nullptr; };
-  auto ld = [&](const float4* row, int u) -> float4 { return row ? row[u] : zero; };
-  int slot_m1 = NSLOT - 1, slot_0 = 0, slot_p1 = 1 % NSLOT;
-  bool val_m1 = false, val_0 = grow(r0) >= 0;
+  // outputs of levels K-1 and K at the rows they form at the current position
+  float4* out_km1 = a.prev_out + (r0 - (K - 2)) * row_units + colA;
+  float4* out_k = a.cur_out + (r0 - (K - 1)) * row_units + colA;
+  // ring slots of level-0 rows r-1, r, r+1 (a slot's phi_{n-1} row follows at + 2 NT + P)
+  // (row r0 - 1 does not exist: its slot stands in as row r0's, which only feeds values outside
+  // the exact region)
+  int slot_m1 = 0, slot_0 = 0, slot_p1 = 1 % NSLOT;
   uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
 
   bool timed_out = !mbar_wait(smem_u32(bars + 0), 0);  // this thread's waits; OR-reduced per position
   const float th = a.th2;
   bool aborted = false;
-  int64_t r_done = r0 - 1;  // last position completed
+  int i_done = -1;  // last position completed
 
-  for (int64_t rb = r0; rb <= r_end && !aborted; rb += 3) {
+  for (int ib = 0; ib < npos && !aborted; ib += 3) {
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
-      const int64_t r = rb + u;
-      if (r > r_end || aborted) break;
+      const int i = ib + u;
+      if (i >= npos || aborted) break;
       const int s0 = u, s1 = (u + 2) % 3, s2 = (u + 1) % 3;  // ages 0, 1, 2
       if (!mbar_wait(smem_u32(bars + slot_p1), wait_par)) timed_out = true;  // level-0 row r+1
-      const bool val_p1 = grow(r + 1) >= 0;
-      const float4* Rm = ring_at(slot_m1, val_m1);
-      const float4* R0 = ring_at(slot_0, val_0);
-      const float4* Rp = ring_at(slot_p1, val_p1);
+      const float4* Rm = ring + slot_m1 * SU + P;
+      const float4* R0 = ring + slot_0 * SU + P;
+      const float4* Rp = ring + slot_p1 * SU + P;
+      if (HAS_DIAG) {
 #pragma unroll
-      for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
-      dh[0] = dn1;
-      dn1 = dn2;
-      dn2 = diag_row(r + 2);
+        for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
+        dh[0] = dn1;
+        dn1 = dn2;
+        dn2 = diag_row(i + 2);
+      }
 #pragma unroll
       for (int L = 1; L <= K; ++L) {
-        const int64_t q = r - (L - 1);
-        const bool ghost = OPEN && (ghx || grow(q) < 0);
+        const int iq = i - (L - 1);  // local row of this level
         float4 ownA, ownB, bxm, axp, bym, ayp, pvA, pvB;
         if (L == 1) {
-          ownA = ld(R0, uA);
-          ownB = ld(R0, uA + P);
-          bxm = ld(R0, uA - P);
-          axp = ld(R0, uA + 2 * P);
-          bym = ld(Rm, uA + P);
-          ayp = ld(Rp, uA);
-          pvA = ld(R0, 2 * NT + P + uA);
-          pvB = ld(R0, 2 * NT + P + uA + P);
+          ownA = R0[uA];
+          ownB = R0[uA + P];
+          bxm = R0[uA - P];
+          axp = R0[uA + 2 * P];
+          bym = Rm[uA + P];
+          ayp = Rp[uA];
+          pvA = R0[2 * NT + P + uA];
+          pvB = R0[2 * NT + 2 * P + uA];
         } else {
-          const float4* Xin = xb + ((L - 2) * 2 + (int)((r - 1) & 1)) * XU;
+          const float4* Xin = xb + ((L - 2) * 2 + ((i - 1) & 1)) * XU;
           ownA = RA[L - 1][s1];
           ownB = RB[L - 1][s1];
           bxm = Xin[wB - P];
@@ -336,37 +359,41 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           bym = RB[L - 1][s2];
           ayp = RA[L - 1][s0];
           if (L == 2) {
-            pvA = ld(Rm, uA);
-            pvB = ld(Rm, uA + P);
+            pvA = Rm[uA];
+            pvB = Rm[uA + P];
           } else {
             pvA = RA[L - 2][s2];
             pvB = RB[L - 2][s2];
           }
         }
-        float4 nA = level_update(dh[L - 1].x, ownA, th, ownB, bxm, bym, pvA);
-        float4 nB = level_update(dh[L - 1].y, ownB, th, ownA, axp, ayp, pvB);
-        if (ghost) {
+        const float dA = HAS_DIAG ? dh[L - 1].x : a.dc2, dB = HAS_DIAG ? dh[L - 1].y : a.dc2;
+        float4 nA = level_update(dA, ownA, th, ownB, bxm, bym, pvA);
+        float4 nB = level_update(dB, ownB, th, ownA, axp, ayp, pvB);
+        if (OPEN && (ghx || iq < v_lo || iq > v_hi)) {
           nA = zero;
           nB = zero;
         }
         if (L < K) {
           RA[L][s0] = nA;
           RB[L][s0] = nB;
-          float4* Xout = xb + ((L - 1) * 2 + (int)(r & 1)) * XU;
+          float4* Xout = xb + ((L - 1) * 2 + (i & 1)) * XU;
           Xout[wA] = nA;
           Xout[wB] = nB;
         }
-        if (intx && q >= ys && q < ye) {
-          if (L >= K - 1) {
-            float4* dst = (L == K - 1) ? a.prev_out : a.cur_out;
-            const int64_t off = q * row_units + colA;
-            __stcs(dst + off, nA);
-            __stcs(dst + off + P, nB);
+        if (intx && (unsigned)(iq - H) < (unsigned)ny) {
+          if (L == K - 1) {
+            __stcs(out_km1, nA);
+            __stcs(out_km1 + P, nB);
+          } else if (L == K) {
+            __stcs(out_k, nA);
+            __stcs(out_k + P, nB);
           }
           moment_terms(acc + (L - 1) * 6, ownA, nA);
           moment_terms(acc + (L - 1) * 6, ownB, nB);
         }
       }
+      out_km1 += row_units;
+      out_k += row_units;
       if (++folded == C::FOLD) {
         folded = 0;
         fold();
@@ -376,25 +403,21 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
         aborted = true;
         break;
       }
-      r_done = r;
+      i_done = i;
       // row r-1 has been read for the last time: refill its slot with row r - 1 + NSLOT
-      if (tid == 0 && r - 1 >= r0) issue_next();
+      if (tid == 0 && i >= 1) issue_next();
       slot_m1 = slot_0;
       slot_0 = slot_p1;
       slot_p1 = slot_p1 + 1 == NSLOT ? 0 : slot_p1 + 1;
       if (slot_p1 == 0) wait_par ^= 1u;
-      val_m1 = val_0;
-      val_0 = val_p1;
     }
   }
   if (aborted && tid == 0) {
     // copies in flight into this CTA's shared memory must land before it exits: rows
-    // r_done + 2 .. next_row - 1 were issued and never waited for (bounded waits)
+    // i_done + 2 .. next_row - 1 were issued and never waited for (bounded waits)
     bool err_wait = false;
-    for (int64_t j = r_done + 2 > r0 ? r_done + 2 : r0; j < next_row; ++j) {
-      const int64_t k = j - r0;
-      if (!mbar_wait(smem_u32(bars + (int)(k % NSLOT)), (uint32_t)((k / NSLOT) & 1))) err_wait = true;
-    }
+    for (int j = i_done + 2 > 0 ? i_done + 2 : 0; j < next_row; ++j)
+      if (!mbar_wait(smem_u32(bars + j % NSLOT), (uint32_t)((j / NSLOT) & 1))) err_wait = true;
     atomicExch(a.status, err_wait ? 2 : 1);
   }
   fold();
