@@ -297,14 +297,55 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] = 0.f;
   int folded = 0;
+  // every FOLD positions: the FP32 partials of the lanes of each state pair (lane = p + P m) are
+  // reduce-scattered across the lanes (each exchange halves the values a lane keeps), so that a
+  // lane ends with 24 / (32 / P) fully summed values (at least 3) and adds only those into the
+  // warp's FP64 slots: the FP64 work is spread over the whole warp instead of P lanes
+  static_assert(NV == 24, "the fold splits 24 values");
   auto fold = [&]() {
+    const int pp = lane & (P - 1);
+    double* slot = red + (warp * P + pp) * NV;
+    auto half = [&](const float* in, float* out, int n, int off) {
+      const bool up = (lane & off) != 0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      float t = acc[v];
-      for (int off = 16; off >= P; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-      if (lane < P) red[(warp * P + lane) * NV + v] += (double)t;
-      acc[v] = 0.f;
+      for (int k = 0; k < 12; ++k) {
+        if (k < n / 2) {
+          const float keep = up ? in[n / 2 + k] : in[k];
+          const float send = up ? in[k] : in[n / 2 + k];
+          out[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+      }
+    };
+    float a12[12];
+    half(acc, a12, 24, 16);
+    const int v16 = (lane & 16) ? 12 : 0;
+    if (P == 16) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) slot[v16 + k] += (double)a12[k];
+    } else {
+      float a6[6];
+      half(a12, a6, 12, 8);
+      const int v8 = v16 + ((lane & 8) ? 6 : 0);
+      if (P == 8) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) slot[v8 + k] += (double)a6[k];
+      } else {
+        float a3[3];
+        half(a6, a3, 6, 4);
+        const int v4 = v8 + ((lane & 4) ? 3 : 0);
+        // below P = 4 the remaining lane bits carry no pair: sum them (every lane ends with the
+        // same three values) and let the lane whose extra bits are zero add them
+        for (int off = 2; off >= P; off >>= 1)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) a3[k] += __shfl_xor_sync(0xffffffffu, a3[k], off);
+        if ((lane & 3 & ~(P - 1)) == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) slot[v4 + k] += (double)a3[k];
+        }
+      }
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
   };
   // outputs of levels K-1 and K at the rows they form at the current position
   float4* out_km1 = a.prev_out + (r0 - (K - 2)) * row_units + colA;
@@ -330,6 +371,15 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       const float4* Rm = ring + slot_m1 * SU + P;
       const float4* R0 = ring + slot_0 * SU + P;
       const float4* Rp = ring + slot_p1 * SU + P;
+      // x-neighbours of levels 1 .. K-1 written at the previous position, loaded before this
+      // position writes any exchange row (the compiler cannot tell the two parities apart)
+      float4 xbm[K], xap[K];
+#pragma unroll
+      for (int L = 2; L <= K; ++L) {
+        const float4* Xin = xb + ((L - 2) * 2 + ((i - 1) & 1)) * XU;
+        xbm[L - 1] = Xin[wB - P];
+        xap[L - 1] = Xin[wA + P];
+      }
       if (HAS_DIAG) {
 #pragma unroll
         for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
@@ -351,11 +401,10 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           pvA = R0[2 * NT + P + uA];
           pvB = R0[2 * NT + 2 * P + uA];
         } else {
-          const float4* Xin = xb + ((L - 2) * 2 + ((i - 1) & 1)) * XU;
           ownA = RA[L - 1][s1];
           ownB = RB[L - 1][s1];
-          bxm = Xin[wB - P];
-          axp = Xin[wA + P];
+          bxm = xbm[L - 1];
+          axp = xap[L - 1];
           bym = RB[L - 1][s2];
           ayp = RA[L - 1][s0];
           if (L == 2) {
