@@ -48,7 +48,7 @@ static __device__ __align__(16) float4 g_zero_rows[2 * 256];
 template <int NT_, int K_, int NSLOT_>
 struct Cfg {
   static constexpr int NT = NT_, K = K_, H = K_ / 2, NSLOT = NSLOT_;
-  static constexpr int NV = 6 * K;     // per level: {|a|^2, Re<n|a>, Im<n|a>} x 2 states
+  static constexpr int NV = 4 * K;     // per level: {|a|^2, Re<n|a>} x 2 states
   static constexpr int FOLD = 16;      // positions per FP32 partial (32 unit terms per thread)
   static constexpr int MINB = NT <= 128 ? 3 : NT <= 192 ? 2 : 1;
   static constexpr int BAR_BYTES = ((NSLOT * 8 + 15) / 16) * 16;
@@ -144,15 +144,16 @@ __device__ __forceinline__ float4 level_update(float d, float4 own, float th, fl
   return make_float4(l.x, l.y, h.x, h.y);
 }
 
-// acc[0..5] += {|a|^2, Re<n|a>, Im... } for the two states of a pair: <phi_j|phi_j> and
-// <phi_{j+1}|phi_j> with a = phi_j, n = phi_{j+1} (the bra is conjugated)
-__device__ __forceinline__ void moment_terms(float* acc, float4 a, float4 n) {
-  acc[0] = fmaf(a.x, a.x, fmaf(a.y, a.y, acc[0]));
-  acc[1] = fmaf(n.x, a.x, fmaf(n.y, a.y, acc[1]));
-  acc[2] = fmaf(n.x, a.y, fmaf(-n.y, a.x, acc[2]));
-  acc[3] = fmaf(a.z, a.z, fmaf(a.w, a.w, acc[3]));
-  acc[4] = fmaf(n.z, a.z, fmaf(n.w, a.w, acc[4]));
-  acc[5] = fmaf(n.z, a.w, fmaf(-n.w, a.z, acc[5]));
+// Moment terms of one level for the two states of a pair, a = phi_j and n = phi_{j+1}:
+// <phi_j|phi_j> and Re<phi_{j+1}|phi_j> as packed (re, im) halves, summed at the fold.  For a
+// Hermitian H~, <phi_{j+1}|phi_j> = <psi|T_{j+1}(H~) T_j(H~)|psi> is real (the two polynomials
+// commute and are Hermitian), so its imaginary part is not accumulated.
+// acc2[0] = |a_0|^2, acc2[1] = |a_1|^2, acc2[2] = Re n_0^* a_0, acc2[3] = Re n_1^* a_1 (halves)
+__device__ __forceinline__ void moment_terms(float2* acc2, float4 a, float4 n) {
+  acc2[0] = __ffma2_rn(lo2(a), lo2(a), acc2[0]);
+  acc2[1] = __ffma2_rn(hi2(a), hi2(a), acc2[1]);
+  acc2[2] = __ffma2_rn(lo2(n), lo2(a), acc2[2]);
+  acc2[3] = __ffma2_rn(hi2(n), hi2(a), acc2[3]);
 }
 
 template <int NT_, int K_, int NSLOT_, bool HAS_DIAG, bool OPEN>
@@ -293,22 +294,28 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
 #pragma unroll
   for (int l = 0; l < K; ++l) dh[l] = make_float2(0.f, 0.f);
   float2 dn1 = diag_row(0), dn2 = diag_row(1);
-  float acc[NV];
+  float2 acc2[NV];  // packed halves of the NV sums (level L: [4(L-1), 4L))
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+  for (int v = 0; v < NV; ++v) acc2[v] = make_float2(0.f, 0.f);
   int folded = 0;
   // every FOLD positions: the FP32 partials of the lanes of each state pair (lane = p + P m) are
   // reduce-scattered across the lanes (each exchange halves the values a lane keeps), so that a
-  // lane ends with 24 / (32 / P) fully summed values (at least 3) and adds only those into the
-  // warp's FP64 slots: the FP64 work is spread over the whole warp instead of P lanes
-  static_assert(NV == 24, "the fold splits 24 values");
+  // lane ends with 16 / (32 / P) fully summed values and adds only those into the warp's FP64
+  // slots: the FP64 work is spread over the whole warp instead of P lanes
+  static_assert(NV == 16, "the fold splits 16 values");
   auto fold = [&]() {
     const int pp = lane & (P - 1);
     double* slot = red + (warp * P + pp) * NV;
+    float v16[16];
+#pragma unroll
+    for (int v = 0; v < 16; ++v) {
+      v16[v] = acc2[v].x + acc2[v].y;
+      acc2[v] = make_float2(0.f, 0.f);
+    }
     auto half = [&](const float* in, float* out, int n, int off) {
       const bool up = (lane & off) != 0;
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
+      for (int k = 0; k < 8; ++k) {
         if (k < n / 2) {
           const float keep = up ? in[n / 2 + k] : in[k];
           const float send = up ? in[k] : in[n / 2 + k];
@@ -316,36 +323,36 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
         }
       }
     };
-    float a12[12];
-    half(acc, a12, 24, 16);
-    const int v16 = (lane & 16) ? 12 : 0;
+    float v8[8];
+    half(v16, v8, 16, 16);
+    const int b16 = (lane & 16) ? 8 : 0;
     if (P == 16) {
 #pragma unroll
-      for (int k = 0; k < 12; ++k) slot[v16 + k] += (double)a12[k];
-    } else {
-      float a6[6];
-      half(a12, a6, 12, 8);
-      const int v8 = v16 + ((lane & 8) ? 6 : 0);
-      if (P == 8) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) slot[v8 + k] += (double)a6[k];
-      } else {
-        float a3[3];
-        half(a6, a3, 6, 4);
-        const int v4 = v8 + ((lane & 4) ? 3 : 0);
-        // below P = 4 the remaining lane bits carry no pair: sum them (every lane ends with the
-        // same three values) and let the lane whose extra bits are zero add them
-        for (int off = 2; off >= P; off >>= 1)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) a3[k] += __shfl_xor_sync(0xffffffffu, a3[k], off);
-        if ((lane & 3 & ~(P - 1)) == 0) {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) slot[v4 + k] += (double)a3[k];
-        }
-      }
+      for (int k = 0; k < 8; ++k) slot[b16 + k] += (double)v8[k];
+      return;
     }
+    float v4[4];
+    half(v8, v4, 8, 8);
+    const int b8 = b16 + ((lane & 8) ? 4 : 0);
+    if (P == 8) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.f;
+      for (int k = 0; k < 4; ++k) slot[b8 + k] += (double)v4[k];
+      return;
+    }
+    float v2[2];
+    half(v4, v2, 4, 4);
+    const int b4 = b8 + ((lane & 4) ? 2 : 0);
+    if (P == 4) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) slot[b4 + k] += (double)v2[k];
+      return;
+    }
+    float v1[1];
+    half(v2, v1, 2, 2);
+    const int b2 = b4 + ((lane & 2) ? 1 : 0);
+    // P = 2: every lane holds one sum; P = 1: lanes 2k and 2k+1 hold halves of the same one
+    if (P == 1) v1[0] += __shfl_xor_sync(0xffffffffu, v1[0], 1);
+    if (P == 2 || (lane & 1) == 0) slot[b2] += (double)v1[0];
   };
   // outputs of levels K-1 and K at the rows they form at the current position
   float4* out_km1 = a.prev_out + (r0 - (K - 2)) * row_units + colA;
@@ -437,8 +444,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
             __stcs(out_k, nA);
             __stcs(out_k + P, nB);
           }
-          moment_terms(acc + (L - 1) * 6, ownA, nA);
-          moment_terms(acc + (L - 1) * 6, ownB, nB);
+          moment_terms(acc2 + (L - 1) * 4, ownA, nA);
+          moment_terms(acc2 + (L - 1) * 4, ownB, nB);
         }
       }
       out_km1 += row_units;
@@ -483,24 +490,23 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   __syncthreads();
   if (ticket != gridDim.x - 1) return;
   __threadfence();
-  const int nval = K * a.S * 3;
+  const int nval = K * a.S * 2;
   for (int v = warp; v < nval; v += NT / 32) {
-    const int k = v / (a.S * 3), rem = v - k * a.S * 3, s = rem / 3, comp = rem - s * 3;
+    const int k = v / (a.S * 2), rem = v - k * a.S * 2, s = rem / 2, comp = rem - s * 2;
     const int pr = s >> 1, sub = s & 1;
-    const int idx = k * 6 + sub * 3 + comp;
+    const int idx = k * 4 + comp * 2 + sub;
     double sum = 0.0;
     for (int t = lane; t < (int)gridDim.x; t += 32) sum += __ldcg(a.partials + ((size_t)t * P + pr) * NV + idx);
     for (int off = 16; off >= 1; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
     if (lane == 0) {
       const int j = a.step0 + k;
       double* ms = a.mu + (size_t)s * a.M * 2;
-      if (comp == 0) {
+      if (comp == 0) {  // m_{2j} = 2 <phi_j|phi_j> - m_0 (real)
         ms[4 * j] = 2.0 * sum - ms[0];
         ms[4 * j + 1] = -ms[1];
-      } else if (comp == 1) {
+      } else {          // m_{2j+1} = 2 <phi_{j+1}|phi_j> - m_1, the inner product real
         ms[4 * j + 2] = 2.0 * sum - ms[2];
-      } else {
-        ms[4 * j + 3] = 2.0 * sum - ms[3];
+        ms[4 * j + 3] = -ms[3];
       }
     }
   }
