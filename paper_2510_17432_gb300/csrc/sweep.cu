@@ -52,10 +52,11 @@ struct Cfg {
   static constexpr int FOLD = 16;      // positions per FP32 partial (32 unit terms per thread)
   static constexpr int MINB = NT <= 128 ? 3 : NT <= 192 ? 2 : 1;
   static constexpr int BAR_BYTES = ((NSLOT * 8 + 15) / 16) * 16;
-  // ring slot: [P zero][phi_n row: 2 NT units][P zero][phi_{n-1} row: 2 NT units]
-  static int slot_units(int P) { return 4 * NT + 2 * P; }
+  // ring slot: [P zero][phi_n row: 2 NT units][P zero][phi_{n-1} row: 2 NT units], padded to a
+  // multiple of 8 units (128 bytes) so that every slot starts on the same bank
+  __host__ __device__ static int slot_units(int P) { return (4 * NT + 2 * P + 7) & ~7; }
   // exchange row: [A plane: NT units][P zero][B plane: NT units]
-  static int xrow_units(int P) { return 2 * NT + P; }
+  __host__ __device__ static int xrow_units(int P) { return 2 * NT + P; }
   static size_t smem(int P) {
     return (size_t)BAR_BYTES + 16 * ((size_t)NSLOT * slot_units(P) + (size_t)2 * (K - 1) * xrow_units(P)) +
            8 * (size_t)(NT / 32) * P * NV;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ unsigned ticket;
   const int P = a.P, logP = a.logP, CW = a.CW;
-  const int SU = 4 * NT + 2 * P, XU = 2 * NT + P;
+  const int SU = C::slot_units(P), XU = 2 * NT + P;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smraw);
   float4* ring = reinterpret_cast<float4*>(smraw + C::BAR_BYTES);  // [NSLOT][SU]
   float4* xb = ring + NSLOT * SU;                                   // [K-1][2][XU]
@@ -209,6 +210,14 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   const int64_t colA = 2 * x * P + p;
   const int uA = 2 * (c << logP) + p;  // unit of A(c, pair p) in a ring row; B is + P
   const int wA = tid, wB = NT + P + tid;
+  // Ring rows interleave A and B per cell, so the A units of the cells of a quarter-warp share
+  // banks.  Threads with bit 2 of tid set take each pair of level-0 loads in the opposite order,
+  // which puts the two halves of a quarter-warp on different banks for any P.
+  const bool swp = (tid >> 2) & 1;
+  const int o_pvA = 2 * NT + P + uA, o_pvB = o_pvA + P;  // phi_{n-1} A, B of row r (R0)
+  const int o_bxm = uA - P, o_axp = uA + 2 * P;          // B(x-1, r), A(x+1, r) (R0)
+  const int o_p1 = swp ? o_pvB : o_pvA, o_p2 = swp ? o_pvA : o_pvB;
+  const int o_n1 = swp ? o_axp : o_bxm, o_n2 = swp ? o_bxm : o_axp;
 
   // row index in the lattice of local row i, or -1 where the row holds no data
   auto grow = [&](int i) -> int64_t {
@@ -357,13 +366,15 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   // outputs of levels K-1 and K at the rows they form at the current position
   float4* out_km1 = a.prev_out + (r0 - (K - 2)) * row_units + colA;
   float4* out_k = a.cur_out + (r0 - (K - 1)) * row_units + colA;
-  // ring slots of level-0 rows r-1, r, r+1 (a slot's phi_{n-1} row follows at + 2 NT + P)
-  // (row r0 - 1 does not exist: its slot stands in as row r0's, which only feeds values outside
-  // the exact region)
-  int slot_m1 = 0, slot_0 = 0, slot_p1 = 1 % NSLOT;
+  // ring slots of level-0 rows r and r+1 (a slot's phi_{n-1} row follows at + 2 NT + P)
+  int slot_0 = 0, slot_p1 = 1 % NSLOT;
   uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
 
   bool timed_out = !mbar_wait(smem_u32(bars + 0), 0);  // this thread's waits; OR-reduced per position
+  // level-0 values carried from position to position: A(r) (loaded as A(x, r+1) one position
+  // earlier), A(r-1), B(r-1) (this thread's own cell); row r0 - 1 stands in as row r0
+  float4 c0A = ring[P + uA];
+  float4 cmA = c0A, cmB = ring[P + uA + P];
   const float th = a.th2;
   bool aborted = false;
   int i_done = -1;  // last position completed
@@ -375,7 +386,6 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       if (i >= npos || aborted) break;
       const int s0 = u, s1 = (u + 2) % 3, s2 = (u + 1) % 3;  // ages 0, 1, 2
       if (!mbar_wait(smem_u32(bars + slot_p1), wait_par)) timed_out = true;  // level-0 row r+1
-      const float4* Rm = ring + slot_m1 * SU + P;
       const float4* R0 = ring + slot_0 * SU + P;
       const float4* Rp = ring + slot_p1 * SU + P;
       // x-neighbours of levels 1 .. K-1 written at the previous position, loaded before this
@@ -394,19 +404,27 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
         dn1 = dn2;
         dn2 = diag_row(i + 2);
       }
+      const float4 prevA = cmA, prevB = cmB;  // level-0 row r-1 of this cell
 #pragma unroll
       for (int L = 1; L <= K; ++L) {
         const int iq = i - (L - 1);  // local row of this level
         float4 ownA, ownB, bxm, axp, bym, ayp, pvA, pvB;
         if (L == 1) {
-          ownA = R0[uA];
-          ownB = R0[uA + P];
-          bxm = R0[uA - P];
-          axp = R0[uA + 2 * P];
-          bym = Rm[uA + P];
-          ayp = Rp[uA];
-          pvA = R0[2 * NT + P + uA];
-          pvB = R0[2 * NT + 2 * P + uA];
+          // three pairs of loads, each issued in the thread's bank order
+          const float4 q1 = swp ? Rp[uA] : R0[uA + P], q2 = swp ? R0[uA + P] : Rp[uA];
+          const float4 n1 = R0[o_n1], n2 = R0[o_n2];
+          const float4 p1 = R0[o_p1], p2 = R0[o_p2];
+          ownA = c0A;
+          ownB = swp ? q2 : q1;
+          ayp = swp ? q1 : q2;
+          bxm = swp ? n2 : n1;
+          axp = swp ? n1 : n2;
+          pvA = swp ? p2 : p1;
+          pvB = swp ? p1 : p2;
+          bym = prevB;
+          cmA = ownA;  // carried to the next position: row r becomes row r-1, A(r+1) becomes A(r)
+          cmB = ownB;
+          c0A = ayp;
         } else {
           ownA = RA[L - 1][s1];
           ownB = RB[L - 1][s1];
@@ -415,8 +433,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           bym = RB[L - 1][s2];
           ayp = RA[L - 1][s0];
           if (L == 2) {
-            pvA = Rm[uA];
-            pvB = Rm[uA + P];
+            pvA = prevA;
+            pvB = prevB;
           } else {
             pvA = RA[L - 2][s2];
             pvB = RB[L - 2][s2];
@@ -462,7 +480,6 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       i_done = i;
       // row r-1 has been read for the last time: refill its slot with row r - 1 + NSLOT
       if (tid == 0 && i >= 1) issue_next();
-      slot_m1 = slot_0;
       slot_0 = slot_p1;
       slot_p1 = slot_p1 + 1 == NSLOT ? 0 : slot_p1 + 1;
       if (slot_p1 == 0) wait_par ^= 1u;
