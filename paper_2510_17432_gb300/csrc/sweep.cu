@@ -299,10 +299,6 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   for (int l = 0; l < K; ++l)
 #pragma unroll
     for (int s = 0; s < 3; ++s) RA[l][s] = RB[l][s] = zero;
-  float2 dh[K];  // 2 D of rows r, r-1, .., r-K+1 (disordered lattices)
-#pragma unroll
-  for (int l = 0; l < K; ++l) dh[l] = make_float2(0.f, 0.f);
-  float2 dn1 = diag_row(0), dn2 = diag_row(1);
   float2 acc2[NV];  // packed halves of the NV sums (level L: [4(L-1), 4L))
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc2[v] = make_float2(0.f, 0.f);
@@ -389,21 +385,12 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       const float4* R0 = ring + slot_0 * SU + P;
       const float4* Rp = ring + slot_p1 * SU + P;
       // x-neighbours of levels 1 .. K-1 written at the previous position, loaded before this
-      // position writes any exchange row (the compiler cannot tell the two parities apart)
+      // position writes the exchange row of the level before (the compiler cannot tell the two
+      // parities apart): level 1's right away, the others once level 1 has been stored
       float4 xbm[K], xap[K];
-#pragma unroll
-      for (int L = 2; L <= K; ++L) {
-        const float4* Xin = xb + ((L - 2) * 2 + ((i - 1) & 1)) * XU;
-        xbm[L - 1] = Xin[wB - P];
-        xap[L - 1] = Xin[wA + P];
-      }
-      if (HAS_DIAG) {
-#pragma unroll
-        for (int l = K - 1; l > 0; --l) dh[l] = dh[l - 1];
-        dh[0] = dn1;
-        dn1 = dn2;
-        dn2 = diag_row(i + 2);
-      }
+      const float4* Xprev = xb + ((i - 1) & 1) * XU;  // level l at + 2 (l - 1) XU
+      xbm[1] = Xprev[wB - P];
+      xap[1] = Xprev[wA + P];
       const float4 prevA = cmA, prevB = cmB;  // level-0 row r-1 of this cell
 #pragma unroll
       for (int L = 1; L <= K; ++L) {
@@ -440,7 +427,10 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
             pvB = RB[L - 2][s2];
           }
         }
-        const float dA = HAS_DIAG ? dh[L - 1].x : a.dc2, dB = HAS_DIAG ? dh[L - 1].y : a.dc2;
+        // disordered lattices: 2 D of this level's row (read by K levels at consecutive
+        // positions, so L1 serves all but the first)
+        const float2 dl = diag_row(iq);
+        const float dA = dl.x, dB = dl.y;
         float4 nA = level_update(dA, ownA, th, ownB, bxm, bym, pvA);
         float4 nB = level_update(dB, ownB, th, ownA, axp, ayp, pvB);
         if (OPEN && (ghx || iq < v_lo || iq > v_hi)) {
@@ -453,6 +443,13 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           float4* Xout = xb + ((L - 1) * 2 + (i & 1)) * XU;
           Xout[wA] = nA;
           Xout[wB] = nB;
+        }
+        if (L == 1) {
+#pragma unroll
+          for (int l = 2; l < K; ++l) {
+            xbm[l] = Xprev[2 * (l - 1) * XU + wB - P];
+            xap[l] = Xprev[2 * (l - 1) * XU + wA + P];
+          }
         }
         if (intx && (unsigned)(iq - H) < (unsigned)ny) {
           if (L == K - 1) {
