@@ -57,9 +57,10 @@ struct Cfg {
   __host__ __device__ static int slot_units(int P) { return (4 * NT + 2 * P + 7) & ~7; }
   // exchange row: [A plane: NT units][P zero][B plane: NT units]
   __host__ __device__ static int xrow_units(int P) { return 2 * NT + P; }
-  static size_t smem(int P) {
+  // + disordered lattices: a thread-private ring of 2 D for the last 4 rows ([4][NT] float2)
+  static size_t smem(int P, bool diag) {
     return (size_t)BAR_BYTES + 16 * ((size_t)NSLOT * slot_units(P) + (size_t)2 * (K - 1) * xrow_units(P)) +
-           8 * (size_t)(NT / 32) * P * NV;
+           8 * (size_t)(NT / 32) * P * NV + (diag ? (size_t)8 * 4 * NT : 0);
   }
 };
 
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   float4* ring = reinterpret_cast<float4*>(smraw + C::BAR_BYTES);  // [NSLOT][SU]
   float4* xb = ring + NSLOT * SU;                                   // [K-1][2][XU]
   double* red = reinterpret_cast<double*>(xb + 2 * (K - 1) * XU);   // [warps][P][NV]
+  float2* dring = reinterpret_cast<float2*>(red + (NT / 32) * P * NV);  // [4][NT] (disorder only)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 
@@ -366,6 +368,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   int slot_0 = 0, slot_p1 = 1 % NSLOT;
   uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
 
+  // disordered lattices: 2 D of row r in flight, stored into the ring at position r
+  float2 dq0 = diag_row(0);
   bool timed_out = !mbar_wait(smem_u32(bars + 0), 0);  // this thread's waits; OR-reduced per position
   // level-0 values carried from position to position: A(r) (loaded as A(x, r+1) one position
   // earlier), A(r-1), B(r-1) (this thread's own cell); row r0 - 1 stands in as row r0
@@ -392,6 +396,10 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       xbm[1] = Xprev[wB - P];
       xap[1] = Xprev[wA + P];
       const float4 prevA = cmA, prevB = cmB;  // level-0 row r-1 of this cell
+      if (HAS_DIAG) {
+        dring[(i & 3) * NT + tid] = dq0;
+        dq0 = diag_row(i + 1);
+      }
 #pragma unroll
       for (int L = 1; L <= K; ++L) {
         const int iq = i - (L - 1);  // local row of this level
@@ -427,9 +435,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
             pvB = RB[L - 2][s2];
           }
         }
-        // disordered lattices: 2 D of this level's row (read by K levels at consecutive
-        // positions, so L1 serves all but the first)
-        const float2 dl = diag_row(iq);
+        // disordered lattices: 2 D of this level's row from the thread's own ring
+        const float2 dl = HAS_DIAG ? dring[(iq & 3) * NT + tid] : make_float2(a.dc2, a.dc2);
         const float dA = dl.x, dB = dl.y;
         float4 nA = level_update(dA, ownA, th, ownB, bxm, bym, pvA);
         float4 nB = level_update(dB, ownB, th, ownA, axp, ayp, pvB);
@@ -532,7 +539,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
 template <int NT, int K, int NSLOT, bool D, bool O>
 static cudaError_t set_sweep_smem() {
   return cudaFuncSetAttribute(sweep::k_sweep_moments<NT, K, NSLOT, D, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sweep::Cfg<NT, K, NSLOT>::smem(16));
+                              (int)sweep::Cfg<NT, K, NSLOT>::smem(16, true));
 }
 
 template <int NT, int K, int NSLOT>
@@ -580,7 +587,7 @@ static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurrence
   static int per_sm = 0;
   if (per_sm == 0) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_moments<NT, K, NSLOT, false, false>, NT,
-                                                      Cf::smem(4)) != cudaSuccess || per_sm < 1) {
+                                                      Cf::smem(4, false)) != cudaSuccess || per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
@@ -613,7 +620,7 @@ static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurrence
   a.counter = ra.counter;
   const bool open = !(a.pbc_x && a.pbc_y);
   const dim3 gr((unsigned)grid), bl(NT);
-  const size_t sm = Cf::smem(a.P);
+  const size_t sm = Cf::smem(a.P, a.diag != nullptr);
   if (a.diag) {
     if (open) k_sweep_moments<NT, K, NSLOT, true, true><<<gr, bl, sm, ctx->stream>>>(a);
     else k_sweep_moments<NT, K, NSLOT, true, false><<<gr, bl, sm, ctx->stream>>>(a);
