@@ -86,7 +86,7 @@ def parse():
     p.add_argument("--no-sequential", action="store_true", help="skip the sequential-form comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--fusion", type=int, default=5,
+    p.add_argument("--fusion", type=int, default=8,
                    help="moment-pass fusion mode: 0 = one step per pass, 1 = 4-step tiles, 2 = 2-step tiles, "
                         "3/4 = 2-step row sweep, 5/6 = 4-step row sweep, 7 = 2-step sweep (K-step code), "
                         "8/9/10 = 4-step register sweep (128/192/256 threads), -1 = autotuned")

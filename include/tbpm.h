@@ -174,7 +174,7 @@ int64_t tbpm_launch_count(const tbpm_ctx* ctx);
  * register-resident sweep (each thread keeps the recurrence levels of its cell in registers and
  * exchanges only the x-neighbours through shared memory, one barrier per row; rows of phi_n and
  * phi_{n-1} arrive by TMA bulk copies; 128-, 192- and 256-thread CTAs; a lattice narrower than
- * one band takes mode 5).  Default 5.  -1 = the fastest of modes 0, 4, 5 and 8 timed on the
+ * one band takes mode 5).  Default 8.  -1 = the fastest of modes 0, 4, 5 and 8 timed on the
  * request's lattice shape.  Results of different modes agree within the complex64 tolerance, not
  * bit for bit; each mode is deterministic.  Modes outside -1..10 are rejected with TBPM_EINVAL. */
 int tbpm_set_fusion(tbpm_ctx* ctx, int mode);

@@ -155,7 +155,7 @@ struct tbpm_ctx {
       ws_energies, ws_recon, ws_phi2[2], ws_fused_partials, ws_qe, ws_qe_coef, ws_xdot, ws_jpsi, ws_ec, ws_fermi, ws_blk, ws_blk_coef;
   // time blocks buffer up to 32 Chebyshev vectors and flush them into the accumulators at once
   bool buffer_blocks = true;
-  int fusion = 5;  // temporal-fusion mode of the moment pass (5 = four-step row sweep; -1 = autotuned)
+  int fusion = 8;  // temporal-fusion mode of the moment pass (8 = four-step register sweep; -1 = autotuned)
   // autotuned fusion modes: key (kind, Lx, Ly, Lz, pbc bits, path, Spad, precision, disorder) -> mode
   std::vector<std::pair<std::vector<int64_t>, int>> fusion_choice;
   std::vector<std::pair<int, double>> fusion_timings;  // last autotune: (mode, ms per step)

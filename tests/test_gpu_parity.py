@@ -321,7 +321,7 @@ def test_fused_passes_match_unfused_and_oracle(capi, ctx, name, spec, S, M, mode
     mf = gpu_moments(capi, ctx, lat, S, M, 0)
     capi.tbpm_set_fusion(ctx, 0)
     mu = gpu_moments(capi, ctx, lat, S, M, 0)
-    capi.tbpm_set_fusion(ctx, 5)
+    capi.tbpm_set_fusion(ctx, 8)
     assert np.max(np.abs(mf - mu)) <= 1e-6
     psi = oprop.random_phase_states(ol, 3, S)
     for s in (0, S - 1):
@@ -339,7 +339,7 @@ def test_fusion_autotune_picks_a_timed_mode_and_matches(capi, ctx):
     rep = capi.tbpm_fusion_report(ctx)
     capi.tbpm_set_fusion(ctx, 0)
     m0 = gpu_moments(capi, ctx, lat, 8, 160, 0)
-    capi.tbpm_set_fusion(ctx, 5)
+    capi.tbpm_set_fusion(ctx, 8)
     assert set(rep) == {0, 4, 5, 8} and all(v > 0 for v in rep.values())
     assert np.max(np.abs(ma - m0)) <= 1e-6
     capi.tbpm_lattice_destroy(lat)
@@ -400,7 +400,7 @@ def test_headline_moment_counts_match_oracle(capi, ctx, name, spec, S, M, check,
     try:
         mu = gpu_moments(capi, ctx, lat, S, M, 0, seed=2)
     finally:
-        capi.tbpm_set_fusion(ctx, 5)
+        capi.tbpm_set_fusion(ctx, 8)
     capi.tbpm_lattice_destroy(lat)
     for s in check:
         ref = oracle_moments_cached(name, ol, 2, s, M)
