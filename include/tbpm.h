@@ -388,6 +388,14 @@ int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_re
 int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int direction,
                       const double* energies, int64_t n_energies, double* C, double* sigma);
 
+/* tbpm_conductivity that also returns the overlaps that normalise C: overlap (may be NULL) =
+ * host [S][n_energies][2], <psi|Psi(E)> of every state and energy exactly as the device computed
+ * and used it, so that C(t,E) x |<psi|Psi(E)>| recovers the un-normalised correlation
+ * <J psi(t)|J Psi(E)> of Eq. dc_corr.  Same arguments, errors and device memory otherwise. */
+int tbpm_conductivity_overlap(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int direction,
+                              const double* energies, int64_t n_energies, double* C, double* sigma,
+                              double* overlap);
+
 /* Fermi-Dirac operator (the operators f(H), f^{1/2}(H) of the OC, DP and CD sections), hbar = k_B = 1:
  *   f(E) = 1/(1 + e^{(E - mu)/kT}); out = f(H) psi (sqrt_f = 0) or f(H)^{1/2} psi (sqrt_f != 0) for
  *   the request's states, as the Chebyshev series sum_n a_n T_n(H~) psi with

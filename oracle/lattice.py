@@ -104,11 +104,16 @@ def neighbour_table(kind: int, L, pbc) -> np.ndarray:
     return np.stack(cols, axis=1).astype(np.int64)
 
 
-def disorder_potential(seed: int, W: float, n_full: int) -> np.ndarray:
-    """Anderson on-site energies V_i, uniform on [-W/2, W/2), FP64, by full site index."""
-    u = draw_u32(seed, np.arange(n_full, dtype=np.uint64), STREAM_DISORDER).astype(np.float64)
+def disorder_at(seed: int, W: float, full_idx) -> np.ndarray:
+    """Anderson on-site energies V_i of the listed full site indices, uniform on [-W/2, W/2), FP64."""
+    u = draw_u32(seed, np.asarray(full_idx, dtype=np.uint64), STREAM_DISORDER).astype(np.float64)
     frac = np.floor(u / 256.0) * 2.0 ** -24          # (u >> 8) * 2^-24, exact
     return W * (frac - 0.5)
+
+
+def disorder_potential(seed: int, W: float, n_full: int) -> np.ndarray:
+    """Anderson on-site energies V_i, uniform on [-W/2, W/2), FP64, by full site index."""
+    return disorder_at(seed, W, np.arange(n_full, dtype=np.uint64))
 
 
 def vacancy_threshold(p: float) -> int:
@@ -272,6 +277,57 @@ def build_lattice(kind: int, L, t: float, W: float = 0.0, vacancy_frac: float = 
     half = (1.0 + BOUND_MARGIN) * (E_max - E_min) / 2.0
     return Lattice(kind, L, pbc, float(t), float(W), float(vacancy_frac), int(seed), n_full,
                    nbr, active, compact, V, H, degree, E_min, E_max, H0, half, float(cutoff), float(decay))
+
+
+def honeycomb_window(L, center, radius: int, t: float, W: float, seed: int, E_min: float, E_max: float):
+    """The cells of a periodic honeycomb lattice within `radius` cells of `center` = (x, y) in
+    x and in y, as a lattice of their own: the global site numbering (for the disorder draw),
+    nearest-neighbour bonds between window sites only, and the spectral bounds E_min, E_max of
+    the WHOLE lattice (so that H~ = (H - H0)/|H| is the whole lattice's rescaling).
+
+    A state supported on the centre cell reaches at most n cells in x and in y after n
+    applications of H, so T_n(H~) applied to it, and its moments <r|T_n(H~)|r>, agree with the
+    whole lattice's for n <= radius: a way to check any lattice, however large, on sampled sites.
+    Returns (lattice, local index of A(center), local index of B(center), full index of every
+    window site)."""
+    Lx, Ly = int(L[0]), int(L[1])
+    if 2 * radius + 1 > min(Lx, Ly):
+        raise ValueError("window wraps onto itself")
+    w = 2 * radius + 1
+    dx, dy = np.meshgrid(np.arange(-radius, radius + 1), np.arange(-radius, radius + 1), indexing="xy")
+    gx = (center[0] + dx.ravel()) % Lx
+    gy = (center[1] + dy.ravel()) % Ly
+    cells = w * w
+    full = np.empty(2 * cells, dtype=np.int64)
+    full[0::2] = 2 * (gy * Lx + gx)
+    full[1::2] = full[0::2] + 1
+    lx = dx.ravel() + radius
+    ly = dy.ravel() + radius
+
+    def cell(ix, iy):
+        ok = (ix >= 0) & (ix < w) & (iy >= 0) & (iy < w)
+        return np.where(ok, iy * w + ix, -1)
+
+    a = 2 * np.arange(cells)
+    rows, cols = [], []
+    for ddx, ddy in ((0, 0), (-1, 0), (0, -1)):        # A(x,y) - B(x+ddx, y+ddy)
+        c = cell(lx + ddx, ly + ddy)
+        keep = c >= 0
+        rows += [a[keep], 2 * c[keep] + 1]
+        cols += [2 * c[keep] + 1, a[keep]]
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    n = 2 * cells
+    V = disorder_at(seed, W, full) if W != 0.0 else np.zeros(n)
+    H = (sp.coo_matrix((np.full(rows.size, float(t)), (rows, cols)), shape=(n, n)).tocsr() + sp.diags(V)).tocsr()
+    H.sum_duplicates()
+    H0 = (E_max + E_min) / 2.0
+    half = (1.0 + BOUND_MARGIN) * (E_max - E_min) / 2.0
+    lat = Lattice(HONEYCOMB, (w, w, 1), (False, False, True), float(t), float(W), 0.0, int(seed), n,
+                  None, np.ones(n, dtype=bool), np.arange(n, dtype=np.int64), V, H,
+                  np.bincount(rows, minlength=n).astype(np.int64), float(E_min), float(E_max), H0, half)
+    centre = radius * w + radius
+    return lat, 2 * centre, 2 * centre + 1, full
 
 
 def rescaled_apply(lat: Lattice, x: np.ndarray) -> np.ndarray:

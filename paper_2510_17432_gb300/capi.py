@@ -106,6 +106,7 @@ def load():
         "tbpm_server_stats": (C.c_int, [_P, C.POINTER(C.c_int64)]),
         "tbpm_quasi_eigenstates": (C.c_int, [_P, _P, C.POINTER(Request), _P, C.c_int64, _P]),
         "tbpm_conductivity": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, _P, C.c_int64, _P, _P]),
+        "tbpm_conductivity_overlap": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, _P, C.c_int64, _P, _P, _P]),
         "tbpm_fermi_apply": (C.c_int, [_P, _P, C.POINTER(Request), C.c_double, C.c_double, C.c_int, _P]),
         "tbpm_optical_conductivity": (C.c_int, [_P, _P, C.POINTER(Request), C.c_int, C.c_int, C.c_double,
                                                 C.c_double, C.c_double, C.c_int64, _P, _P]),
@@ -136,7 +137,8 @@ def exported_symbols():
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
             "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
-            "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_fermi_apply",
+            "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_conductivity_overlap",
+            "tbpm_fermi_apply",
             "tbpm_optical_conductivity", "tbpm_polarization", "tbpm_charge_density", "tbpm_set_pass_states", "tbpm_fusion_report", "tbpm_set_graphs", "tbpm_set_block_buffering", "tbpm_moment_step_noalloc", "tbpm_truncation_order", "tbpm_block_counts", "tbpm_block_opt",
             "tbpm_block_autotune", "tbpm_server_create", "tbpm_server_destroy", "tbpm_submit", "tbpm_wait",
             "tbpm_server_stats"]
@@ -319,6 +321,14 @@ def tbpm_conductivity(ctx, lat, req: Request, direction: int, energies: np.ndarr
     e = np.ascontiguousarray(energies, dtype=np.float64)
     _check(load().tbpm_conductivity(ctx, lat, C.byref(req), int(direction), _host_ptr(e), int(e.size),
                                     _host_ptr(C_out), _host_ptr(sigma)))
+
+
+def tbpm_conductivity_overlap(ctx, lat, req: Request, direction: int, energies: np.ndarray,
+                              C_out: np.ndarray | None, sigma: np.ndarray, overlap: np.ndarray | None):
+    """As tbpm_conductivity; overlap: [S][n_energies] complex128 (<psi|Psi(E)> as the device used it) or None."""
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    _check(load().tbpm_conductivity_overlap(ctx, lat, C.byref(req), int(direction), _host_ptr(e), int(e.size),
+                                            _host_ptr(C_out), _host_ptr(sigma), _host_ptr(overlap)))
 
 
 def tbpm_fermi_apply(ctx, lat, req: Request, mu: float, kT: float, sqrt_f: bool, out: np.ndarray):

@@ -2349,6 +2349,11 @@ int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_
 
 int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int direction,
                       const double* energies, int64_t nE, double* C, double* sigma) {
+  return tbpm_conductivity_overlap(ctx, lat_c, req, direction, energies, nE, C, sigma, nullptr);
+}
+
+int tbpm_conductivity_overlap(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int direction,
+                              const double* energies, int64_t nE, double* C, double* sigma, double* overlap) {
   clear_error();
   if (!ctx || !energies || !sigma || nE < 1 || nE > 4096) {
     set_error("tbpm_conductivity: invalid argument");
@@ -2369,6 +2374,9 @@ int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
     TBPM_CK(cudaMemcpyAsync(C, d_C, sizeof(double) * 2 * rows * (req->n_steps + 1), cudaMemcpyDeviceToHost,
                             ctx->stream));
   TBPM_CK(cudaMemcpyAsync(sigma, d_sigma, sizeof(double) * rows, cudaMemcpyDeviceToHost, ctx->stream));
+  // <psi|Psi(E)> of every state and energy, [Spad][nE][2] at the head of the EC workspace
+  if (overlap)
+    TBPM_CK(cudaMemcpyAsync(overlap, ctx->ws_ec.p, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, ctx->stream));
   TBPM_CK(cudaStreamSynchronize(ctx->stream));
   return TBPM_OK;
 }

@@ -406,3 +406,43 @@ def test_headline_moment_counts_match_oracle(capi, ctx, name, spec, S, M, check,
         ref = oracle_moments_cached(name, ol, 2, s, M)
         err = np.max(np.abs(mu[s] - ref)) / abs(ref[0])
         assert err <= 1e-5, (s, err)
+
+
+# ---------------------------------------------------------------- the 1.015e9-site lattice, sampled
+
+def test_largest_lattice_sampled_sites_match_oracle_windows(capi, ctx):
+    """Honeycomb 22528 x 22528 cells (1,015,021,568 sites), t = -2.7 eV, V in [-0.5, 0.5) eV: the
+    largest workload, in the default fused pass with disorder, at byte offsets far beyond 2^32.
+    Its Gershgorin bounds equal the oracle's (from the disorder range over all sites, stored by
+    tests/golden/make_disorder_range.py), and the LDOS moments of four sites (a corner whose light
+    cone wraps both periodic directions, the last site, the centre, a band edge of the sweep)
+    equal those of the oracle on a window of the lattice around each site, exact while the
+    moment index stays below the window's radius."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "honeycomb22528_W1_disorder_range.json")) as f:
+        rng = json.load(f)
+    Lx = Ly = 22528
+    t, W, seed = -2.7, 1.0, 0x7B1A5
+    assert rng["lattice"]["L"] == [Lx, Ly] and rng["lattice"]["W"] == W and rng["lattice"]["seed"] == seed
+    E_min = rng["V_min"] - 3 * abs(t)
+    E_max = rng["V_max"] + 3 * abs(t)
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(1, (Lx, Ly), t=t, W=W, seed=seed))
+    try:
+        info = capi.tbpm_lattice_info(lat)
+        assert info.n_sites == 2 * Lx * Ly
+        assert (info.E_min, info.E_max) == (E_min, E_max)
+        cells = [(0, 0, 0), (Lx - 1, Ly - 1, 1), (Lx // 2, Ly // 2 - 1, 0), (60 * 187, 7509, 1)]
+        sites = np.array([2 * (y * Lx + x) + s for x, y, s in cells], np.int64)
+        M = 256
+        mu = gpu_moments(capi, ctx, lat, 4, M, 0, sites=sites)
+    finally:
+        capi.tbpm_lattice_destroy(lat)
+    for k, (x, y, s) in enumerate(cells):
+        wl, ia, ib, full = olat.honeycomb_window((Lx, Ly), (x, y), M, t, W, seed, E_min, E_max)
+        local = ia if s == 0 else ib
+        assert full[local] == sites[k]
+        e = np.zeros(wl.n, np.complex128)
+        e[local] = 1.0
+        ref = oprop.moments(wl, e, e, M)
+        assert np.max(np.abs(mu[k] - ref)) <= 1e-5, (k, np.max(np.abs(mu[k] - ref)))
