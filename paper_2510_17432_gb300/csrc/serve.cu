@@ -10,6 +10,13 @@
 // the batch: results are bit-identical alone and in any mix.  A request that has produced its
 // M moments leaves the batch, its DOS is reconstructed (Jackson kernel) and copied to pinned
 // host memory, and its memory is released for the next admission.
+//
+// Requests large enough to fill the GPU with one step on their own (at least kLaneSiteStates
+// site-states) do not join the batched kernel: each gets a direct lane, a context of its own
+// whose stream runs the direct path's moment passes (the fused sweep where it applies, the
+// one-step stencil or ELL pass otherwise) and the reconstruction, overlapping the batch and the
+// other lanes on the device.  Which way a request goes depends only on the request, and both
+// ways are deterministic, so a result is the same alone and in any mix.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -28,6 +35,7 @@
 namespace tbpm {
 
 constexpr int kServeTU = 32 * kThreads;  // largest tile (32 units per thread, FP32 partial sums)
+constexpr int64_t kLaneSiteStates = 1 << 21;  // full sites x padded states of a direct-lane request
 
 // Units per tile of a request with `units` thread units: 32 per thread (the per-tile reduction
 // and bookkeeping amortised) unless the request would get fewer than 64 tiles, then fewer.
@@ -306,6 +314,8 @@ struct ServeJob {
   int S = 1, Spad = 1, spt = 1, P = 1, logP = 0;
   size_t elem = 8, state_bytes = 0;
   int64_t n_tiles = 0;
+  bool lane = false;            // direct lane: own context and stream, the direct path's kernels
+  tbpm_ctx* lane_ctx = nullptr;
 };
 
 int ilog2i(int v) {
@@ -343,7 +353,10 @@ struct tbpm_server {
 
 static size_t job_footprint(const ServeJob* j, int64_t n_sites, int64_t n_full, int z) {
   size_t lat = (size_t)n_sites * (8 + 4 + 8) + (j->ldesc.vacancy_frac > 0 ? (size_t)n_full * 8 + (size_t)n_sites * (8 + 4 * z) : 0);
-  return lat + 2 * j->state_bytes + (size_t)j->n_tiles * j->Spad * 3 * 8 + (size_t)j->Spad * j->req.n_moments * 16 +
+  // a direct lane holds up to four state blocks (the fused passes write a second pair) and the
+  // partial sums of its passes
+  const size_t states = j->lane ? 4 * j->state_bytes + (16u << 20) : 2 * j->state_bytes;
+  return lat + states + (size_t)j->n_tiles * j->Spad * 3 * 8 + (size_t)j->Spad * j->req.n_moments * 16 +
          j->energies.size() * 8 * (1 + j->S) + 4096;
 }
 
@@ -386,7 +399,7 @@ static void fail_job(tbpm_server* srv, ServeJob* j, int code) {
 }
 
 static void release_job(tbpm_server* srv, ServeJob* j) {
-  cudaStream_t st = srv->ctx->stream;
+  cudaStream_t st = j->lane_ctx ? j->lane_ctx->stream : srv->ctx->stream;
   void* ps[] = {j->buf[0], j->buf[1], j->mu, j->tile_partials, j->counter, j->dE, j->dD};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
@@ -401,10 +414,54 @@ static void release_job(tbpm_server* srv, ServeJob* j) {
     cudaEventDestroy(j->done_ev);
     j->done_ev = nullptr;
   }
+  if (j->lane_ctx) {  // waits for the lane's stream, frees its workspaces
+    srv->launches += tbpm_launch_count(j->lane_ctx);
+    tbpm_destroy(j->lane_ctx);
+    j->lane_ctx = nullptr;
+  }
+}
+
+// A direct lane: lattice (builder stream), buffers, then the whole request -- moment passes,
+// reconstruction, copy of the DOS to pinned host memory -- enqueued on the lane's own stream.
+static int setup_lane_job(tbpm_server* srv, ServeJob* j) {
+  TBPM_TRY(tbpm_create(&j->lane_ctx, srv->ctx->device));
+  tbpm_ctx* c = j->lane_ctx;
+  TBPM_TRY(tbpm_lattice_create(srv->builder, &j->ldesc, &j->lat));
+  tbpm_lattice* lat = j->lat;
+  if (j->req.precision == TBPM_C128) TBPM_TRY(lattice_ensure_d64(lat));
+  TBPM_CK(cudaStreamSynchronize(srv->builder->stream));
+  cudaStream_t st = c->stream;
+  const int64_t M = j->req.n_moments, nE = (int64_t)j->energies.size();
+  auto alloc = [&](void** p, size_t bytes) -> int {
+    if (cudaMallocAsync(p, std::max<size_t>(bytes, 256), st) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("serving: device allocation of %zu bytes failed", bytes);
+      return TBPM_ENOMEM;
+    }
+    return TBPM_OK;
+  };
+  TBPM_TRY(alloc((void**)&j->mu, sizeof(double) * 2 * (size_t)M * j->Spad));
+  TBPM_TRY(alloc((void**)&j->dE, sizeof(double) * nE));
+  TBPM_TRY(alloc((void**)&j->dD, sizeof(double) * nE * j->S));
+  TBPM_CK(cudaMemcpyAsync(j->dE, j->energies.data(), sizeof(double) * nE, cudaMemcpyHostToDevice, st));
+  TBPM_CK(cudaEventCreateWithFlags(&j->done_ev, cudaEventDisableTiming));
+  tbpm_request rq = j->req;
+  rq.sites = j->sites.empty() ? nullptr : j->sites.data();
+  TBPM_TRY(tbpm_moments_device(c, lat, &rq, j->mu));
+  int r;
+  if (srv->cfg.recon == TBPM_RECON_TENSOR)
+    r = launch_dos_jackson_tensor_async(c, j->mu, j->S, (int)M, j->dE, nE, lat->H0, lat->half, j->dD, j->h_err);
+  else
+    r = launch_dos_jackson_fp64(c, j->mu, j->S, (int)M, j->dE, nE, lat->H0, lat->half, j->dD);
+  TBPM_TRY(r);
+  TBPM_CK(cudaMemcpyAsync(j->hD, j->dD, sizeof(double) * nE * j->S, cudaMemcpyDeviceToHost, st));
+  TBPM_CK(cudaEventRecord(j->done_ev, st));
+  return TBPM_OK;
 }
 
 // Device set-up of an admitted job: lattice (builder stream), buffers, initial states.
 static int setup_job(tbpm_server* srv, ServeJob* j) {
+  if (j->lane) return setup_lane_job(srv, j);
   tbpm_ctx* ctx = srv->ctx;
   TBPM_TRY(tbpm_lattice_create(srv->builder, &j->ldesc, &j->lat));
   tbpm_lattice* lat = j->lat;
@@ -549,6 +606,9 @@ static void scheduler(tbpm_server* srv) {
         release_job(srv, j);
         srv->used -= j->footprint;
         srv->cv_done.notify_all();
+      } else if (j->lane) {  // already enqueued whole on its own stream
+        j->status = JOB_FINISHING;
+        srv->finishing.push_back(j);
       } else {
         srv->active.push_back(j);
         dirty = true;
@@ -755,8 +815,9 @@ int tbpm_submit(tbpm_server* srv, const tbpm_lattice_desc* ldesc, const tbpm_req
   const int64_t nf = full_sites(j->ldesc);
   const int z = ldesc->kind == TBPM_SQUARE ? 4 : ldesc->kind == TBPM_HONEYCOMB ? 3 : 6;
   j->state_bytes = (size_t)nf * j->Spad * j->elem;
+  j->lane = nf * j->Spad >= kLaneSiteStates;
   const int tu = serve_tile_units(nf * j->P);
-  j->n_tiles = (nf * j->P + tu - 1) / tu + (ldesc->L[1] * (ldesc->kind == TBPM_CUBIC ? ldesc->L[2] : 1));
+  j->n_tiles = j->lane ? 0 : (nf * j->P + tu - 1) / tu + (ldesc->L[1] * (ldesc->kind == TBPM_CUBIC ? ldesc->L[2] : 1));
   j->footprint = job_footprint(j, nf, nf, z);
   if (cudaMallocHost((void**)&j->hD, sizeof(double) * n_energies * j->S) != cudaSuccess ||
       cudaMallocHost((void**)&j->h_err, sizeof(int)) != cudaSuccess) {

@@ -1,6 +1,7 @@
 """Serving: continuous batching of DOS/LDOS requests (tbpm_submit / tbpm_wait).
 
-Checks that a served result equals the direct API's result within the path tolerance, that a
+Checks that every served result matches the oracle, that a batched result equals the direct API's
+result within the path tolerance and a direct-lane result equals it bit for bit, that a
 request's result is bit-identical alone and inside a mix of other requests, that admission
 follows the HBM budget, that requests submitted while others run join the batch and finish
 first when they are short, and that waits time out and servers cancel cleanly.
@@ -45,6 +46,15 @@ CASES = [
     ("square_ldos_c64", dict(kind=0, L=(300, 3), t=1.0, W=1.0, seed=7),
      dict(sites=[0, 17, 599, 899], precision=0, n_moments=128)),
     ("honey_long_lines", dict(kind=1, L=(1500, 4), t=-2.7, W=1.0, seed=8), dict(n_states=16, precision=0, n_moments=64)),
+]
+
+
+# requests of at least 2^21 site-states run in a direct lane (own stream, the direct path's kernels)
+LANE_CASES = [
+    ("square_lane_S1", dict(kind=0, L=(1500, 1500), t=1.0, W=1.0, seed=21), dict(n_states=1, precision=0, n_moments=64)),
+    ("honey_lane_ldos", dict(kind=1, L=(768, 768), t=-2.7, W=0.5, seed=22),
+     dict(sites=[5, 100000, 1179647], precision=0, n_moments=96)),
+    ("honey_lane_S8_fused", dict(kind=1, L=(400, 330), t=-2.7, W=0.0, seed=23), dict(n_states=8, precision=0, n_moments=160)),
 ]
 
 
@@ -101,7 +111,7 @@ def test_served_results_match_oracle(capi, ctx, recon):
     srv = capi.tbpm_server_create(ctx, recon=capi.RECON_TENSOR if recon == "tensor" else capi.RECON_FP64)
     try:
         tickets = [(name, lk, rk, capi.tbpm_submit(srv, capi.lattice_desc(**lk), capi.request(**rk), E))
-                   for name, lk, rk in CASES]
+                   for name, lk, rk in CASES + LANE_CASES]
         for name, lk, rk, t in tickets:
             S = len(rk["sites"]) if "sites" in rk else rk["n_states"]
             D = np.zeros((S, E.size))
@@ -111,6 +121,26 @@ def test_served_results_match_oracle(capi, ctx, recon):
             for s in range(S):
                 err = np.max(np.abs(D[s] - ref[s])) / np.max(np.abs(ref[s]))
                 assert err <= tol, (name, s, err)
+    finally:
+        capi.tbpm_server_destroy(srv)
+
+
+def test_lane_results_equal_the_direct_api_bit_for_bit(capi, ctx):
+    """A direct-lane request runs the same kernels as tbpm_dos on its own stream: its DOS equals
+    the direct call's bit for bit, also while batched requests and other lanes run beside it."""
+    E = energies()
+    srv = capi.tbpm_server_create(ctx)
+    try:
+        tickets = [(lk, rk, capi.tbpm_submit(srv, capi.lattice_desc(**lk), capi.request(**rk), E))
+                   for _, lk, rk in LANE_CASES + CASES[:3]]
+        for lk, rk, t in tickets[:len(LANE_CASES)]:
+            S = len(rk["sites"]) if "sites" in rk else rk["n_states"]
+            D = np.zeros((S, E.size))
+            capi.tbpm_wait(srv, t, D)
+            assert np.array_equal(D, direct_dos(capi, ctx, capi.lattice_desc(**lk), rk, E))
+        for lk, rk, t in tickets[len(LANE_CASES):]:
+            S = len(rk["sites"]) if "sites" in rk else rk["n_states"]
+            capi.tbpm_wait(srv, t, np.zeros((S, E.size)))
     finally:
         capi.tbpm_server_destroy(srv)
 
