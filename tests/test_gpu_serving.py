@@ -173,8 +173,9 @@ def test_short_requests_join_and_finish_first(capi, ctx):
     E = energies(64)
     srv = capi.tbpm_server_create(ctx)
     try:
-        long_t = capi.tbpm_submit(srv, capi.lattice_desc(1, (1024, 512), t=-2.7, W=0.0),
-                                  capi.request(n_states=8, precision=0, n_moments=4096), E)
+        # a direct-lane request of ~1.4e11 site-updates (a few hundred ms on the fused pass)
+        long_t = capi.tbpm_submit(srv, capi.lattice_desc(1, (2048, 1024), t=-2.7, W=0.0),
+                                  capi.request(n_states=8, precision=0, n_moments=8192), E)
         time.sleep(0.05)
         shorts = [capi.tbpm_submit(srv, capi.lattice_desc(0, (32, 32), t=1.0, W=1.0, seed=s),
                                    capi.request(n_states=1, precision=0, n_moments=64), E) for s in range(5)]
