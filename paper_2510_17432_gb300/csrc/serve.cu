@@ -21,6 +21,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -316,6 +317,9 @@ struct ServeJob {
   int64_t n_tiles = 0;
   bool lane = false;            // direct lane: own context and stream, the direct path's kernels
   tbpm_ctx* lane_ctx = nullptr;
+  std::thread lane_thread;      // enqueues the lane's work (may block on a full launch queue)
+  std::atomic<int> lane_state{0};  // 0 enqueueing, 1 enqueued, 2 failed
+  int lane_result = TBPM_OK;
 };
 
 int ilog2i(int v) {
@@ -335,7 +339,7 @@ struct tbpm_server {
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<ServeJob*> pending;
-  std::vector<ServeJob*> active, finishing;
+  std::vector<ServeJob*> active, finishing, lanes;
   std::unordered_map<uint64_t, ServeJob*> jobs;
   bool stop = false;
   uint64_t next_ticket = 1;
@@ -426,10 +430,9 @@ static void release_job(tbpm_server* srv, ServeJob* j) {
 static int setup_lane_job(tbpm_server* srv, ServeJob* j) {
   TBPM_TRY(tbpm_create(&j->lane_ctx, srv->ctx->device));
   tbpm_ctx* c = j->lane_ctx;
-  TBPM_TRY(tbpm_lattice_create(srv->builder, &j->ldesc, &j->lat));
+  TBPM_TRY(tbpm_lattice_create(c, &j->ldesc, &j->lat));
   tbpm_lattice* lat = j->lat;
   if (j->req.precision == TBPM_C128) TBPM_TRY(lattice_ensure_d64(lat));
-  TBPM_CK(cudaStreamSynchronize(srv->builder->stream));
   cudaStream_t st = c->stream;
   const int64_t M = j->req.n_moments, nE = (int64_t)j->energies.size();
   auto alloc = [&](void** p, size_t bytes) -> int {
@@ -572,6 +575,16 @@ static void scheduler(tbpm_server* srv) {
   cudaSetDevice(srv->ctx->device);
   bool dirty = true;
   const size_t depth = 4;
+  // a lane job's set-up and enqueue run on a thread of their own, so that the batch keeps going
+  auto start_lane = [srv](ServeJob* j) {
+    j->lane_thread = std::thread([srv, j] {
+      cudaSetDevice(srv->ctx->device);
+      const int r = setup_lane_job(srv, j);
+      if (r != TBPM_OK) j->message = tbpm_last_error();
+      j->lane_result = r;
+      j->lane_state.store(r == TBPM_OK ? 1 : 2);
+    });
+  };
   while (true) {
     std::vector<ServeJob*> admitted;
     {
@@ -593,12 +606,17 @@ static void scheduler(tbpm_server* srv) {
         j->t_admit = Clock::now();
         admitted.push_back(j);
       }
-      if (admitted.empty() && srv->active.empty() && srv->finishing.empty()) {
+      if (admitted.empty() && srv->active.empty() && srv->finishing.empty() && srv->lanes.empty()) {
         srv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         continue;
       }
     }
     for (ServeJob* j : admitted) {
+      if (j->lane) {
+        start_lane(j);
+        srv->lanes.push_back(j);
+        continue;
+      }
       int r = setup_job(srv, j);
       std::lock_guard<std::mutex> lk(srv->mu);
       if (r != TBPM_OK) {
@@ -606,9 +624,6 @@ static void scheduler(tbpm_server* srv) {
         release_job(srv, j);
         srv->used -= j->footprint;
         srv->cv_done.notify_all();
-      } else if (j->lane) {  // already enqueued whole on its own stream
-        j->status = JOB_FINISHING;
-        srv->finishing.push_back(j);
       } else {
         srv->active.push_back(j);
         dirty = true;
@@ -672,6 +687,36 @@ static void scheduler(tbpm_server* srv) {
       }
       srv->active.swap(still);
     }
+    // direct lanes: set-up failures and completed streams
+    {
+      std::vector<ServeJob*> keep;
+      for (ServeJob* j : srv->lanes) {
+        const int st = j->lane_state.load();
+        if (st == 0 || (st == 1 && cudaEventQuery(j->done_ev) != cudaSuccess)) {
+          keep.push_back(j);
+          continue;
+        }
+        j->lane_thread.join();
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (st == 2) {
+          j->result = j->lane_result;
+          j->status = JOB_DONE;
+          j->t_done = Clock::now();
+        } else {
+          j->t_done = Clock::now();
+          if (j->h_err && *j->h_err) {
+            j->result = TBPM_ETIMEOUT;
+            j->message = "tensor-core reconstruction: bounded wait expired";
+          }
+          j->status = JOB_DONE;
+          srv->completed++;
+        }
+        release_job(srv, j);
+        srv->used -= j->footprint;
+        srv->cv_done.notify_all();
+      }
+      srv->lanes.swap(keep);
+    }
     // completions
     std::vector<ServeJob*> left;
     for (ServeJob* j : srv->finishing) {
@@ -692,9 +737,12 @@ static void scheduler(tbpm_server* srv) {
       }
     }
     srv->finishing.swap(left);
-    if (srv->active.empty() && !srv->finishing.empty()) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (srv->active.empty() && (!srv->finishing.empty() || !srv->lanes.empty()))
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
-  // shutdown: cancel everything still queued or running
+  // shutdown: cancel everything still queued or running (a lane that is enqueued runs to its end)
+  for (ServeJob* j : srv->lanes)
+    if (j->lane_thread.joinable()) j->lane_thread.join();
   cudaStreamSynchronize(srv->ctx->stream);
   std::lock_guard<std::mutex> lk(srv->mu);
   for (ServeJob* j : srv->pending) {
@@ -702,7 +750,7 @@ static void scheduler(tbpm_server* srv) {
     j->status = JOB_DONE;
   }
   srv->pending.clear();
-  for (auto* v : {&srv->active, &srv->finishing}) {
+  for (auto* v : {&srv->active, &srv->finishing, &srv->lanes}) {
     for (ServeJob* j : *v) {
       release_job(srv, j);
       j->result = j->status == JOB_FINISHING ? TBPM_OK : TBPM_ECANCELLED;
@@ -898,7 +946,7 @@ int tbpm_server_stats(tbpm_server* srv, int64_t out[7]) {
   }
   std::lock_guard<std::mutex> lk(srv->mu);
   out[0] = (int64_t)srv->pending.size();
-  out[1] = (int64_t)srv->active.size();
+  out[1] = (int64_t)(srv->active.size() + srv->lanes.size());
   out[2] = srv->completed;
   out[3] = srv->launches;
   out[4] = (int64_t)srv->used;
