@@ -445,6 +445,8 @@ int tbpm_destroy(tbpm_ctx* ctx) {
     cudaEventDestroy(ph.b);
   }
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->queue_ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -1188,6 +1190,18 @@ int choose_fusion(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, con
   return TBPM_OK;
 }
 
+// Bounded launch queue (ctx->max_queue > 0, never while a graph is being captured): every 64
+// launches record an event and wait for the one recorded 64 launches before.
+void throttle_queue(tbpm_ctx* ctx, bool capturing) {
+  if (ctx->max_queue <= 0 || capturing) return;
+  if (++ctx->queue_count % 64 != 0) return;
+  const int k = (int)((ctx->queue_count / 64) & 1);
+  if (!ctx->queue_ev[k]) cudaEventCreateWithFlags(&ctx->queue_ev[k], cudaEventDisableTiming);
+  if (ctx->queue_live[k]) cudaEventSynchronize(ctx->queue_ev[k]);
+  cudaEventRecord(ctx->queue_ev[k], ctx->stream);
+  ctx->queue_live[k] = true;
+}
+
 // Moments of all Spad states into d_mu [Spad][M][2].
 int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan& pl, int64_t M,
                 double* d_mu) {
@@ -1211,6 +1225,7 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
     TBPM_TRY(ensure(ctx, ctx->ws_phi2[1], pl.state_bytes));
   }
   // the pass sequence: step n reads cur = phi_n and overwrites prev (phi_{n-1}) with phi_{n+1}
+  bool capturing = false;
   auto body = [&]() -> int {
     void* cur = ctx->ws_phi[0].p;
     void* prev = ctx->ws_phi[1].p;
@@ -1220,6 +1235,7 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
       a.prev_out = prev;
       a.step = (int)n;
       TBPM_TRY(launch_moment_step(ctx, a, pl.precision, n == 0));
+      throttle_queue(ctx, capturing);
       std::swap(cur, prev);
       ++n;
       return TBPM_OK;
@@ -1230,6 +1246,7 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
       void* pair_out[2] = {ctx->ws_phi2[0].p, ctx->ws_phi2[1].p};
       while (n + K <= M / 2) {
         TBPM_TRY(launch_fused_pass(ctx, lat, a, prev, cur, pair_out[0], pair_out[1], (int)n, fmode));
+        throttle_queue(ctx, capturing);
         void* old_prev = prev;
         void* old_cur = cur;
         prev = pair_out[0];
@@ -1281,7 +1298,9 @@ int run_moments(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const
         cudaGraph_t graph = nullptr;
         const int64_t l0 = ctx->launches;
         TBPM_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        capturing = true;
         const int r = body();
+        capturing = false;
         const cudaError_t ec = cudaStreamEndCapture(ctx->stream, &graph);
         const int64_t kernels = ctx->launches - l0;
         ctx->launches = l0;

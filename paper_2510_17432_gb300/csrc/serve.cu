@@ -430,6 +430,7 @@ static void release_job(tbpm_server* srv, ServeJob* j) {
 static int setup_lane_job(tbpm_server* srv, ServeJob* j) {
   TBPM_TRY(tbpm_create(&j->lane_ctx, srv->ctx->device));
   tbpm_ctx* c = j->lane_ctx;
+  c->max_queue = 128;  // the lane's thread waits instead of filling the launch queue
   TBPM_TRY(tbpm_lattice_create(c, &j->ldesc, &j->lat));
   tbpm_lattice* lat = j->lat;
   if (j->req.precision == TBPM_C128) TBPM_TRY(lattice_ensure_d64(lat));
@@ -777,6 +778,19 @@ int tbpm_server_create(tbpm_ctx* ctx, const tbpm_server_config* cfg, tbpm_server
   if (srv->cfg.max_queue <= 0) srv->cfg.max_queue = 4096;
   int r = tbpm_create(&srv->ctx, ctx->device);
   if (r == TBPM_OK) r = tbpm_create(&srv->builder, ctx->device);
+  if (r == TBPM_OK) {
+    // the batch (small requests) runs at the highest stream priority, so its kernels take SMs as
+    // soon as the direct lanes' passes free them
+    int least = 0, greatest = 0;
+    cudaStream_t hi = nullptr;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest) == cudaSuccess) {
+      cudaStreamSynchronize(srv->ctx->stream);
+      cudaStreamDestroy(srv->ctx->stream);
+      srv->ctx->stream = hi;
+    }
+    cudaGetLastError();
+  }
   if (r != TBPM_OK) {
     if (srv->ctx) tbpm_destroy(srv->ctx);
     delete srv;

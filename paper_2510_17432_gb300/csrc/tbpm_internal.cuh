@@ -173,6 +173,13 @@ struct tbpm_ctx {
   double* pinned = nullptr;
   size_t pinned_cap = 0;
   // phase timing with CUDA events on the context stream (tbpm_profile)
+  // bounded launch queue (0 = unbounded): an eager moment sequence waits, every 64 launches, for
+  // the launches enqueued two windows earlier, so that a long sequence never fills the driver's
+  // launch queue (serving lanes run beside other streams)
+  int max_queue = 0;
+  int64_t queue_count = 0;
+  cudaEvent_t queue_ev[2] = {nullptr, nullptr};
+  bool queue_live[2] = {false, false};
   bool profiling = false;
   struct Phase {
     cudaEvent_t a, b;
