@@ -1540,9 +1540,13 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
   // every T terms one flush adds sum_t c_t(j) phi_t to every accumulator of the block (each
   // accumulator crosses HBM once per T terms instead of once per term); C(t_j) = <psi|acc_j>
   // for the whole block comes from one block inner product at its end.  Slots 0 and 1 carry the
-  // two latest vectors of the previous window, slot 2 + k holds term n0 + k.
+  // two latest vectors of the previous window, slot 2 + k holds term n0 + k.  Where the register
+  // sweep applies, four terms at a time come from one window pass (phi_n and phi_{n-1} read once
+  // for four slots), which pays even for b = 1: the sequential form then buffers too; otherwise
+  // the sequential form keeps its fused one-accumulator pass.
+  const bool sweep_win = sweep_window_applicable(lat, pl.precision, pl.Spad);
   int T = 0;
-  if (ctx->buffer_blocks && b >= 2) {  // the sequential form keeps its fused one-accumulator pass
+  if (ctx->buffer_blocks && (b >= 2 || sweep_win)) {
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     const int64_t fit = (int64_t)(0.5 * (double)free_b / (double)pl.state_bytes) - 2;
@@ -1592,6 +1596,12 @@ int run_blocks(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const 
           TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
           TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
           n0 = n;
+        }
+        if (sweep_win && n >= 2 && n + 3 < Nb && n - n0 + 4 <= T) {  // terms n .. n+3 in one pass
+          void* const w[4] = {slot_of(n), slot_of(n + 1), slot_of(n + 2), slot_of(n + 3)};
+          TBPM_TRY(launch_sweep_window(ctx, lat, gr.r, slot_of(n - 2), slot_of(n - 1), w));
+          n += 3;
+          continue;
         }
         gr.r.cur = slot_of(n - 1);
         gr.r.prev_out = n >= 2 ? slot_of(n - 2) : slot_of(n - 1);  // not read by the first step

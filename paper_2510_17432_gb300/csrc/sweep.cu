@@ -82,6 +82,7 @@ struct Args {
   int M;
   int step0;
   int* status;            // host-visible status word: nonzero = a bounded wait expired
+  float4* win[4];         // window mode: phi_{n+1} .. phi_{n+4}, one buffer each
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -158,7 +159,9 @@ __device__ __forceinline__ void moment_terms(float2* acc2, float4 a, float4 n) {
   acc2[3] = __ffma2_rn(hi2(n), hi2(a), acc2[3]);
 }
 
-template <int NT_, int K_, int NSLOT_, bool HAS_DIAG, bool OPEN>
+// WIN: window mode for the time blocks -- every level goes to its own buffer (a.win[L-1]) and no
+// moment is summed; otherwise levels K-1 and K go to prev_out, cur_out with the moments.
+template <int NT_, int K_, int NSLOT_, bool HAS_DIAG, bool OPEN, bool WIN = false>
 __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_moments(Args a) {
   using C = Cfg<NT_, K_, NSLOT_>;
   constexpr int NT = C::NT, K = C::K, H = C::H, NSLOT = C::NSLOT, NV = C::NV;
@@ -364,6 +367,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   // outputs of levels K-1 and K at the rows they form at the current position
   float4* out_km1 = a.prev_out + (r0 - (K - 2)) * row_units + colA;
   float4* out_k = a.cur_out + (r0 - (K - 1)) * row_units + colA;
+  int64_t off_r = r0 * row_units + colA;  // window mode: offset of row r in every level's buffer
   // ring slots of level-0 rows r and r+1 (a slot's phi_{n-1} row follows at + 2 NT + P)
   int slot_0 = 0, slot_p1 = 1 % NSLOT;
   uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
@@ -459,22 +463,32 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           }
         }
         if (intx && (unsigned)(iq - H) < (unsigned)ny) {
-          if (L == K - 1) {
-            __stcs(out_km1, nA);
-            __stcs(out_km1 + P, nB);
-          } else if (L == K) {
-            __stcs(out_k, nA);
-            __stcs(out_k + P, nB);
+          if (WIN) {
+            float4* dst = a.win[L - 1] + (off_r - (int64_t)(L - 1) * row_units);
+            __stcs(dst, nA);
+            __stcs(dst + P, nB);
+          } else {
+            if (L == K - 1) {
+              __stcs(out_km1, nA);
+              __stcs(out_km1 + P, nB);
+            } else if (L == K) {
+              __stcs(out_k, nA);
+              __stcs(out_k + P, nB);
+            }
+            moment_terms(acc2 + (L - 1) * 4, ownA, nA);
+            moment_terms(acc2 + (L - 1) * 4, ownB, nB);
           }
-          moment_terms(acc2 + (L - 1) * 4, ownA, nA);
-          moment_terms(acc2 + (L - 1) * 4, ownB, nB);
         }
       }
-      out_km1 += row_units;
-      out_k += row_units;
-      if (++folded == C::FOLD) {
-        folded = 0;
-        fold();
+      if (WIN) {
+        off_r += row_units;
+      } else {
+        out_km1 += row_units;
+        out_k += row_units;
+        if (++folded == C::FOLD) {
+          folded = 0;
+          fold();
+        }
       }
       // one barrier per position; it also tells every thread whether any wait expired
       if (__syncthreads_or(timed_out ? 1 : 0)) {
@@ -497,6 +511,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       if (!mbar_wait(smem_u32(bars + j % NSLOT), (uint32_t)((j / NSLOT) & 1))) err_wait = true;
     atomicExch(a.status, err_wait ? 2 : 1);
   }
+  if (WIN) return;
   fold();
   __syncthreads();
   for (int qv = tid; qv < P * NV; qv += NT) {  // warps in order
@@ -536,22 +551,27 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
 
 }  // namespace sweep
 
-template <int NT, int K, int NSLOT, bool D, bool O>
+template <int NT, int K, int NSLOT, bool D, bool O, bool W = false>
 static cudaError_t set_sweep_smem() {
-  return cudaFuncSetAttribute(sweep::k_sweep_moments<NT, K, NSLOT, D, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)sweep::Cfg<NT, K, NSLOT>::smem(16, true));
+  return cudaFuncSetAttribute(sweep::k_sweep_moments<NT, K, NSLOT, D, O, W>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep::Cfg<NT, K, NSLOT>::smem(16, true));
 }
 
+// win != null: window mode, phi_{n+1..n+4} into win[0..3] (no moments)
 template <int NT, int K, int NSLOT>
 static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
-                        const void* cur_in, void* prev_out, void* cur_out, int step0) {
+                        const void* cur_in, void* prev_out, void* cur_out, int step0, void* const* win = nullptr) {
   using namespace sweep;
   using Cf = Cfg<NT, K, NSLOT>;
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    cudaError_t e[4] = {set_sweep_smem<NT, K, NSLOT, false, false>(), set_sweep_smem<NT, K, NSLOT, false, true>(),
-                        set_sweep_smem<NT, K, NSLOT, true, false>(), set_sweep_smem<NT, K, NSLOT, true, true>()};
+    cudaError_t e[8] = {set_sweep_smem<NT, K, NSLOT, false, false>(), set_sweep_smem<NT, K, NSLOT, false, true>(),
+                        set_sweep_smem<NT, K, NSLOT, true, false>(), set_sweep_smem<NT, K, NSLOT, true, true>(),
+                        set_sweep_smem<NT, K, NSLOT, false, false, true>(),
+                        set_sweep_smem<NT, K, NSLOT, false, true, true>(),
+                        set_sweep_smem<NT, K, NSLOT, true, false, true>(),
+                        set_sweep_smem<NT, K, NSLOT, true, true, true>()};
     for (cudaError_t x : e)
       if (x != cudaSuccess) attr = x;
   });
@@ -621,7 +641,16 @@ static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurrence
   const bool open = !(a.pbc_x && a.pbc_y);
   const dim3 gr((unsigned)grid), bl(NT);
   const size_t sm = Cf::smem(a.P, a.diag != nullptr);
-  if (a.diag) {
+  if (win) {
+    for (int l = 0; l < 4; ++l) a.win[l] = (float4*)win[l];
+    if (a.diag) {
+      if (open) k_sweep_moments<NT, K, NSLOT, true, true, true><<<gr, bl, sm, ctx->stream>>>(a);
+      else k_sweep_moments<NT, K, NSLOT, true, false, true><<<gr, bl, sm, ctx->stream>>>(a);
+    } else {
+      if (open) k_sweep_moments<NT, K, NSLOT, false, true, true><<<gr, bl, sm, ctx->stream>>>(a);
+      else k_sweep_moments<NT, K, NSLOT, false, false, true><<<gr, bl, sm, ctx->stream>>>(a);
+    }
+  } else if (a.diag) {
     if (open) k_sweep_moments<NT, K, NSLOT, true, true><<<gr, bl, sm, ctx->stream>>>(a);
     else k_sweep_moments<NT, K, NSLOT, true, false><<<gr, bl, sm, ctx->stream>>>(a);
   } else {
@@ -630,6 +659,17 @@ static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurrence
   }
   TBPM_CK_LAUNCH(ctx);
   return TBPM_OK;
+}
+
+// Window pass of the time blocks: phi_{n+1} .. phi_{n+4} from (prev_in = phi_{n-1}, cur_in = phi_n)
+// into win[0..3] by the 128-thread register sweep; false when the lattice does not take it.
+bool sweep_window_applicable(const tbpm_lattice* lat, int precision, int Spad) {
+  return fused_applicable(lat, precision, Spad) && lat->geom.Lx >= 128 / (Spad / 2);
+}
+
+int launch_sweep_window(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                        const void* cur_in, void* const win[4]) {
+  return launch_sweep<128, 4, 5>(ctx, lat, ra, prev_in, cur_in, nullptr, nullptr, 0, win);
 }
 
 // One register-resident sweep pass: steps step0 .. step0+K-1 from (prev_in, cur_in) into

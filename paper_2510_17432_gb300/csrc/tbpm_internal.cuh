@@ -331,6 +331,10 @@ constexpr int kSweepStatusSlot = 16;
 int launch_sweep_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant);
 int sweep_status(tbpm_ctx* ctx);  // TBPM_ETIMEOUT (and clears the word) after an expired wait
+// window pass of the time blocks (no moments): phi_{n+1..n+4} into win[0..3]
+bool sweep_window_applicable(const tbpm_lattice* lat, int precision, int Spad);
+int launch_sweep_window(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
+                        const void* cur_in, void* const win[4]);
 int fused_steps(int variant);
 int launch_fused_pass(tbpm_ctx* ctx, const tbpm_lattice* lat, const RecurrenceArgs& ra, const void* prev_in,
                       const void* cur_in, void* prev_out, void* cur_out, int step0, int variant);

@@ -200,6 +200,24 @@ def test_correlation_forms_match_oracle(capi, ctx, prec):
     capi.tbpm_lattice_destroy(lat)
 
 
+@pytest.mark.parametrize("pbc", [(1, 1, 1), (0, 1, 1)])
+def test_correlation_forms_through_window_sweep(capi, ctx, pbc):
+    """Honeycomb lattices wide enough for the register sweep's window pass (four Chebyshev terms
+    of a time block per pass into four buffer slots): the sequential form (b = 1) and the time
+    blocks of every size against the oracle's sequential propagation, periodic and open in x."""
+    lat, ol = make(capi, ctx, kind=1, L=(100, 64), t=-2.7, W=1.0, pbc=pbc)
+    Nt, S = 30, 4
+    psi = oprop.random_phase_states(ol, 3, S)
+    refs = {s: oprop.correlation_sequential(ol, psi[s], Nt) for s in (0, S - 1)}
+    for form, b in ((capi.SEQUENTIAL, 0), (capi.CONCURRENT_S, 7), (capi.CONCURRENT_S, 30), (capi.CONCURRENT_S, 0),
+                    (capi.CONCURRENT_M, 0)):
+        C = gpu_corr(capi, ctx, lat, S, Nt, 0, form, b)
+        for s, ref in refs.items():
+            err = np.max(np.abs(C[s] - ref)) / abs(ref[0])
+            assert err <= TOL[0], (form, b, s, err)
+    capi.tbpm_lattice_destroy(lat)
+
+
 def test_correlation_vacancy_lattice(capi, ctx):
     lat, ol = make(capi, ctx, kind=1, L=(24, 16), t=-2.7, W=2.0, vac=0.02)
     psi = oprop.random_phase_states(ol, 3, 1)[0]
