@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "tbpm_internal.cuh"
@@ -669,21 +670,23 @@ __global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, 
 // accumulators of a time block, with T buffered Chebyshev vectors phi_t (consecutive state
 // blocks) and complex coefficients c_t(j) = coef[(t * nb + j) * 2 + {0, 1}] (zero once term t is
 // past N(j tau~)).  Each accumulator is read and written once per T terms instead of once per
-// term.  grid: (accumulator tiles of kQeEB, unit blocks).
+// term.  grid: (accumulator tiles of EB, unit blocks); EB = 1, 4 or 16 accumulators per tile
+// (the registers of a tile's accumulators limit how many threads, and so how many buffer loads,
+// an SM keeps in flight: a one-accumulator flush, the sequential form's, runs at full occupancy).
 #ifndef TBPM_FLUSH_UNROLL
-#define TBPM_FLUSH_UNROLL 4
+#define TBPM_FLUSH_UNROLL 8
 #endif
 constexpr int kFlushUnroll = TBPM_FLUSH_UNROLL;
 
-template <typename R, int SPT>
+template <typename R, int SPT, int EB>
 __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int T, int64_t stride_packs, void* accv,
                                                           int nb, const double* coef, int64_t n_units) {
   using PK = Pack<R, SPT>;
-  __shared__ R cr[kQeMaxT][kQeEB], ci[kQeMaxT][kQeEB];
-  const int e0 = blockIdx.x * kQeEB;
-  const int ne = min(kQeEB, nb - e0);
-  for (int i = threadIdx.x; i < T * kQeEB; i += kThreads) {
-    const int t = i / kQeEB, e = i - t * kQeEB;
+  __shared__ R cr[kQeMaxT][EB], ci[kQeMaxT][EB];
+  const int e0 = blockIdx.x * EB;
+  const int ne = min(EB, nb - e0);
+  for (int i = threadIdx.x; i < T * EB; i += kThreads) {
+    const int t = i / EB, e = i - t * EB;
     const bool ok = e < ne;
     cr[t][e] = ok ? (R)coef[((int64_t)t * nb + e0 + e) * 2] : R(0);
     ci[t][e] = ok ? (R)coef[((int64_t)t * nb + e0 + e) * 2 + 1] : R(0);
@@ -692,9 +695,9 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
   const PK* Phi = reinterpret_cast<const PK*>(phiv);
   PK* Q = reinterpret_cast<PK*>(accv);
   for (int64_t u = (int64_t)blockIdx.y * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.y * kThreads) {
-    PK acc[kQeEB];
+    PK acc[EB];
 #pragma unroll
-    for (int e = 0; e < kQeEB; ++e) {
+    for (int e = 0; e < EB; ++e) {
       if (e < ne) acc[e] = ld(Q + (int64_t)(e0 + e) * stride_packs + u);
       else
 #pragma unroll
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
     for (int t = 0; t < T; ++t) {  // unrolled so that several buffer loads are in flight
       const PK x = ld(Phi + (int64_t)t * stride_packs + u);
 #pragma unroll
-      for (int e = 0; e < kQeEB; ++e) {
+      for (int e = 0; e < EB; ++e) {
         if (e < ne) {  // uniform: a tile of fewer accumulators does no work for the rest
           const R a = cr[t][e], b = ci[t][e];
 #pragma unroll
@@ -717,7 +720,7 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
       }
     }
 #pragma unroll
-    for (int e = 0; e < kQeEB; ++e)
+    for (int e = 0; e < EB; ++e)
       if (e < ne) st(Q + (int64_t)(e0 + e) * stride_packs + u, acc[e]);
   }
 }
@@ -889,13 +892,20 @@ int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, co
   }
   const int spt = spt_of(precision, a.S);
   const int64_t n_units = a.n_sites * a.P;
-  const int etiles = (nb + kQeEB - 1) / kQeEB;
-  const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * 8 / etiles);
+  const int eb = nb == 1 ? 1 : nb <= 4 ? 4 : 16;
+  const int etiles = (nb + eb - 1) / eb;
+  const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * (eb == 16 ? 8 : 16) / etiles);
   const int ublocks = (int)std::min<int64_t>(std::min<int64_t>(want, (n_units + kThreads - 1) / kThreads), 65535);
   void* fn;
-  if (precision == TBPM_C128) fn = (void*)k_block_flush<double, 1>;
-  else if (spt == 2) fn = (void*)k_block_flush<float, 2>;
-  else fn = (void*)k_block_flush<float, 1>;
+  auto pick = [&](auto eb_tag) -> void* {
+    constexpr int E = decltype(eb_tag)::value;
+    if (precision == TBPM_C128) return (void*)k_block_flush<double, 1, E>;
+    if (spt == 2) return (void*)k_block_flush<float, 2, E>;
+    return (void*)k_block_flush<float, 1, E>;
+  };
+  if (eb == 1) fn = pick(std::integral_constant<int, 1>());
+  else if (eb == 4) fn = pick(std::integral_constant<int, 4>());
+  else fn = pick(std::integral_constant<int, 16>());
   int64_t stride = n_units;
   int64_t nu = n_units;
   void* args[] = {(void*)&phi, &T, &stride, &acc, &nb, (void*)&coef, &nu};
