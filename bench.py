@@ -527,12 +527,26 @@ def run_gpu(args, work):
         conc_su = (Mtot + (Mtot & 1)) // 2 * info.n_sites * S
         diff = float(np.max(np.abs(res["concurrent_m"][2] - res["sequential"][2])) /
                      np.max(np.abs(res["sequential"][2])))
+        block = float(info.n_sites) * S * elem
+        fused = args.fusion in FUSION_STEPS and FUSION_STEPS[args.fusion] == 4 and spec.kind == wl.HONEYCOMB
+        conc_blocks = concurrent_m_blocks(Mtot, fused)
+        seq_blocks = Nt * sequential_step_blocks(Ntrunc, fused)
+        peak, _ = measured_hbm_peak()
         out["sequential"] = {
             "n_steps": Nt, "tau": "pi", "dos": "Hann-windowed Fourier DOS on 512 energies",
             "wall_s_concurrent": res["concurrent_m"][0], "wall_s_sequential": res["sequential"][0],
             "speedup_wall": res["sequential"][0] / res["concurrent_m"][0],
             "matrix_applications_concurrent": conc_su // (info.n_sites * S),
             "matrix_applications_sequential": seq_su // (info.n_sites * S),
+            "speedup_matrix_applications": seq_su / conc_su,
+            "state_block_crossings_concurrent": conc_blocks, "state_block_crossings_sequential": seq_blocks,
+            "speedup_hbm_bytes": seq_blocks / conc_blocks,
+            "hbm_frac_concurrent": conc_blocks * block / res["concurrent_m"][0] / 1e9 / peak,
+            "hbm_frac_sequential": seq_blocks * block / res["sequential"][0] / 1e9 / peak,
+            "bytes_model": "state blocks of N x S x 8 B crossing HBM: concurrent = moment passes (4 per "
+                           "four-step pass, 3 per one-step pass); sequential = per time step the buffered "
+                           "time block of the library (copy, first step, four-term window passes writing 4 "
+                           "slots, one-step passes, one flush reading every term, <psi|psi(t)>, carry)",
             "site_updates_per_s_sequential": seq_su / res["sequential"][0],
             "site_updates_per_s_concurrent": conc_su / res["concurrent_m"][0],
             "max_rel_dos_difference": diff}
@@ -561,6 +575,38 @@ def run_gpu(args, work):
     if pg is not None:
         pg.barrier()
         pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- byte models of the two forms
+def concurrent_m_blocks(n_moments: int, fused: bool) -> float:
+    """State-block crossings of the moment pass for n_moments moments (cost halving: M/2 steps):
+    initialisation writes phi_0, the first one-step pass reads it and writes phi_1 (with the
+    moments), then four-step passes (read 2, write 2) where the register sweep runs, and one-step
+    passes (read phi_n, phi_{n-1}, write phi_{n+1}) for the rest."""
+    steps = (n_moments + (n_moments & 1)) // 2
+    blocks = 1 + 2
+    n = 1
+    if fused:
+        while n + 4 <= steps:
+            blocks += 4
+            n += 4
+    return blocks + 3 * (steps - n)
+
+
+def sequential_step_blocks(n_terms: int, fused: bool) -> float:
+    """State-block crossings of one sequential time step as the library buffers it (b = 1):
+    clear the accumulator, copy psi(t) into the first slot, the first term H~ phi_0, four-term
+    window passes (read 2, write 4) while four terms fit, one-step passes (read 2, write 1) for
+    the rest, one flush (read every term, read and write the accumulator), <psi|psi(t)> (2) and
+    the copy of psi(t) for the next step (2)."""
+    blocks = 1 + 2 + 2
+    n = 2
+    if fused:
+        while n + 3 < n_terms:
+            blocks += 6
+            n += 4
+    blocks += 3 * (n_terms - n)
+    return blocks + n_terms + 2 + 2 + 2
 
 
 # ---------------------------------------------------------------- state-based correlation (vacancy lattices)
