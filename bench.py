@@ -205,6 +205,63 @@ print(json.dumps(out))
 """
 
 
+# the same sample, one process per host core, each starting its timed loop once every process
+# has built its lattice (a file barrier), so that the loops overlap
+ORACLE_SAMPLE_SYNC = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import lattice as L, propagate as P
+lat = L.build_lattice({kind}, {dims}, t={t}, W={W}, vacancy_frac={vac}, seed={seed}, cutoff={cutoff}, decay={decay})
+psi = P.random_phase_states(lat, 1 + {rank}, 1)[0]
+P.moments(lat, psi, psi, 4)
+open(os.path.join({sync!r}, "ready{rank}"), "w").close()
+while not os.path.exists(os.path.join({sync!r}, "go")):
+    time.sleep(0.01)
+t0 = time.perf_counter(); k = 0; n = 0
+while time.perf_counter() - t0 < {seconds}:
+    P.moments(lat, psi, psi, 16); k += 16
+dt = time.perf_counter() - t0
+print(json.dumps(dict(steps=k, seconds=dt, site_updates=k * lat.n)))
+"""
+
+
+def oracle_sample_all_cores(work: wl.Workload, seconds: float, max_procs: int = 16):
+    """The oracle on every host core at once: one single-threaded process per core."""
+    spec = work.lattice
+    nproc = max(1, min(os.cpu_count() or 1, max_procs))
+    sync = tempfile.mkdtemp()
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = []
+    for rank in range(nproc):
+        code = ORACLE_SAMPLE_SYNC.format(root=ROOT, kind=spec.kind, dims=oracle_lattice_dims(spec), t=spec.t, W=spec.W,
+                                         vac=spec.vacancy_frac, seed=spec.seed, seconds=seconds, rank=rank, sync=sync,
+                                         cutoff=spec.cutoff, decay=spec.decay)
+        procs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                      text=True, env=env))
+    deadline = time.time() + 600
+    while sum(os.path.exists(os.path.join(sync, f"ready{r}")) for r in range(nproc)) < nproc:
+        if time.time() > deadline or any(p.poll() not in (None, 0) for p in procs):
+            for p in procs:
+                p.kill()
+            raise RuntimeError("oracle processes did not start")
+        time.sleep(0.05)
+    open(os.path.join(sync, "go"), "w").close()
+    res = []
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError(err[-1000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    su = sum(r["site_updates"] for r in res)
+    wall = max(r["seconds"] for r in res)
+    dims = oracle_lattice_dims(spec)
+    return {"value": su / wall, "unit": "site-updates/s", "cores": nproc, "kind": "oracle",
+            "sample": f"FP64 oracle (numpy/scipy CSR matvec), {nproc} single-threaded processes at once (one per "
+                      f"host core), each timing plain Chebyshev steps of one state for {seconds:.0f} s on the "
+                      f"{'x'.join(str(d) for d in dims if d > 1)} lattice; rate = all site-updates / the longest loop"}
+
+
 ORACLE_MAX_SITES = 1 << 25  # larger lattices are sampled on a 2^24-site lattice of the same kind
 
 
@@ -566,6 +623,11 @@ def run_gpu(args, work):
         except Exception as exc:  # the GPU number stands; say why the baseline is missing
             out["cpu_baseline"] = {"value": None, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
                                    "sample": f"failed: {exc!r}"[:300]}
+        try:
+            out["cpu_baseline_all_cores"] = oracle_sample_all_cores(work, min(10.0, args.cpu_seconds))
+        except Exception as exc:
+            out["cpu_baseline_all_cores"] = {"value": None, "unit": "site-updates/s", "kind": "oracle",
+                                             "sample": f"failed: {exc!r}"[:300]}
     elif rank == 0 and not args.no_cpu:
         out["cpu_baseline"] = None
 
@@ -1091,25 +1153,29 @@ def run_dense(args, work):
     e2e = {"value": whole_job_rate(site_updates, world, e2e_s), "unit": "site-updates/s",
            "h2d_bytes_per_step": int(hE.numel() * 8 + 72), "d2h_bytes_per_step": int(hD.numel() * 8)}
 
-    # roofline of the recurrence pass.  Clean lattices with complex64 and >= 2 states run the
-    # matrix-free tap kernel, bound by FP32 FMA issue: 2 FMAs (real weight x complex state) per tap
-    # per site-update, against 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (the part's unit
-    # counts and maximum clock).  Otherwise the ELL kernel: HBM-bound on the index lists.
+    # roofline of the recurrence pass.  The library reports which kernel carries it.  The tap
+    # kernel (clean long-range lattices, complex64, >= 2 states, a tile that fits shared memory)
+    # is bound by FP32 FMA issue: 2 FMAs (real weight x complex state) per tap per site-update,
+    # against the device's SM count x 128 FP32 lanes x 2 flops x the median SM clock sampled during
+    # the timed region.  Otherwise the ELL kernel: HBM-bound on the index lists.
     z = info.coordination
     elem = 8 if work.precision == capi.C64 else 16
     per_launch_ms = prof["recurrence_ms"] / max(1, prof["recurrence_launches"])
     peak, peak_kind = measured_hbm_peak()
     state_bytes = 3.0 * elem * S * info.n_sites
     flops_per_launch = 4.0 * z * info.n_sites * S
-    sm_count, lanes, fmax = 152, 128, 2.070e9
-    alu_peak = sm_count * lanes * fmax * 2 / 1e12
-    taps = work.precision == capi.C64 and S >= 2 and spec.vacancy_frac == 0 and spec.kind != wl.CUBIC
-    if taps:
+    props = torch.cuda.get_device_properties(dev)
+    sm_count, lanes = props.multi_processor_count, 128
+    sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    alu_peak = sm_count * lanes * sm_mhz * 1e6 * 2 / 1e12
+    pass_kind = capi.tbpm_moment_pass_kind(ctx, lat, req)
+    if pass_kind == capi.PASS_TAPS:
         achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz",
-                    "kernel": "k_taps_moment<honeycomb> (matrix-free taps, two complex64 states per pack)",
+                    "peak_source": f"derived: {sm_count} SMs (device) x {lanes} FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                                   "(median SM clock sampled during the timed region)",
+                    "kernel": f"k_taps_moment<{wl.KIND_NAMES[spec.kind]}> (matrix-free taps, two complex64 states per pack)",
                     "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_us": per_launch_ms * 1e3,
                     "hbm_algorithmic_gbs": state_bytes / (per_launch_ms / 1e3) / 1e9, "hbm_peak_gbs": peak,
                     "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
@@ -1118,7 +1184,7 @@ def run_dense(args, work):
         achieved = bytes_per_launch / (per_launch_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": None, "peak_source": peak_kind,
-                    "kernel": "k_moment_step<CSR> (ELL lists + per-slot weights)",
+                    "kernel": f"k_moment_step<CSR> (ELL lists + per-slot weights, {wl.KIND_NAMES[spec.kind]})",
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
                     "fp32_tflops": flops_per_launch / (per_launch_ms / 1e3) / 1e12, "fp32_peak_tflops": alu_peak,
                     "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}

@@ -238,6 +238,20 @@ int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, in
  * z = tbpm_lattice_props.coordination.  Nearest-neighbour lattices report their fixed order. */
 int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t);
 
+/* Which kernel carries the moment recurrence (a4) of a request on this lattice under the
+ * context's fusion mode (a diagnostic for benchmarks and profiles; no device work):
+ *   TBPM_PASS_STENCIL  one-step matrix-free stencil pass (k_moment_stencil)
+ *   TBPM_PASS_ELL      one-step pass over ELL neighbour lists (vacancies; k_moment_step)
+ *   TBPM_PASS_TAPS     matrix-free tap kernel of a long-range lattice (k_taps_moment)
+ *   TBPM_PASS_SWEEP    four-step register sweep (fusion modes 8-10; k_sweep_moments)
+ *   TBPM_PASS_ROWS     row-sweep fused pass with shared-memory level rings (modes 3-7)
+ *   TBPM_PASS_TILES    2-D tile fused pass (modes 1, 2)
+ * Under fusion mode -1 a fused lattice reports TBPM_PASS_STENCIL (the mode is chosen by timing
+ * at the first request).  Errors: TBPM_EINVAL for NULL arguments or an invalid request. */
+enum { TBPM_PASS_STENCIL = 0, TBPM_PASS_ELL = 1, TBPM_PASS_TAPS = 2, TBPM_PASS_SWEEP = 3, TBPM_PASS_ROWS = 4,
+       TBPM_PASS_TILES = 5 };
+int tbpm_moment_pass_kind(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int* kind);
+
 /* ---------------------------------------------------------------- states */
 
 /* Initial state block as stored for the recurrence, exported to the host:

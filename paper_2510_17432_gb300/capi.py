@@ -87,6 +87,7 @@ def load():
         "tbpm_lattice_info": (C.c_int, [_P, C.POINTER(LatticeProps)]),
         "tbpm_lattice_export": (C.c_int, [_P, _P, _P, _P]),
         "tbpm_lattice_taps": (C.c_int, [_P, _P, _P]),
+        "tbpm_moment_pass_kind": (C.c_int, [_P, _P, C.POINTER(Request), C.POINTER(C.c_int)]),
         "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
         "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
         "tbpm_moments": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
@@ -135,7 +136,7 @@ def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
-            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_conductivity_overlap",
             "tbpm_fermi_apply",
@@ -321,6 +322,16 @@ def tbpm_conductivity(ctx, lat, req: Request, direction: int, energies: np.ndarr
     e = np.ascontiguousarray(energies, dtype=np.float64)
     _check(load().tbpm_conductivity(ctx, lat, C.byref(req), int(direction), _host_ptr(e), int(e.size),
                                     _host_ptr(C_out), _host_ptr(sigma)))
+
+
+PASS_STENCIL, PASS_ELL, PASS_TAPS, PASS_SWEEP, PASS_ROWS, PASS_TILES = 0, 1, 2, 3, 4, 5
+
+
+def tbpm_moment_pass_kind(ctx, lat, req: Request) -> int:
+    """The kernel family that carries the request's moment recurrence (PASS_* constants)."""
+    k = C.c_int(0)
+    _check(load().tbpm_moment_pass_kind(ctx, lat, C.byref(req), C.byref(k)))
+    return k.value
 
 
 def tbpm_conductivity_overlap(ctx, lat, req: Request, direction: int, energies: np.ndarray,

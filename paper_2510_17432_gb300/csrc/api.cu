@@ -2175,6 +2175,31 @@ int tbpm_states_export(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_requ
   return TBPM_OK;
 }
 
+int tbpm_moment_pass_kind(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int* kind) {
+  clear_error();
+  if (!ctx || !lat_c || !req || !kind) {
+    set_error("tbpm_moment_pass_kind: NULL argument");
+    return TBPM_EINVAL;
+  }
+  tbpm_lattice* lat = const_cast<tbpm_lattice*>(lat_c);
+  Plan pl;
+  TBPM_TRY(make_plan(lat, req, &pl));
+  if (lat->chunks && pl.precision == TBPM_C64 && pl.Spad >= 2) {
+    *kind = TBPM_PASS_TAPS;
+    return TBPM_OK;
+  }
+  const int m = ctx->fusion;  // -1: autotuned on first use, reported as the mode it would time first
+  const int64_t M = req->n_moments > 0 ? req->n_moments : truncation_order_host(req->n_steps * pl.tau);
+  if (m > 0 && fused_applicable(lat, pl.precision, pl.Spad) && M / 2 - 1 >= fused_steps(m)) {
+    const int band = (m == 8 ? 128 : m == 9 ? 192 : 256) / (pl.Spad / 2);
+    *kind = (m >= 8 && m <= 10 && lat->geom.Lx >= band) ? TBPM_PASS_SWEEP
+            : (m >= 3) ? TBPM_PASS_ROWS : TBPM_PASS_TILES;
+    return TBPM_OK;
+  }
+  *kind = lat->path == TBPM_PATH_CSR ? TBPM_PASS_ELL : TBPM_PASS_STENCIL;
+  return TBPM_OK;
+}
+
 int tbpm_moments_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_mu) {
   clear_error();
   if (!ctx || !d_mu) {
