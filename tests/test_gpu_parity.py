@@ -464,3 +464,29 @@ def test_largest_lattice_sampled_sites_match_oracle_windows(capi, ctx):
         e[local] = 1.0
         ref = oprop.moments(wl, e, e, M)
         assert np.max(np.abs(mu[k] - ref)) <= 1e-5, (k, np.max(np.abs(mu[k] - ref)))
+
+
+def test_moment_pass_kind_names_the_kernel(capi, ctx):
+    """tbpm_moment_pass_kind names the kernel family that carries a request's recurrence."""
+    cases = [
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=8, n_moments=256), 8, capi.PASS_SWEEP),
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=8, n_moments=256), 5, capi.PASS_ROWS),
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=8, n_moments=256), 1, capi.PASS_TILES),
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=8, n_moments=256), 0, capi.PASS_STENCIL),
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=1, n_moments=256), 8, capi.PASS_STENCIL),
+        (dict(kind=1, L=(100, 64), t=-2.7), dict(n_states=8, n_moments=256, precision=1), 8, capi.PASS_STENCIL),
+        (dict(kind=1, L=(40, 40), t=-2.7), dict(n_states=8, n_moments=256), 8, capi.PASS_STENCIL),
+        (dict(kind=0, L=(64, 64), t=1.0), dict(n_states=8, n_moments=256), 8, capi.PASS_STENCIL),
+        (dict(kind=1, L=(40, 40), t=-2.7, vac=0.05), dict(n_states=2, n_moments=64), 8, capi.PASS_ELL),
+    ]
+    for spec, rk, mode, want in cases:
+        lat, _ = make(capi, ctx, **spec)
+        capi.tbpm_set_fusion(ctx, mode)
+        try:
+            assert capi.tbpm_moment_pass_kind(ctx, lat, capi.request(**rk)) == want, (spec, rk, mode)
+        finally:
+            capi.tbpm_set_fusion(ctx, 8)
+            capi.tbpm_lattice_destroy(lat)
+    lat = capi.tbpm_lattice_create(ctx, capi.lattice_desc(1, (70, 36), t=-2.7, cutoff=7.1, decay=0.3187))
+    assert capi.tbpm_moment_pass_kind(ctx, lat, capi.request(n_states=2, n_moments=64)) == capi.PASS_TAPS
+    capi.tbpm_lattice_destroy(lat)
