@@ -248,6 +248,16 @@ int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t);
  *   TBPM_PASS_TILES    2-D tile fused pass (modes 1, 2)
  * Under fusion mode -1 a fused lattice reports TBPM_PASS_STENCIL (the mode is chosen by timing
  * at the first request).  Errors: TBPM_EINVAL for NULL arguments or an invalid request. */
+/* Index checks of a debug build (libtbpm_debug.so, compiled with TBPM_DEBUG; the paper has no
+ * counterpart).  There the hot kernels (stencil, ELL and serving passes, the register sweep's
+ * stores and row copies) skip any global-memory access whose index falls outside its buffer and
+ * record the first such index per source unit; they never trap, so the context stays usable.
+ * words[k] (k = 0: recurrence passes, 1: register sweep, 2: serving) = (kernel id << 48) |
+ * (index & 0xFFFFFFFFFFFF), 0 when no check failed; kernel ids: 1 stencil units, 2 ELL
+ * neighbour index, 3 sweep store, 4 sweep row copy, 5 serving units.  Reading clears the words
+ * and synchronises the device.  The regular library returns TBPM_EUNSUPPORTED and zero words. */
+int tbpm_debug_status(tbpm_ctx* ctx, uint64_t words[3]);
+
 enum { TBPM_PASS_STENCIL = 0, TBPM_PASS_ELL = 1, TBPM_PASS_TAPS = 2, TBPM_PASS_SWEEP = 3, TBPM_PASS_ROWS = 4,
        TBPM_PASS_TILES = 5 };
 int tbpm_moment_pass_kind(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int* kind);

@@ -16,6 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtbpm.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libtbpm_debug.so")  # index-checked build (TBPM_DEBUG)
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["api.cu", "cheb.cu", "conduct.cu", "fused.cu", "recon.cu", "recon_tc.cu", "response.cu", "serve.cu",
            "sweep.cu", "taps.cu"]
@@ -45,8 +47,8 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(p) > t for p in [src] + _headers())
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
+def _compile(src: str, extra, build_dir: str = BUILD) -> str:
+    obj = os.path.join(build_dir, os.path.splitext(os.path.basename(src))[0] + ".o")
     if _stale(obj, src):
         cmd = [nvcc()] + FLAGS + list(extra) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,27 +57,31 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, extra=(), verbose: bool = False) -> str:
-    """Compile every CUDA source for sm_103a and link libtbpm.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, extra=(), verbose: bool = False, debug: bool = False) -> str:
+    """Compile every CUDA source for sm_103a and link libtbpm.so (debug: the index-checked
+    libtbpm_debug.so, compiled with TBPM_DEBUG); returns the library's path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if debug:
+        extra = tuple(extra) + ("-DTBPM_DEBUG",)
+    os.makedirs(build_dir, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     if force:
         for s in srcs:
-            obj = os.path.join(BUILD, os.path.splitext(os.path.basename(s))[0] + ".o")
+            obj = os.path.join(build_dir, os.path.splitext(os.path.basename(s))[0] + ".o")
             if os.path.exists(obj):
                 os.remove(obj)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, build_dir), srcs))
+    if force or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -12,7 +12,7 @@ import os
 
 import numpy as np
 
-from ._build import LIB
+from ._build import LIB, LIB_DEBUG
 
 SQUARE, HONEYCOMB, CUBIC = 0, 1, 2
 PATH_AUTO, PATH_STENCIL, PATH_CSR = 0, 1, 2
@@ -71,7 +71,24 @@ def load():
     if not os.path.exists(LIB):
         raise ImportError(f"{LIB} is missing: build it with __graft_entry__.build() "
                           "(there is no fallback implementation)")
-    lib = C.CDLL(LIB)
+    _lib = _bind(C.CDLL(LIB))
+    return _lib
+
+
+_lib_debug = None
+
+
+def load_debug():
+    """Load the index-checked libtbpm_debug.so (paper_2510_17432_gb300._build.build(debug=True))."""
+    global _lib_debug
+    if _lib_debug is None:
+        if not os.path.exists(LIB_DEBUG):
+            raise ImportError(f"{LIB_DEBUG} is missing: build it with _build.build(debug=True)")
+        _lib_debug = _bind(C.CDLL(LIB_DEBUG))
+    return _lib_debug
+
+
+def _bind(lib):
     sig = {
         "tbpm_create": (C.c_int, [C.POINTER(_P), C.c_int]),
         "tbpm_destroy": (C.c_int, [_P]),
@@ -88,6 +105,7 @@ def load():
         "tbpm_lattice_export": (C.c_int, [_P, _P, _P, _P]),
         "tbpm_lattice_taps": (C.c_int, [_P, _P, _P]),
         "tbpm_moment_pass_kind": (C.c_int, [_P, _P, C.POINTER(Request), C.POINTER(C.c_int)]),
+        "tbpm_debug_status": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
         "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
         "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
         "tbpm_moments": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
@@ -128,7 +146,6 @@ def load():
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
     return lib
 
 
@@ -136,7 +153,7 @@ def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
-            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_debug_status", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_conductivity_overlap",
             "tbpm_fermi_apply",
@@ -145,9 +162,9 @@ def exported_symbols():
             "tbpm_server_stats"]
 
 
-def _check(status: int):
+def _check(status: int, lib=None):
     if status != 0:
-        raise TbpmError(status, load().tbpm_last_error().decode(errors="replace"))
+        raise TbpmError(status, (lib or load()).tbpm_last_error().decode(errors="replace"))
 
 
 def _host_ptr(a: np.ndarray | None):
@@ -325,6 +342,23 @@ def tbpm_conductivity(ctx, lat, req: Request, direction: int, energies: np.ndarr
 
 
 PASS_STENCIL, PASS_ELL, PASS_TAPS, PASS_SWEEP, PASS_ROWS, PASS_TILES = 0, 1, 2, 3, 4, 5
+DEBUG_KERNELS = {1: "stencil units", 2: "ELL neighbour index", 3: "sweep store", 4: "sweep row copy",
+                 5: "serving units"}
+
+
+def tbpm_debug_status(ctx, lib=None) -> list:
+    """The debug build's three index-check words (recurrence passes, register sweep, serving),
+    read and cleared; raises TbpmError(TBPM_EUNSUPPORTED) on the regular library."""
+    words = (C.c_uint64 * 3)()
+    _check((lib or load()).tbpm_debug_status(ctx, words), lib)
+    return [int(w) for w in words]
+
+
+def decode_debug_word(word: int):
+    """(kernel name, index) of a failed check, or None for a clean word."""
+    if word == 0:
+        return None
+    return DEBUG_KERNELS.get(word >> 48, f"kernel {word >> 48}"), word & 0xFFFFFFFFFFFF
 
 
 def tbpm_moment_pass_kind(ctx, lat, req: Request) -> int:

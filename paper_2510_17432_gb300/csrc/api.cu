@@ -949,6 +949,26 @@ int tbpm_lattice_export(const tbpm_lattice* lat, int64_t* compact, double* V, in
   return TBPM_OK;
 }
 
+int tbpm_debug_status(tbpm_ctx* ctx, uint64_t words[3]) {
+  clear_error();
+  if (!ctx || !words) {
+    set_error("tbpm_debug_status: NULL argument");
+    return TBPM_EINVAL;
+  }
+#ifdef TBPM_DEBUG
+  TBPM_CK(cudaSetDevice(ctx->device));
+  TBPM_CK(cudaDeviceSynchronize());
+  words[0] = debug_take_cheb();
+  words[1] = debug_take_sweep();
+  words[2] = debug_take_serve();
+  return TBPM_OK;
+#else
+  words[0] = words[1] = words[2] = 0;
+  set_error("tbpm_debug_status: this library was built without TBPM_DEBUG (use libtbpm_debug.so)");
+  return TBPM_EUNSUPPORTED;
+#endif
+}
+
 int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t) {
   clear_error();
   if (!lat) {

@@ -42,7 +42,7 @@ __device__ __forceinline__ void neighbour_sum(const RecurrenceArgs& a, const Pac
 #pragma unroll
   for (int k = 0; k < 2 * SPT; ++k) h.v[k] = R(0);
   auto add = [&](int64_t j) {
-    if (j >= 0) {
+    if (j >= 0 && TBPM_DBG_OK(j, a.n_sites, TBPM_DBG_ELL)) {
       const Pack<R, SPT> q = ld(cur + j * a.P + p);
 #pragma unroll
       for (int k = 0; k < 2 * SPT; ++k) h.v[k] += q.v[k];
@@ -56,7 +56,7 @@ __device__ __forceinline__ void neighbour_sum(const RecurrenceArgs& a, const Pac
       const R* w = reinterpret_cast<const R*>(a.wrel);
       for (int d = 0; d < z; ++d) {
         const int32_t j = __ldg(row + d);
-        if (j >= 0) {
+        if (j >= 0 && TBPM_DBG_OK(j, a.n_sites, TBPM_DBG_ELL)) {
           const R wd = __ldg(w + d);
           const Pack<R, SPT> q = ld(cur + (int64_t)j * a.P + p);
 #pragma unroll
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, kStencilMinBlocks) k_moment_stencil(
 #pragma unroll
     for (int k = 0; k < kStencilUPT; ++k) {
       const int u = chunk * TU + k * kThreads + threadIdx.x;
-      valid[k] = u < upr;
+      valid[k] = u < upr && TBPM_DBG_OK(b.own + u, g.n_full * P, TBPM_DBG_STENCIL);
 #pragma unroll
       for (int q = 0; q < 2 * SPT; ++q) h[k].v[q] = R(0);
       if (valid[k]) {
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, kStencilMinBlocks) k_moment_stencil(
         stencil_neighbours<KIND>(g, b, u, P, logP, p, upr, nb);
 #pragma unroll
         for (int q = 0; q < Z; ++q) {
-          if (nb[q] >= 0) {
+          if (nb[q] >= 0 && TBPM_DBG_OK(nb[q], g.n_full * P, TBPM_DBG_STENCIL)) {
             const PK t = ld(cur + nb[q]);
 #pragma unroll
             for (int w = 0; w < 2 * SPT; ++w) h[k].v[w] += t.v[w];
@@ -1075,3 +1075,5 @@ extern "C" int tbpm_moment_step_noalloc(int kind, const int64_t L[3], const int3
   }
   return TBPM_OK;
 }
+
+TBPM_DEBUG_UNIT(cheb)

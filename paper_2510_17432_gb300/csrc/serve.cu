@@ -99,7 +99,7 @@ __device__ __forceinline__ void serve_unit(const ServeItem& it, const Pack<R, SP
     stencil_neighbours<KIND>(it.geom, b, u, it.P, it.logP, p, it.upr, nb);
 #pragma unroll
     for (int q = 0; q < Z; ++q) {
-      if (q < 6 && nb[q] >= 0) {
+      if (q < 6 && nb[q] >= 0 && TBPM_DBG_OK(nb[q], it.n_sites * it.P, TBPM_DBG_SERVE)) {
         const PK t = ld(cur + nb[q]);
 #pragma unroll
         for (int w = 0; w < 2 * SPT; ++w) h.v[w] += t.v[w];
@@ -970,3 +970,5 @@ int tbpm_server_stats(tbpm_server* srv, int64_t out[7]) {
 }
 
 }  // extern "C"
+
+TBPM_DEBUG_UNIT(serve)

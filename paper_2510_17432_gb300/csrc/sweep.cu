@@ -275,12 +275,17 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       bulk_g2s(sp, g_zero_rows, zero_bytes, bar);
       return;
     }
-    mbar_arrive_tx(bar, 2u * (piece_bytes0 + piece_bytes1));
     const int64_t src0 = gy * row_units + pg0 * 2 * P;
+    const int64_t src1 = gy * row_units + pg1 * 2 * P;
+    if (!TBPM_DBG_OK(src0 + (int64_t)pn0 * 2 * P - 1, a.Ly * row_units, TBPM_DBG_SWEEP_ROW) ||
+        (pn1 > 0 && !TBPM_DBG_OK(src1 + (int64_t)pn1 * 2 * P - 1, a.Ly * row_units, TBPM_DBG_SWEEP_ROW))) {
+      mbar_arrive(bar);  // debug build: the row is not copied (the kernel's results are void)
+      return;
+    }
+    mbar_arrive_tx(bar, 2u * (piece_bytes0 + piece_bytes1));
     bulk_g2s(sn + 32u * pc0 * P, a.cur_in + src0, piece_bytes0, bar);
     bulk_g2s(sp + 32u * pc0 * P, a.prev_in + src0, piece_bytes0, bar);
     if (pn1 > 0) {
-      const int64_t src1 = gy * row_units + pg1 * 2 * P;
       bulk_g2s(sn + 32u * pc1 * P, a.cur_in + src1, piece_bytes1, bar);
       bulk_g2s(sp + 32u * pc1 * P, a.prev_in + src1, piece_bytes1, bar);
     }
@@ -462,7 +467,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
             xap[l] = Xprev[2 * (l - 1) * XU + wA + P];
           }
         }
-        if (intx && (unsigned)(iq - H) < (unsigned)ny) {
+        if (intx && (unsigned)(iq - H) < (unsigned)ny &&
+            TBPM_DBG_OK(off_r - (int64_t)(L - 1) * row_units, a.Ly * row_units, TBPM_DBG_SWEEP_STORE)) {
           if (WIN) {
             float4* dst = a.win[L - 1] + (off_r - (int64_t)(L - 1) * row_units);
             __stcs(dst, nA);
@@ -480,9 +486,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           }
         }
       }
-      if (WIN) {
-        off_r += row_units;
-      } else {
+      off_r += row_units;
+      if (!WIN) {
         out_km1 += row_units;
         out_k += row_units;
         if (++folded == C::FOLD) {
@@ -693,3 +698,5 @@ int sweep_status(tbpm_ctx* ctx) {
 }
 
 }  // namespace tbpm
+
+TBPM_DEBUG_UNIT(sweep)

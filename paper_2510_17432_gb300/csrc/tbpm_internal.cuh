@@ -18,7 +18,49 @@
 
 #include "../../include/tbpm.h"
 
+// ------------------------------------------------------------------ debug builds (TBPM_DEBUG)
+// A debug build (libtbpm_debug.so) checks the global-memory indices of the hot kernels: an index
+// outside its buffer is not accessed, and the first one is recorded in a device status word of
+// the translation unit ((kernel id << 48) | (index & 0xFFFFFFFFFFFF)); there is no trap, so the
+// context stays usable.  tbpm_debug_status() collects and clears the words of every unit.  In
+// the regular build the checks compile to nothing.
+enum {
+  TBPM_DBG_STENCIL = 1,     // k_moment_stencil: own and neighbour units
+  TBPM_DBG_ELL = 2,         // ELL neighbour index against the site count
+  TBPM_DBG_SWEEP_STORE = 3, // k_sweep_moments: output units
+  TBPM_DBG_SWEEP_ROW = 4,   // k_sweep_moments: source range of a row copy
+  TBPM_DBG_SERVE = 5        // k_serve_step: neighbour units
+};
+#ifdef TBPM_DEBUG
+static __device__ unsigned long long g_tbpm_dbg;
+__device__ __forceinline__ bool tbpm_dbg_ok(int64_t idx, int64_t n, int kid) {
+  if ((uint64_t)idx < (uint64_t)n) return true;
+  atomicCAS(&g_tbpm_dbg, 0ull, ((unsigned long long)kid << 48) | ((unsigned long long)idx & 0xFFFFFFFFFFFFull));
+  return false;
+}
+#define TBPM_DBG_OK(idx, n, kid) tbpm_dbg_ok((int64_t)(idx), (int64_t)(n), (kid))
+// host accessor of a unit's word (reads and clears it on the current device)
+#define TBPM_DEBUG_UNIT(name)                                                      \
+  namespace tbpm {                                                                 \
+  unsigned long long debug_take_##name() {                                         \
+    unsigned long long v = 0, z = 0;                                               \
+    if (cudaMemcpyFromSymbol(&v, g_tbpm_dbg, sizeof(v)) != cudaSuccess) v = ~0ull; \
+    cudaMemcpyToSymbol(g_tbpm_dbg, &z, sizeof(z));                                 \
+    return v;                                                                      \
+  }                                                                                \
+  }
+#else
+#define TBPM_DBG_OK(idx, n, kid) true
+#define TBPM_DEBUG_UNIT(name)
+#endif
+
 namespace tbpm {
+
+#ifdef TBPM_DEBUG
+unsigned long long debug_take_cheb();
+unsigned long long debug_take_sweep();
+unsigned long long debug_take_serve();
+#endif
 
 // ------------------------------------------------------------------ error reporting
 void set_error(const char* fmt, ...);
