@@ -1451,13 +1451,15 @@ int measure_pass_costs(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req
       cudaEventRecord(e[0], ctx->stream);
       for (int i = 0; i < reps && r == TBPM_OK; ++i) r = launch_accum_step(ctx, g, pl.precision, ACC_REGULAR);
       cudaEventRecord(e[1], ctx->stream);
+      // both flushes in the 16-accumulator tile of the block sizes being chosen between, so that
+      // the difference is the cost of the extra accumulators, not of another kernel
       for (int i = 0; i < reps && r == TBPM_OK; ++i)
         r = launch_block_flush(ctx, g.r, pl.precision, ctx->ws_blk.p, Tm, ctx->ws_acc.p, 1,
-                               (const double*)ctx->ws_blk_coef.p);
+                               (const double*)ctx->ws_blk_coef.p, 16);
       cudaEventRecord(e[2], ctx->stream);
       for (int i = 0; i < reps && r == TBPM_OK; ++i)
         r = launch_block_flush(ctx, g.r, pl.precision, ctx->ws_blk.p, Tm, ctx->ws_acc.p, k_acc,
-                               (const double*)ctx->ws_blk_coef.p);
+                               (const double*)ctx->ws_blk_coef.p, 16);
       cudaEvent_t e3;
       cudaEventCreate(&e3);
       cudaEventRecord(e3, ctx->stream);

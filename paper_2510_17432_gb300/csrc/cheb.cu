@@ -33,6 +33,7 @@ namespace tbpm {
 template <int KIND, bool CSR, typename R, int SPT>
 struct Row {
   int64_t base, up, dn, zup, zdn;
+  int32_t nb[6];  // ELL path, nearest-neighbour lists: the unit's indices, loaded one unit ahead
 };
 
 template <int KIND, bool CSR, typename R, int SPT>
@@ -51,7 +52,11 @@ __device__ __forceinline__ void neighbour_sum(const RecurrenceArgs& a, const Pac
   if constexpr (CSR) {
     const int z = a.geom.z;
     const int32_t* row = a.ell + site * z;
-    if (a.wrel) {
+    if (!a.wrel && z <= 6) {  // indices prefetched by the walk (for_each_unit)
+#pragma unroll
+      for (int d = 0; d < 6; ++d)
+        if (d < z) add((int64_t)rw.nb[d]);
+    } else if (a.wrel) {
       // long-range hopping: slot d carries the weight t_d / t
       const R* w = reinterpret_cast<const R*>(a.wrel);
       for (int d = 0; d < z; ++d) {
@@ -128,14 +133,29 @@ template <int KIND, bool CSR, typename R, int SPT, typename F>
 __device__ __forceinline__ void for_each_unit(const RecurrenceArgs& a, F f) {
   const int tid = threadIdx.x;
   if constexpr (CSR) {
+    // nearest-neighbour ELL lists: the indices of the next unit are loaded before the current
+    // unit's neighbours are gathered, so that the two dependent loads of a unit overlap with the
+    // previous unit's instead of following each other
     const int64_t n_units = a.n_sites * a.P;
     const int64_t n_tiles = (n_units + kThreads - 1) / kThreads;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int z = a.geom.z;
+    const bool pre = a.wrel == nullptr && z <= 6;
+    auto load_idx = [&](int64_t u, int32_t* dst) {
+      const int32_t* row = a.ell + (u >> a.logP) * z;
+#pragma unroll
+      for (int d = 0; d < 6; ++d) dst[d] = d < z ? __ldg(row + d) : -1;
+    };
+    Row<KIND, CSR, R, SPT> rw{};
+    int64_t t = blockIdx.x;
+    if (pre && t < n_tiles && t * kThreads + tid < n_units) load_idx(t * kThreads + tid, rw.nb);
+    for (; t < n_tiles; t += gridDim.x) {
       const int64_t u = t * kThreads + tid;
-      if (u < n_units) {
-        Row<KIND, CSR, R, SPT> rw{};
-        f(u >> a.logP, (int64_t)0, (int64_t)0, rw);
-      }
+      const int64_t un = (t + gridDim.x) * kThreads + tid;
+      int32_t nxt[6] = {-1, -1, -1, -1, -1, -1};
+      if (pre && t + gridDim.x < n_tiles && un < n_units) load_idx(un, nxt);
+      if (u < n_units) f(u >> a.logP, (int64_t)0, (int64_t)0, rw);
+#pragma unroll
+      for (int d = 0; d < 6; ++d) rw.nb[d] = nxt[d];
     }
   } else {
     const int64_t upr = a.geom.row_sites * a.P;
@@ -673,10 +693,12 @@ __global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, 
 // term.  grid: (accumulator tiles of EB, unit blocks); EB = 1, 4 or 16 accumulators per tile
 // (the registers of a tile's accumulators limit how many threads, and so how many buffer loads,
 // an SM keeps in flight: a one-accumulator flush, the sequential form's, runs at full occupancy).
-#ifndef TBPM_FLUSH_UNROLL
-#define TBPM_FLUSH_UNROLL 8
-#endif
-constexpr int kFlushUnroll = TBPM_FLUSH_UNROLL;
+// Buffer loads in flight per thread: 8 for the small tiles, 4 for 16 accumulators (whose registers
+// already bound the occupancy).
+template <int EB>
+struct FlushUnroll {
+  static constexpr int value = EB >= 16 ? 4 : 8;
+};
 
 template <typename R, int SPT, int EB>
 __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int T, int64_t stride_packs, void* accv,
@@ -703,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
 #pragma unroll
         for (int k = 0; k < 2 * SPT; ++k) acc[e].v[k] = R(0);
     }
-#pragma unroll (kFlushUnroll)
+#pragma unroll (FlushUnroll<EB>::value)
     for (int t = 0; t < T; ++t) {  // unrolled so that several buffer loads are in flight
       const PK x = ld(Phi + (int64_t)t * stride_packs + u);
 #pragma unroll
@@ -885,14 +907,14 @@ int launch_qe_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const
 }
 
 int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* acc,
-                       int nb, const double* coef) {
+                       int nb, const double* coef, int tile) {
   if (T < 1 || T > kQeMaxT || nb < 1) {
     set_error("block flush of %d terms into %d accumulators", T, nb);
     return TBPM_EINVAL;
   }
   const int spt = spt_of(precision, a.S);
   const int64_t n_units = a.n_sites * a.P;
-  const int eb = nb == 1 ? 1 : nb <= 4 ? 4 : 16;
+  const int eb = tile > 0 ? tile : (nb == 1 ? 1 : nb <= 4 ? 4 : 16);
   const int etiles = (nb + eb - 1) / eb;
   const int64_t want = std::max<int64_t>(1, (int64_t)ctx->num_sms * (eb == 16 ? 8 : 16) / etiles);
   const int ublocks = (int)std::min<int64_t>(std::min<int64_t>(want, (n_units + kThreads - 1) / kThreads), 65535);

@@ -350,8 +350,9 @@ size_t taps_partials_bytes(const RecurrenceArgs& a);
 int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& a, int precision, int mode);
 // acc_j += sum_{t<T} c_t(j) phi_t over T consecutive buffered state blocks phi and nb
 // consecutive accumulators; coef [T][nb] complex (csrc/cheb.cu)
+// tile: accumulators per CTA tile (1, 4 or 16); 0 = chosen from nb
 int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* phi, int T, void* acc,
-                       int nb, const double* coef);
+                       int nb, const double* coef, int tile = 0);
 int launch_dot(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const void* x, const void* y,
                double* out /* device [S][2] at stride out_stride */, int out_stride);
 int recurrence_blocks(tbpm_ctx* ctx, int precision, int S);
