@@ -40,6 +40,9 @@ WORKLOADS = {
     "graphene512": wl.Workload("honeycomb512x512_S8_M1024", wl.honeycomb(512, 512, t=-2.7), n_states=8,
                                n_moments=1024, precision=wl.C64, n_steps=300, n_energies=2048),
     "graphene22528": wl.GRAPHENE_22528,
+    # the 1.015e9-site workload's state count and disorder on a 2048 x 2048 lattice (profiling case)
+    "graphene2048_W1_S4": wl.Workload("honeycomb2048x2048_W1_S4_M256", wl.honeycomb(2048, 2048, t=-2.7, W=1.0),
+                                      n_states=4, n_moments=256, precision=wl.C64, n_steps=0, n_energies=1024),
     "square64": wl.SQUARE_64,
     "vacancy4096": wl.GRAPHENE_4096_VAC,
     "dense61": wl.dense_honeycomb(61),
