@@ -51,9 +51,6 @@ struct Cfg {
   static constexpr int NV = 4 * K;     // per level: {|a|^2, Re<n|a>} x 2 states
   static constexpr int FOLD = 16;      // positions per FP32 partial (32 unit terms per thread)
   static constexpr int MINB = NT <= 128 ? 3 : NT <= 192 ? 2 : 1;
-  // disordered lattices need a few more registers (the diagonal's ring): one CTA fewer per SM
-  // instead of spills in the sweep loop
-  static constexpr int MINB_DIAG = MINB > 1 ? MINB - 1 : 1;
   static constexpr int BAR_BYTES = ((NSLOT * 8 + 15) / 16) * 16;
   // ring slot: [P zero][phi_n row: 2 NT units][P zero][phi_{n-1} row: 2 NT units], padded to a
   // multiple of 8 units (128 bytes) so that every slot starts on the same bank
@@ -165,8 +162,7 @@ __device__ __forceinline__ void moment_terms(float2* acc2, float4 a, float4 n) {
 // WIN: window mode for the time blocks -- every level goes to its own buffer (a.win[L-1]) and no
 // moment is summed; otherwise levels K-1 and K go to prev_out, cur_out with the moments.
 template <int NT_, int K_, int NSLOT_, bool HAS_DIAG, bool OPEN, bool WIN = false>
-__global__ void __launch_bounds__(NT_, HAS_DIAG ? Cfg<NT_, K_, NSLOT_>::MINB_DIAG : Cfg<NT_, K_, NSLOT_>::MINB)
-    k_sweep_moments(Args a) {
+__global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_moments(Args a) {
   using C = Cfg<NT_, K_, NSLOT_>;
   constexpr int NT = C::NT, K = C::K, H = C::H, NSLOT = C::NSLOT, NV = C::NV;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -613,17 +609,10 @@ static int launch_sweep(tbpm_ctx* ctx, const tbpm_lattice* lat, const Recurrence
     return TBPM_EUNSUPPORTED;
   }
   a.nbx = (int)((a.Lx + a.BX - 1) / a.BX);
-  // resident CTAs per SM of the variant that runs (the disordered one keeps fewer)
-  static int per_sm_v[2] = {0, 0};
-  const bool dv = ra.diag != nullptr;
-  int& per_sm = per_sm_v[dv ? 1 : 0];
+  static int per_sm = 0;
   if (per_sm == 0) {
-    const cudaError_t oe =
-        dv ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_moments<NT, K, NSLOT, true, false>, NT,
-                                                           Cf::smem(4, true))
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_moments<NT, K, NSLOT, false, false>, NT,
-                                                           Cf::smem(4, false));
-    if (oe != cudaSuccess || per_sm < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_moments<NT, K, NSLOT, false, false>, NT,
+                                                      Cf::smem(4, false)) != cudaSuccess || per_sm < 1) {
       cudaGetLastError();
       per_sm = 1;
     }
