@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   float4* out_k = a.cur_out + (r0 - (K - 1)) * row_units + colA;
   int64_t off_r = r0 * row_units + colA;  // window mode: offset of row r in every level's buffer
   // ring slots of level-0 rows r and r+1 (a slot's phi_{n-1} row follows at + 2 NT + P)
-  int slot_0 = 0, slot_p1 = 1 % NSLOT;
+  int slot_m1 = 0, slot_0 = 0, slot_p1 = 1 % NSLOT;  // row r0 - 1 stands in as row r0
   uint32_t wait_par = NSLOT == 1 ? 1u : 0u;  // phase parity of row r+1's slot
 
   // disordered lattices: 2 D of row r in flight, stored into the ring at position r
@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       if (!mbar_wait(smem_u32(bars + slot_p1), wait_par)) timed_out = true;  // level-0 row r+1
       const float4* R0 = ring + slot_0 * SU + P;
       const float4* Rp = ring + slot_p1 * SU + P;
+      const float4* Rm_ = ring + slot_m1 * SU + P;  // row r-1 (disordered lattices)
       // x-neighbours of levels 1 .. K-1 written at the previous position, loaded before this
       // position writes the exchange row of the level before (the compiler cannot tell the two
       // parities apart): level 1's right away, the others once level 1 has been stored
@@ -418,14 +419,16 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           const float4 q1 = swp ? Rp[uA] : R0[uA + P], q2 = swp ? R0[uA + P] : Rp[uA];
           const float4 n1 = R0[o_n1], n2 = R0[o_n2];
           const float4 p1 = R0[o_p1], p2 = R0[o_p2];
-          ownA = c0A;
+          // disordered lattices: level-0 values of rows r and r-1 from the ring (the registers
+          // that would carry them go to the diagonal's prefetch)
+          ownA = HAS_DIAG ? R0[uA] : c0A;
           ownB = swp ? q2 : q1;
           ayp = swp ? q1 : q2;
           bxm = swp ? n2 : n1;
           axp = swp ? n1 : n2;
           pvA = swp ? p2 : p1;
           pvB = swp ? p1 : p2;
-          bym = prevB;
+          bym = HAS_DIAG ? Rm_[uA + P] : prevB;
           cmA = ownA;  // carried to the next position: row r becomes row r-1, A(r+1) becomes A(r)
           cmB = ownB;
           c0A = ayp;
@@ -437,8 +440,8 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
           bym = RB[L - 1][s2];
           ayp = RA[L - 1][s0];
           if (L == 2) {
-            pvA = prevA;
-            pvB = prevB;
+            pvA = HAS_DIAG ? Rm_[uA] : prevA;
+            pvB = HAS_DIAG ? Rm_[uA + P] : prevB;
           } else {
             pvA = RA[L - 2][s2];
             pvB = RB[L - 2][s2];
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
       i_done = i;
       // row r-1 has been read for the last time: refill its slot with row r - 1 + NSLOT
       if (tid == 0 && i >= 1) issue_next();
+      slot_m1 = slot_0;
       slot_0 = slot_p1;
       slot_p1 = slot_p1 + 1 == NSLOT ? 0 : slot_p1 + 1;
       if (slot_p1 == 0) wait_par ^= 1u;
