@@ -1999,12 +1999,19 @@ int apply_series_bufs(tbpm_ctx* ctx, tbpm_lattice* lat, const Plan& pc, void* b0
     TBPM_CK(cudaMemsetAsync(out, 0, pc.state_bytes, ctx->stream));
     TBPM_CK(cudaMemcpyAsync(slot(2), b0, pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     g.b = 0;
+    const bool sweep_win = sweep_window_applicable(lat, pc.precision, pc.Spad);
     for (int n = 1; n < n_terms; ++n) {
       if (n - n0 == T) {
         TBPM_TRY(launch_block_flush(ctx, g.r, pc.precision, slot(2), T, out, 1, coef + 2 * (size_t)n0));
         TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pc.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
         n0 = n;
+      }
+      if (sweep_win && n >= 2 && n + 3 < n_terms && n - n0 + 4 <= T) {  // terms n .. n+3 in one pass
+        void* const w[4] = {slot_of(n), slot_of(n + 1), slot_of(n + 2), slot_of(n + 3)};
+        TBPM_TRY(launch_sweep_window(ctx, lat, g.r, slot_of(n - 2), slot_of(n - 1), w));
+        n += 3;
+        continue;
       }
       g.r.cur = slot_of(n - 1);
       g.r.prev_out = n >= 2 ? slot_of(n - 2) : slot_of(n - 1);  // not read by the first step

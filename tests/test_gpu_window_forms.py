@@ -95,3 +95,20 @@ def test_optical_conductivity_through_window_passes(capi, ctx, form, b):
         Cref = R.oc_correlation_sequential(ol, psi[s], alpha, beta, mu, kT, Nt)
         assert np.max(np.abs(C[s] - Cref)) / np.max(np.abs(Cref)) <= 3e-5, s
     capi.tbpm_lattice_destroy(lat)
+
+
+@pytest.mark.parametrize("sqrt_f", [0, 1])
+def test_fermi_operator_through_window_passes(capi, ctx, sqrt_f):
+    """The Fermi-Dirac series (its buffered terms through the window passes) against the exact
+    operator from the eigen-decomposition."""
+    lat, ol = _lattice(capi, ctx, QE_SPEC)
+    S = 4
+    mu = ol.H0 + 0.2 * (ol.E_max - ol.E_min) / 2
+    kT = 0.05 * (ol.E_max - ol.E_min) / 2
+    out = np.zeros((S, ol.n), np.complex64)
+    capi.tbpm_fermi_apply(ctx, lat, capi.request(n_states=S, precision=0, state_seed=9), mu, kT, sqrt_f, out)
+    psi = oprop.random_phase_states(ol, 9, S)
+    for s in (0, S - 1):
+        ref = R.fermi_operator_exact(ol, psi[s], mu, kT, power=0.5 if sqrt_f else 1.0)
+        assert np.max(np.abs(out[s] - ref)) / np.max(np.abs(ref)) <= 3e-5, s
+    capi.tbpm_lattice_destroy(lat)
