@@ -1887,12 +1887,19 @@ int run_ec(tbpm_ctx* ctx, tbpm_lattice* lat, const tbpm_request* req, const Plan
       int64_t n0 = 0;
       auto slot_of = [&](int64_t t) { return t >= n0 ? slot(2 + (t - n0)) : (t == n0 - 1 ? slot(1) : slot(0)); };
       TBPM_CK(cudaMemcpyAsync(slot(2), ctx->ws_jpsi.p, pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      const bool sweep_win = sweep_window_applicable(lat, pl.precision, pl.Spad);
       for (int64_t k = 1; k < Nn; ++k) {
         if (k - n0 == T) {
           TBPM_TRY(launch_xdot(ctx, pl.precision, pl.Spad, n, slot(2), T, kets, nE, m, (int64_t)nE * Nn, 1, Nn, n0));
           TBPM_CK(cudaMemcpyAsync(slot(0), slot(T), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
           TBPM_CK(cudaMemcpyAsync(slot(1), slot(T + 1), pl.state_bytes, cudaMemcpyDeviceToDevice, ctx->stream));
           n0 = k;
+        }
+        if (sweep_win && k >= 2 && k + 3 < Nn && k - n0 + 4 <= T) {  // terms k .. k+3 in one pass
+          void* const w[4] = {slot_of(k), slot_of(k + 1), slot_of(k + 2), slot_of(k + 3)};
+          TBPM_TRY(launch_sweep_window(ctx, lat, g.r, slot_of(k - 2), slot_of(k - 1), w));
+          k += 3;
+          continue;
         }
         g.r.cur = slot_of(k - 1);
         g.r.prev_out = k >= 2 ? slot_of(k - 2) : slot_of(k - 1);  // not read by the first step

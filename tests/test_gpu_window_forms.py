@@ -75,6 +75,26 @@ def test_conductivity_through_window_passes(capi, ctx, form, b):
     capi.tbpm_lattice_destroy(lat)
 
 
+def test_conductivity_moment_form_through_window_passes(capi, ctx):
+    """Concurrent-M form: the moments m_n(E) of J psi take four Chebyshev terms per window pass
+    into the buffered slots; compared with the oracle's moment form term by term of C(t, E)."""
+    lat, ol = _lattice(capi, ctx, QE_SPEC)
+    S, Nt, direction = 4, 15, 1
+    E = ol.H0 + np.array([-0.6, 0.05, 0.4]) * (ol.E_max - ol.E_min) / 2
+    C = np.zeros((S, E.size, Nt + 1), np.complex128)
+    sigma = np.zeros((S, E.size))
+    capi.tbpm_conductivity(ctx, lat, capi.request(n_states=S, precision=0, form=1, n_steps=Nt, state_seed=13),
+                           direction, E, C, sigma)
+    psi = oprop.random_phase_states(ol, 13, S)
+    for s in (0, S - 1):
+        m, qe = oec.ec_moments(ol, psi[s], E, Nt, direction)
+        Cref = oec.ec_correlation_from_moments(ol, m, qe, psi[s], Nt)
+        for k in range(E.size):
+            err = np.max(np.abs(C[s, k] - Cref[k])) / np.max(np.abs(Cref[k]))
+            assert err <= 3e-5, ("C", s, k, err)
+    capi.tbpm_lattice_destroy(lat)
+
+
 OC_SPEC = dict(kind=1, L=(48, 32), t=-2.7, W=1.0, seed=52)  # 4 states: a pair block of 8, band of 32 cells
 
 
