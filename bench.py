@@ -108,6 +108,9 @@ def parse():
     p.add_argument("--serving-requests", type=int, default=512,
                    help="requests of the serving leg (reduced to fit --serving-budget-s, stated in the line)")
     p.add_argument("--serving-budget-s", type=float, default=150.0)
+    p.add_argument("--no-c128", action="store_true", help="state-based workloads: complex64 only")
+    p.add_argument("--no-state-based", action="store_true",
+                   help="skip the time-block leg (vacancy graphene 4096^2) of the default line")
     p.add_argument("--no-largest", action="store_true",
                    help="skip the 1.015e9-site honeycomb leg (S = 4, M = 8192) of the default line")
     p.add_argument("--prof-steps", type=int, default=2,
@@ -620,6 +623,12 @@ def run_gpu(args, work):
         except Exception as exc:  # the headline number stands; say why this leg is missing
             out["largest_config"] = {"workload": wl.GRAPHENE_22528.name, "failed": f"{exc!r}"[:300]}
 
+    if rank == 0 and not args.no_state_based and work is wl.GRAPHENE_2048:
+        try:
+            out["state_based"] = state_based_leg(capi, ctx, args)
+        except Exception as exc:
+            out["state_based"] = {"workload": wl.GRAPHENE_4096_VAC.name, "failed": f"{exc!r}"[:300]}
+
     if rank == 0 and not args.no_cpu and world == 1:
         try:
             out["cpu_baseline"] = cpu_baseline_obj(work, oracle_sample(work, args.cpu_seconds))
@@ -739,6 +748,90 @@ def state_based_bytes_buffered(n_steps: int, b: int, tau: float, trunc, n_sites,
     return total
 
 
+def time_block_forms(capi, ctx, lat, spec, N, S, Nt, prec, warmup, reps, peak, seed=1, seq_warmup=1) -> dict:
+    """C(t_j), j <= Nt, at tau~ = pi through the state-based time-block form (b autotuned from
+    measured pass costs) and the sequential form on one lattice in one precision: seconds per
+    call (CUDA events on the library stream, inputs resident), matrix applications, launches,
+    site-updates/s, HBM fraction by the byte model, and the largest relative C difference."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
+    elem, dbytes = (8, 4) if prec == capi.C64 else (16, 8)
+    tau = math.pi
+    trunc = capi.tbpm_truncation_order
+    z = wl.COORDINATION[spec.kind]
+
+    def timed_corr(form, b, n_warm, n_reps):
+        req = capi.request(n_states=S, precision=prec, form=form, n_steps=Nt, time_block=b, state_seed=seed)
+        d_C = torch.empty((max(S, 1), Nt + 1, 2), device=dev, dtype=torch.float64)
+        for _ in range(n_warm):
+            capi.tbpm_correlation_device(ctx, lat, req, d_C)
+        capi.tbpm_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = capi.tbpm_launch_count(ctx)
+        e0.record(stream)
+        for _ in range(n_reps):
+            capi.tbpm_correlation_device(ctx, lat, req, d_C)
+        e1.record(stream)
+        capi.tbpm_sync(ctx)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / n_reps, (capi.tbpm_launch_count(ctx) - l0) // n_reps, d_C.cpu().numpy()
+
+    b_opt, t_a, t_x = capi.tbpm_block_autotune(ctx, lat, capi.request(n_states=S, precision=prec, form=2,
+                                                                        n_steps=Nt, state_seed=seed), Nt)
+    res = {}
+    for name, form, b in (("concurrent_s", capi.CONCURRENT_S, b_opt), ("sequential", capi.SEQUENTIAL, 1)):
+        n_reps = reps if name == "concurrent_s" else 1
+        n_warm = (warmup if n_reps > 1 else 1) if name == "concurrent_s" else seq_warmup
+        sec, launches, C = timed_corr(form, b, n_warm, n_reps)
+        apps, passes, blocks = state_based_schedule(Nt, b, tau, trunc)
+        if b >= 2:  # buffered time blocks (the library's default for b >= 2)
+            alg = state_based_bytes_buffered(Nt, b, tau, trunc, N, S, elem, z, dbytes if spec.W != 0 else 0)
+        else:
+            alg = state_based_bytes(passes, blocks, N, S, elem, z, dbytes if spec.W != 0 else 0, Nt)
+        res[name] = {"b": b, "seconds": sec, "reps": n_reps, "matrix_applications": apps, "launches": launches,
+                     "site_updates_per_s": apps * N * S / sec, "algorithmic_gbs": alg / sec / 1e9,
+                     "frac_of_hbm": alg / sec / 1e9 / peak, "C": C}
+    diff = float(np.max(np.abs(res["concurrent_s"]["C"] - res["sequential"]["C"])) /
+                 np.max(np.abs(res["sequential"]["C"])))
+    for r in res.values():
+        r.pop("C")
+    return {"t_amxsy_ms": t_a, "t_axpy_ms": t_x, "b_opt": b_opt, **res,
+            "speedup_wall": res["sequential"]["seconds"] / res["concurrent_s"]["seconds"],
+            "max_rel_correlation_difference": diff}
+
+
+def state_based_leg(capi, ctx, args) -> dict:
+    """Time evolution on graphene 4096 x 4096 with 1 % vacancies and V in [-1, 1] eV (33.2M sites
+    on the ELL path), one complex64 state, Nt = 2048 steps at the Nyquist step tau~ = pi: the
+    state-based time-block form against the sequential form, one timed call each."""
+    work = wl.GRAPHENE_4096_VAC
+    spec = work.lattice
+    desc = capi.lattice_desc(spec.kind, spec.L, t=spec.t, W=spec.W, vacancy_frac=spec.vacancy_frac,
+                             seed=spec.seed, pbc=spec.pbc, path=spec.path)
+    t0 = time.perf_counter()
+    lat = capi.tbpm_lattice_create(ctx, desc)
+    capi.tbpm_sync(ctx)
+    build_s = time.perf_counter() - t0
+    try:
+        info = capi.tbpm_lattice_info(lat)
+        peak, peak_kind = measured_hbm_peak()
+        import torch
+        clocks = Clocks(torch.cuda.current_device())
+        clocks.start()
+        forms = time_block_forms(capi, ctx, lat, spec, info.n_sites, work.n_states, work.n_steps, capi.C64,
+                                 1, 1, peak, seed=1, seq_warmup=0)
+        clk = clocks.stop()
+    finally:
+        capi.tbpm_lattice_destroy(lat)
+    return {"workload": work.name, "sites": info.n_sites, "states": work.n_states, "n_steps": work.n_steps,
+            "tau": "pi", "precision": "c64", "path": "ELL (vacancies)", "lattice_build_s": build_s,
+            "peak_gbs": peak, "peak_source": peak_kind, **forms, "clocks": clk,
+            "timing": "CUDA events on the library stream; one warm-up call of the time-block form, none "
+                      "of the sequential form (same kernels)"}
+
+
 def run_state_based(args, work):
     import torch
     from paper_2510_17432_gb300 import capi
@@ -758,54 +851,15 @@ def run_state_based(args, work):
     lat = capi.tbpm_lattice_create(ctx, desc)
     info = capi.tbpm_lattice_info(lat)
     N, S, Nt = info.n_sites, work.n_states, work.n_steps
-    stream = torch.cuda.ExternalStream(capi.tbpm_stream(ctx), device=dev)
-    tau = math.pi
-    trunc = capi.tbpm_truncation_order
-    z = wl.COORDINATION[spec.kind]
-
-    def timed_corr(prec, form, b, reps):
-        req = capi.request(n_states=S, precision=prec, form=form, n_steps=Nt, time_block=b, state_seed=1 + rank)
-        d_C = torch.empty((max(S, 1), Nt + 1, 2), device=dev, dtype=torch.float64)
-        for _ in range(args.warmup if reps > 1 else 1):
-            capi.tbpm_correlation_device(ctx, lat, req, d_C)
-        capi.tbpm_sync(ctx)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0 = capi.tbpm_launch_count(ctx)
-        e0.record(stream)
-        for _ in range(reps):
-            capi.tbpm_correlation_device(ctx, lat, req, d_C)
-        e1.record(stream)
-        capi.tbpm_sync(ctx)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / reps, (capi.tbpm_launch_count(ctx) - l0) // reps, d_C.cpu().numpy()
 
     out_forms = {}
     peak, peak_kind = measured_hbm_peak()
     clocks = Clocks(local)
     clocks.start()
-    for prec, elem, dbytes in ((capi.C64, 8, 4), (capi.C128, 16, 8)):
-        b_opt, t_a, t_x = capi.tbpm_block_autotune(ctx, lat, capi.request(n_states=S, precision=prec, form=2,
-                                                                            n_steps=Nt, state_seed=1), Nt)
-        res = {}
-        for name, form, b in (("concurrent_s", capi.CONCURRENT_S, b_opt), ("sequential", capi.SEQUENTIAL, 1)):
-            reps = args.steps if (prec == capi.C64 and name == "concurrent_s") else 1
-            sec, launches, C = timed_corr(prec, form, b, reps)
-            apps, passes, blocks = state_based_schedule(Nt, b, tau, trunc)
-            if b >= 2:  # buffered time blocks (the library's default for b >= 2)
-                alg = state_based_bytes_buffered(Nt, b, tau, trunc, N, S, elem, z, dbytes if spec.W != 0 else 0)
-            else:
-                alg = state_based_bytes(passes, blocks, N, S, elem, z, dbytes if spec.W != 0 else 0, Nt)
-            res[name] = {"b": b, "seconds": sec, "matrix_applications": apps, "launches": launches,
-                         "site_updates_per_s": apps * N * S / sec, "algorithmic_gbs": alg / sec / 1e9,
-                         "frac_of_hbm": alg / sec / 1e9 / peak, "C": C}
-        diff = float(np.max(np.abs(res["concurrent_s"]["C"] - res["sequential"]["C"])) /
-                     np.max(np.abs(res["sequential"]["C"])))
-        for r in res.values():
-            r.pop("C")
-        out_forms["c64" if prec == capi.C64 else "c128"] = {
-            "t_amxsy_ms": t_a, "t_axpy_ms": t_x, "b_opt": b_opt, **res,
-            "speedup_wall": res["sequential"]["seconds"] / res["concurrent_s"]["seconds"],
-            "max_rel_correlation_difference": diff}
+    for prec in ((capi.C64,) if args.no_c128 else (capi.C64, capi.C128)):
+        reps = {capi.C64: args.steps, capi.C128: 1}
+        out_forms["c64" if prec == capi.C64 else "c128"] = time_block_forms(
+            capi, ctx, lat, spec, N, S, Nt, prec, args.warmup, reps[prec], peak, seed=1 + rank)
     clk = clocks.stop()
 
     # DC conductivity and quasi-eigenstates at the workload's energies (complex64), all three EC forms

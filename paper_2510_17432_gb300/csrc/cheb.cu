@@ -584,6 +584,149 @@ __global__ void __launch_bounds__(kThreads) k_accum_step(AccumArgs g) {
   });
 }
 
+// ------------------------------------------------------------------ nearest-neighbour ELL step
+// One Chebyshev step phi_{n+1} = 2 H~ phi_n - phi_{n-1} (phi_1 = H~ phi_0) on the compact ELL
+// lists of a nearest-neighbour lattice with vacancies: with no accumulator and no inner product
+// (MOM = false: the recurrence pass of the buffered time blocks and of the sequential form), or
+// with the moment inner products of k_moment_step (MOM = true; FP32 partial sums over at most 32
+// units per thread folded into FP64, then the deterministic grid reduction).  A CTA takes tiles
+// of UPT x 256 units; thread t owns units t, t + 256, ... of the tile, so every load and store of
+// a warp is one contiguous run.  All z index loads of the UPT units are issued first, then the
+// own, previous and diagonal loads, then all z gathers, and only then the arithmetic: UPT (z + 3)
+// independent loads in flight per thread, where the generic walk has two dependent rounds per
+// unit; the index loads of the next tile are issued before the gathers of the current one.  Unit
+// offsets are 32-bit (the host takes this kernel only below 2^31 - 2^24 units).
+constexpr int kEllUPT = 4;
+
+template <typename R, int SPT, int Z, bool FIRST, bool MOM>
+__global__ void __launch_bounds__(kThreads) k_ell_step(RecurrenceArgs a) {
+  using PK = Pack<R, SPT>;
+  constexpr int UPT = kEllUPT, TU = UPT * kThreads;
+  const PK* __restrict__ cur = reinterpret_cast<const PK*>(a.cur);
+  const PK* prev = reinterpret_cast<const PK*>(a.prev_out);  // may be the output (in place)
+  PK* out = reinterpret_cast<PK*>(a.next ? a.next : a.prev_out);
+  const R* __restrict__ diag = reinterpret_cast<const R*>(a.diag);
+  const int32_t* __restrict__ ell = a.ell;
+  const int logP = a.logP, p = threadIdx.x & (a.P - 1);
+  const int n_units = (int)(a.n_sites << logP);
+  const R th = coef_th<R>(a, FIRST);
+  const R dc = coef_dc<R>(a, true);
+  Partial<R> A[SPT], Br[SPT], Bi[SPT];
+  int fold = 0;
+  const int stride = gridDim.x * TU;
+  // the index lists of a tile are loaded one tile ahead, so that their round trip overlaps with
+  // the gathers of the tile before
+  auto load_idx = [&](int b0, int (&nbo)[UPT][Z], int (&so)[UPT]) {
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+      const int u = b0 + k * kThreads + (int)threadIdx.x;
+      so[k] = u < n_units ? (u >> logP) : -1;
+#pragma unroll
+      for (int d = 0; d < Z; ++d) nbo[k][d] = so[k] >= 0 ? __ldg(ell + (int64_t)so[k] * Z + d) : -1;
+    }
+  };
+  int nb[UPT][Z];
+  int site[UPT];
+  load_idx(blockIdx.x * TU, nb, site);
+  for (int base = blockIdx.x * TU; base < n_units; base += stride) {
+    int nbn[UPT][Z];
+    int siten[UPT];
+    load_idx(base + stride, nbn, siten);  // base + stride < 2^31: the host bounds the unit count
+    PK ph[UPT], pv[UPT];
+    R dd[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+      const int u = base + k * kThreads + (int)threadIdx.x;
+      if (site[k] >= 0) {
+        ph[k] = ld(cur + u);
+        if (!FIRST) pv[k] = ld_stream(prev + u);
+        dd[k] = diag ? __ldg(diag + site[k]) : dc;
+      }
+    }
+    PK h[UPT];
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+#pragma unroll
+      for (int q = 0; q < 2 * SPT; ++q) h[k].v[q] = R(0);
+#pragma unroll
+      for (int d = 0; d < Z; ++d) {
+        const int j = nb[k][d];
+        if (j >= 0 && TBPM_DBG_OK(j, a.n_sites, TBPM_DBG_ELL)) {
+          const PK q = ld(cur + (((int64_t)j << logP) + p));
+#pragma unroll
+          for (int c = 0; c < 2 * SPT; ++c) h[k].v[c] += q.v[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+      if (site[k] < 0) continue;
+      const int u = base + k * kThreads + (int)threadIdx.x;
+      R d = dd[k];
+      if (!FIRST) d = d + d;
+      PK o;
+      if constexpr (FIRST) {
+#pragma unroll
+        for (int c = 0; c < 2 * SPT; ++c) o.v[c] = d * ph[k].v[c] + th * h[k].v[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 2 * SPT; ++c) o.v[c] = d * ph[k].v[c] + th * h[k].v[c] - pv[k].v[c];
+      }
+      st(out + u, o);
+      if constexpr (MOM) {
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          const R pr = ph[k].v[2 * q], pi = ph[k].v[2 * q + 1], orr = o.v[2 * q], oi = o.v[2 * q + 1];
+          A[q].add(pr * pr + pi * pi);
+          Br[q].add(orr * pr + oi * pi);
+          Bi[q].add(orr * pi - oi * pr);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+      site[k] = siten[k];
+#pragma unroll
+      for (int d = 0; d < Z; ++d) nb[k][d] = nbn[k][d];
+    }
+    if constexpr (MOM) {
+      if (++fold == 32 / UPT) {
+        fold = 0;
+#pragma unroll
+        for (int q = 0; q < SPT; ++q) {
+          A[q].fold();
+          Br[q].fold();
+          Bi[q].fold();
+        }
+      }
+    }
+  }
+  if constexpr (MOM) {
+    double v[3 * SPT];
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+      v[3 * q] = A[q].value();
+      v[3 * q + 1] = Br[q].value();
+      v[3 * q + 2] = Bi[q].value();
+    }
+    double* mu = a.mu;
+    const int M = a.M, n = a.step;
+    grid_reduce<3 * SPT, SPT, 3>(v, a.P, a.S, a.partials, a.counter, a.nblocks, [&](int q, double val) {
+      const int s = q / 3, c = q - 3 * s;
+      double* ms = mu + (size_t)s * M * 2;
+      if (FIRST) {
+        if (c == 0) { ms[0] = val; ms[1] = 0.0; }
+        else if (c == 1) ms[2] = val;
+        else ms[3] = val;
+      } else {
+        if (c == 0) { ms[4 * n] = 2.0 * val - ms[0]; ms[4 * n + 1] = -ms[1]; }
+        else if (c == 1) ms[4 * n + 2] = 2.0 * val - ms[2];
+        else ms[4 * n + 3] = 2.0 * val - ms[3];
+      }
+    });
+  }
+}
+
 // ------------------------------------------------------------------ plain dot <x|y> per state
 template <typename R, int SPT>
 __global__ void __launch_bounds__(kThreads) k_dot(RecurrenceArgs a, const void* xv, const void* yv,
@@ -780,6 +923,22 @@ static void* accum_kernel_m(int kind, bool csr) {
   }
 }
 
+template <typename R, int SPT, bool MOM>
+static void* ell_step_kernel(int z, bool first) {
+  if (z == 3) return first ? (void*)k_ell_step<R, SPT, 3, true, MOM> : (void*)k_ell_step<R, SPT, 3, false, MOM>;
+  if (z == 4) return first ? (void*)k_ell_step<R, SPT, 4, true, MOM> : (void*)k_ell_step<R, SPT, 4, false, MOM>;
+  return first ? (void*)k_ell_step<R, SPT, 6, true, MOM> : (void*)k_ell_step<R, SPT, 6, false, MOM>;
+}
+
+// the batched nearest-neighbour ELL kernel applies: ELL lists without per-slot weights, z of
+// 3, 4 or 6, fewer than 2^31 - 2^24 units
+static bool ell_batched(const RecurrenceArgs& a) {
+  const int z = a.geom.z;
+  return a.path == TBPM_PATH_CSR && !a.wrel && (z == 3 || z == 4 || z == 6) &&
+         a.n_sites * a.P < (int64_t)INT32_MAX - (int64_t)(1 << 24);
+}
+
+
 template <typename R, int SPT>
 static void* accum_kernel(int kind, bool csr, int mode) {
   if (mode == ACC_FIRST) return accum_kernel_m<R, SPT, ACC_FIRST>(kind, csr);
@@ -829,10 +988,25 @@ static int launch(tbpm_ctx* ctx, void* fn, int nblocks, void** args) {
   return TBPM_OK;
 }
 
+template <bool MOM>
+static int launch_ell(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first) {
+  const int spt = spt_of(precision, a.S);
+  void* fe;
+  if (precision == TBPM_C128) fe = ell_step_kernel<double, 1, MOM>(a.geom.z, first);
+  else if (spt == 2) fe = ell_step_kernel<float, 2, MOM>(a.geom.z, first);
+  else fe = ell_step_kernel<float, 1, MOM>(a.geom.z, first);
+  RecurrenceArgs ra = a;
+  // the moment partials are sized for recurrence_blocks() CTAs
+  ra.nblocks = persistent_grid(ctx, fe, (a.n_sites * a.P + kEllUPT * kThreads - 1) / (kEllUPT * kThreads));
+  void* args[] = {&ra};
+  return launch(ctx, fe, ra.nblocks, args);
+}
+
 int launch_moment_step(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, bool first) {
   const bool csr = a.path == TBPM_PATH_CSR;
   const int spt = spt_of(precision, a.S);
   if (a.taps && precision == TBPM_C64 && spt == 2) return launch_taps_moment(ctx, a, first);
+  if (ell_batched(a)) return launch_ell<true>(ctx, a, precision, first);
   void* fn;
   if (precision == TBPM_C128) fn = moment_kernel<double, 1>(a.geom.kind, csr, first);
   else if (spt == 2) fn = moment_kernel<float, 2>(a.geom.kind, csr, first);
@@ -852,6 +1026,8 @@ int launch_accum_step(tbpm_ctx* ctx, const AccumArgs& g, int precision, int mode
     if (g.j_lo >= g.b && g.j_done < 0) return TBPM_OK;
     mode = ACC_NOSPMV;
   }
+  if (mode != ACC_NOSPMV && g.j_lo >= g.b && g.j_done < 0 && ell_batched(g.r))
+    return launch_ell<false>(ctx, g.r, precision, mode == ACC_FIRST);  // a plain step, loads batched
   void* fn;
   if (precision == TBPM_C128) fn = accum_kernel<double, 1>(g.r.geom.kind, csr, mode);
   else if (spt == 2) fn = accum_kernel<float, 2>(g.r.geom.kind, csr, mode);
