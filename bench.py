@@ -1224,14 +1224,19 @@ def run_dense(args, work):
     props = torch.cuda.get_device_properties(dev)
     sm_count, lanes = props.multi_processor_count, 128
     sm_mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-    alu_peak = sm_count * lanes * sm_mhz * 1e6 * 2 / 1e12
+    derived_peak = sm_count * lanes * sm_mhz * 1e6 * 2 / 1e12
+    fma_scalar, fma_packed = capi.tbpm_fp32_fma_peak(ctx)
+    alu_peak = max(fma_scalar, fma_packed)
     pass_kind = capi.tbpm_moment_pass_kind(ctx, lat, req)
     if pass_kind == capi.PASS_TAPS:
         achieved = flops_per_launch / (per_launch_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak, "traffic": None,
-                    "peak_source": f"derived: {sm_count} SMs (device) x {lanes} FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
-                                   "(median SM clock sampled during the timed region)",
+                    "peak_source": "measured: FMA chains on this device (tbpm_fp32_fma_peak), the larger of "
+                                   f"scalar {fma_scalar:.1f} and packed f32x2 {fma_packed:.1f} TFLOP/s",
+                    "derived_peak_tflops": derived_peak,
+                    "derived_peak_source": f"{sm_count} SMs (device) x {lanes} FP32 lanes x 2 flops x {sm_mhz:.0f} MHz "
+                                           "(median SM clock sampled during the timed region)",
                     "kernel": f"k_taps_moment<{wl.KIND_NAMES[spec.kind]}> (matrix-free taps, two complex64 states per pack)",
                     "algorithmic_flops_per_launch": flops_per_launch, "avg_launch_us": per_launch_ms * 1e3,
                     "hbm_algorithmic_gbs": state_bytes / (per_launch_ms / 1e3) / 1e9, "hbm_peak_gbs": peak,
@@ -1244,6 +1249,7 @@ def run_dense(args, work):
                     "kernel": f"k_moment_step<CSR> (ELL lists + per-slot weights, {wl.KIND_NAMES[spec.kind]})",
                     "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_us": per_launch_ms * 1e3,
                     "fp32_tflops": flops_per_launch / (per_launch_ms / 1e3) / 1e12, "fp32_peak_tflops": alu_peak,
+                    "fp32_peak_source": "measured (tbpm_fp32_fma_peak)",
                     "recurrence_share_of_step": prof["recurrence_ms"] / dev_ms}
     out = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s", "n_gpus": world,

@@ -258,6 +258,12 @@ int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t);
  * and synchronises the device.  The regular library returns TBPM_EUNSUPPORTED and zero words. */
 int tbpm_debug_status(tbpm_ctx* ctx, uint64_t words[3]);
 
+/* Measured FP32 FMA throughput of the context's device in TFLOP/s (an FMA counts as two flops),
+ * scalar FMAs and packed f32x2 FMAs: the denominator of the roofline of the FP32-issue-bound tap
+ * kernel (the paper has no counterpart; it reports CPU times).  Runs about a millisecond of
+ * FMA chains on the context stream and synchronises it. */
+int tbpm_fp32_fma_peak(tbpm_ctx* ctx, double* tflops_scalar, double* tflops_packed);
+
 enum { TBPM_PASS_STENCIL = 0, TBPM_PASS_ELL = 1, TBPM_PASS_TAPS = 2, TBPM_PASS_SWEEP = 3, TBPM_PASS_ROWS = 4,
        TBPM_PASS_TILES = 5 };
 int tbpm_moment_pass_kind(tbpm_ctx* ctx, const tbpm_lattice* lat, const tbpm_request* req, int* kind);

@@ -19,8 +19,8 @@ LIB = os.path.join(HERE, "libtbpm.so")
 BUILD_DEBUG = os.path.join(HERE, "_build_debug")
 LIB_DEBUG = os.path.join(HERE, "libtbpm_debug.so")  # index-checked build (TBPM_DEBUG)
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["api.cu", "cheb.cu", "conduct.cu", "fused.cu", "recon.cu", "recon_tc.cu", "response.cu", "serve.cu",
-           "sweep.cu", "taps.cu"]
+SOURCES = ["api.cu", "cheb.cu", "conduct.cu", "fused.cu", "recon.cu", "recon_tc.cu", "peak.cu", "response.cu",
+           "serve.cu", "sweep.cu", "taps.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                 "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

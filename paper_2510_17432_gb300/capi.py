@@ -105,6 +105,7 @@ def _bind(lib):
         "tbpm_lattice_export": (C.c_int, [_P, _P, _P, _P]),
         "tbpm_lattice_taps": (C.c_int, [_P, _P, _P]),
         "tbpm_moment_pass_kind": (C.c_int, [_P, _P, C.POINTER(Request), C.POINTER(C.c_int)]),
+        "tbpm_fp32_fma_peak": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tbpm_debug_status": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
         "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
         "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
@@ -153,7 +154,7 @@ def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
-            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_debug_status", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_fp32_fma_peak", "tbpm_debug_status", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_conductivity_overlap",
             "tbpm_fermi_apply",
@@ -366,6 +367,13 @@ def tbpm_moment_pass_kind(ctx, lat, req: Request) -> int:
     k = C.c_int(0)
     _check(load().tbpm_moment_pass_kind(ctx, lat, C.byref(req), C.byref(k)))
     return k.value
+
+
+def tbpm_fp32_fma_peak(ctx) -> tuple:
+    """Measured FP32 FMA throughput (scalar, packed f32x2) of the context's device in TFLOP/s."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(load().tbpm_fp32_fma_peak(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def tbpm_conductivity_overlap(ctx, lat, req: Request, direction: int, energies: np.ndarray,

@@ -890,6 +890,107 @@ __global__ void __launch_bounds__(kThreads) k_block_flush(const void* phiv, int 
   }
 }
 
+// Complex64 flush of a tile of EB >= 4 accumulators with packed f32x2 FMAs.  The coefficient
+// table holds (Re c, Re c, Im c, Im c) per term and accumulator, so one broadcast shared load
+// feeds every state of the thread's U units, each with two packed FMAs:
+//   (acc_re, acc_im) += Re c (x_re, x_im) + Im c (-x_im, x_re).
+// Per term and accumulator that is 2 SPT U FMA instructions and 1 / (SPT U) shared loads per
+// state, where the scalar flush above issues 4 FMAs and 2 shared loads per state.
+template <int SPT, int EB, int U, int TB>
+__global__ void __launch_bounds__(kThreads, 2) k_block_flush_c64(const void* phiv, int T, int64_t stride_packs,
+                                                              void* accv, int nb, const double* coef,
+                                                              int64_t n_units) {
+  using PK = Pack<float, SPT>;
+  __shared__ float4 cf[kQeMaxT][EB];
+  const int e0 = blockIdx.x * EB;
+  const int ne = min(EB, nb - e0);
+  for (int i = threadIdx.x; i < T * EB; i += kThreads) {
+    const int t = i / EB, e = i - t * EB;
+    const bool ok = e < ne;
+    const float cr = ok ? (float)coef[((int64_t)t * nb + e0 + e) * 2] : 0.f;
+    const float ci = ok ? (float)coef[((int64_t)t * nb + e0 + e) * 2 + 1] : 0.f;
+    cf[t][e] = make_float4(cr, cr, ci, ci);
+  }
+  __syncthreads();
+  const PK* Phi = reinterpret_cast<const PK*>(phiv);
+  PK* Q = reinterpret_cast<PK*>(accv);
+  const int64_t step = (int64_t)gridDim.y * kThreads * U;
+  for (int64_t ub = (int64_t)blockIdx.y * kThreads * U + threadIdx.x; ub < n_units; ub += step) {
+    bool valid[U];
+    float2 ac[U][EB][SPT];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      valid[k] = ub + k * kThreads < n_units;
+#pragma unroll
+      for (int e = 0; e < EB; ++e) {
+        PK q;
+        if (valid[k] && e < ne) q = ld(Q + (int64_t)(e0 + e) * stride_packs + ub + k * kThreads);
+        else
+#pragma unroll
+          for (int c = 0; c < 2 * SPT; ++c) q.v[c] = 0.f;
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) ac[k][e][s] = make_float2(q.v[2 * s], q.v[2 * s + 1]);
+      }
+    }
+    // the buffered vectors are read TB terms at a time, all loads issued before the FMAs, so
+    // that TB loads per thread are in flight (the flush streams T + 2 ne state blocks)
+    for (int t0 = 0; t0 < T; t0 += TB) {
+      PK x[TB][U];
+#pragma unroll
+      for (int j = 0; j < TB; ++j)
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+          if (valid[k] && t0 + j < T) x[j][k] = ld(Phi + (int64_t)(t0 + j) * stride_packs + ub + k * kThreads);
+          else
+#pragma unroll
+            for (int c = 0; c < 2 * SPT; ++c) x[j][k].v[c] = 0.f;
+        }
+#pragma unroll
+      for (int j = 0; j < TB; ++j) {
+        if (t0 + j >= T) break;  // uniform
+        float2 xs[U][SPT], xw[U][SPT];
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            xs[k][s] = make_float2(x[j][k].v[2 * s], x[j][k].v[2 * s + 1]);
+            xw[k][s] = make_float2(-x[j][k].v[2 * s + 1], x[j][k].v[2 * s]);
+          }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+          if (e < ne) {  // uniform: a tile of fewer accumulators does no work for the rest
+            const float4 c = cf[t0 + j][e];
+            const float2 cre = make_float2(c.x, c.y), cim = make_float2(c.z, c.w);
+#pragma unroll
+            for (int k = 0; k < U; ++k)
+#pragma unroll
+              for (int s = 0; s < SPT; ++s) {
+                ac[k][e][s] = __ffma2_rn(cre, xs[k][s], ac[k][e][s]);
+                ac[k][e][s] = __ffma2_rn(cim, xw[k][s], ac[k][e][s]);
+              }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (!valid[k]) continue;
+#pragma unroll
+      for (int e = 0; e < EB; ++e) {
+        if (e < ne) {
+          PK q;
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            q.v[2 * s] = ac[k][e][s].x;
+            q.v[2 * s + 1] = ac[k][e][s].y;
+          }
+          st(Q + (int64_t)(e0 + e) * stride_packs + ub + k * kThreads, q);
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ dispatch
 template <typename R, int SPT>
 static void* moment_kernel(int kind, bool csr, bool first) {
@@ -1098,6 +1199,10 @@ int launch_block_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, co
   auto pick = [&](auto eb_tag) -> void* {
     constexpr int E = decltype(eb_tag)::value;
     if (precision == TBPM_C128) return (void*)k_block_flush<double, 1, E>;
+    if constexpr (E >= 4) {  // complex64: packed FMAs
+      if (spt == 2) return (void*)k_block_flush_c64<2, E, 1, 2>;
+      return (void*)k_block_flush_c64<1, E, 1, 8>;
+    }
     if (spt == 2) return (void*)k_block_flush<float, 2, E>;
     return (void*)k_block_flush<float, 1, E>;
   };
