@@ -49,6 +49,9 @@ WORKLOADS = {
     "dense124": wl.dense_honeycomb(124),
     "dense235": wl.dense_honeycomb(235),
     "dense235_small": wl.dense_honeycomb(235, n_steps=64, L=(1024, 2048)),   # profiling case
+    "vacancy2048": wl.Workload("honeycomb2048x2048_vac1pct_W2_Nt512", wl.honeycomb(2048, 2048, t=-2.7, W=2.0,
+                                                                                 vacancy_frac=0.01, path=wl.PATH_CSR),
+                               n_states=1, n_moments=0, precision=wl.C64, n_steps=512, n_energies=16),
     "vacancy1024": wl.Workload("honeycomb1024x1024_vac1pct_W2_Nt256", wl.honeycomb(1024, 1024, t=-2.7, W=2.0,
                                                                                  vacancy_frac=0.01, path=wl.PATH_CSR),
                                n_states=1, n_moments=0, precision=wl.C64, n_steps=256, n_energies=16),

@@ -367,3 +367,13 @@ def test_unsupported_calls_and_invalid_descriptions(capi, ctx):
                              capi.request(n_states=1, n_moments=64), np.array([0.0]))
     finally:
         capi.tbpm_server_destroy(srv)
+
+
+def test_fp32_fma_peak_is_a_plausible_device_rate(capi, ctx):
+    """The measured FP32 FMA rate that the tap kernel's roofline divides by: positive for both
+    forms and below what the device's SMs could issue at 128 FP32 lanes and 3 GHz."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    scalar, packed = capi.tbpm_fp32_fma_peak(ctx)
+    bound = sms * 128 * 2 * 3.0e9 / 1e12
+    assert 0.0 < scalar < bound and 0.0 < packed < 2 * bound, (scalar, packed, bound)
