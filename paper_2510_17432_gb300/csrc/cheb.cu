@@ -828,6 +828,81 @@ __global__ void __launch_bounds__(kThreads) k_qe_flush(const void* phiv, int T, 
   }
 }
 
+// Complex64 form of k_qe_flush: the real weights C_n(E) of two energies sit in one shared quad
+// (C_e, C_e, C_{e+1}, C_{e+1}), so one broadcast load feeds one packed f32x2 FMA per state and
+// energy, (q_re, q_im) += C (x_re, x_im); each thread reads TB buffered terms before their FMAs.
+template <int SPT, int TB>
+__global__ void __launch_bounds__(kThreads, 2) k_qe_flush_c64(const void* phiv, int T, int64_t stride_packs,
+                                                              void* qev, int nE, const double* coef, int n0,
+                                                              int64_t n_units) {
+  using PK = Pack<float, SPT>;
+  constexpr int EB = kQeEB;
+  __shared__ float4 cs[kQeMaxT][EB / 2];
+  const int e0 = blockIdx.x * EB;
+  const int ne = min(EB, nE - e0);
+  for (int i = threadIdx.x; i < T * (EB / 2); i += kThreads) {
+    const int t = i / (EB / 2), e = 2 * (i - t * (EB / 2));
+    const float c0 = e < ne ? (float)coef[((int64_t)(n0 + t) * nE + e0 + e) * 2] : 0.f;  // C_n(E) is real
+    const float c1 = e + 1 < ne ? (float)coef[((int64_t)(n0 + t) * nE + e0 + e + 1) * 2] : 0.f;
+    cs[t][e / 2] = make_float4(c0, c0, c1, c1);
+  }
+  __syncthreads();
+  const PK* Phi = reinterpret_cast<const PK*>(phiv);
+  PK* Q = reinterpret_cast<PK*>(qev);
+  for (int64_t u = (int64_t)blockIdx.y * kThreads + threadIdx.x; u < n_units; u += (int64_t)gridDim.y * kThreads) {
+    float2 ac[EB][SPT];
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      PK q;
+      if (e < ne) q = ld(Q + (int64_t)(e0 + e) * stride_packs + u);
+      else
+#pragma unroll
+        for (int c = 0; c < 2 * SPT; ++c) q.v[c] = 0.f;
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) ac[e][s] = make_float2(q.v[2 * s], q.v[2 * s + 1]);
+    }
+    for (int t0 = 0; t0 < T; t0 += TB) {
+      PK x[TB];
+#pragma unroll
+      for (int j = 0; j < TB; ++j) {
+        if (t0 + j < T) x[j] = ld(Phi + (int64_t)(t0 + j) * stride_packs + u);
+        else
+#pragma unroll
+          for (int c = 0; c < 2 * SPT; ++c) x[j].v[c] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < TB; ++j) {
+        if (t0 + j >= T) break;  // uniform
+#pragma unroll
+        for (int e = 0; e < EB; e += 2) {
+          if (e < ne) {  // uniform
+            const float4 c = cs[t0 + j][e / 2];
+            const float2 c0 = make_float2(c.x, c.y), c1 = make_float2(c.z, c.w);
+#pragma unroll
+            for (int s = 0; s < SPT; ++s) {
+              const float2 xv = make_float2(x[j].v[2 * s], x[j].v[2 * s + 1]);
+              ac[e][s] = __ffma2_rn(c0, xv, ac[e][s]);
+              ac[e + 1][s] = __ffma2_rn(c1, xv, ac[e + 1][s]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      if (e < ne) {
+        PK q;
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) {
+          q.v[2 * s] = ac[e][s].x;
+          q.v[2 * s + 1] = ac[e][s].y;
+        }
+        st(Q + (int64_t)(e0 + e) * stride_packs + u, q);
+      }
+    }
+  }
+}
+
 // Buffered time-block accumulation: acc_j += sum_{t < T} c_t(j) phi_t for the open
 // accumulators of a time block, with T buffered Chebyshev vectors phi_t (consecutive state
 // blocks) and complex coefficients c_t(j) = coef[(t * nb + j) * 2 + {0, 1}] (zero once term t is
@@ -1169,8 +1244,8 @@ int launch_qe_flush(tbpm_ctx* ctx, const RecurrenceArgs& a, int precision, const
   const int ublocks = (int)std::min<int64_t>(std::min<int64_t>(want, (n_units + kThreads - 1) / kThreads), 65535);
   void* fn;
   if (precision == TBPM_C128) fn = (void*)k_qe_flush<double, 1>;
-  else if (spt == 2) fn = (void*)k_qe_flush<float, 2>;
-  else fn = (void*)k_qe_flush<float, 1>;
+  else if (spt == 2) fn = (void*)k_qe_flush_c64<2, 2>;
+  else fn = (void*)k_qe_flush_c64<1, 8>;
   int64_t stride = n_units;
   int64_t nu = n_units;
   void* args[] = {(void*)&phi, &T, &stride, &qe, &nE, (void*)&coef, &n0, &nu};
