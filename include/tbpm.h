@@ -258,6 +258,19 @@ int tbpm_lattice_taps(const tbpm_lattice* lat, int32_t* offsets, double* t);
  * and synchronises the device.  The regular library returns TBPM_EUNSUPPORTED and zero words. */
 int tbpm_debug_status(tbpm_ctx* ctx, uint64_t words[3]);
 
+/* Expiry check of the device-side bounded waits (failure detection; the paper has no
+ * counterpart).  The kernels fed by TMA copies (the register sweep, the tensor-core GEMM) wait
+ * on mbarriers for at most 2 s each; on expiry they record a code in a status word, wait
+ * (bounded) for their own copies in flight and return, so the context stays usable and the call
+ * reports TBPM_ETIMEOUT.  This call runs the register sweep's bounded wait in a one-warp kernel
+ * on the context stream and reports it through the sweep's status word:
+ *   arrive != 0   the barrier's one expected arrival happens first; returns TBPM_OK;
+ *   arrive == 0   nothing arrives and no copy is in flight; the wait gives up after budget_s
+ *                 seconds and the call returns TBPM_ETIMEOUT (the status word is cleared).
+ * Synchronises the context stream.  Errors: TBPM_EINVAL for a NULL context or a budget outside
+ * (0, 2] seconds. */
+int tbpm_wait_probe(tbpm_ctx* ctx, int arrive, double budget_s);
+
 /* Measured FP32 FMA throughput of the context's device in TFLOP/s (an FMA counts as two flops),
  * scalar FMAs and packed f32x2 FMAs: the denominator of the roofline of the FP32-issue-bound tap
  * kernel (the paper has no counterpart; it reports CPU times).  Runs about a millisecond of

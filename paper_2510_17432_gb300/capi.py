@@ -107,6 +107,7 @@ def _bind(lib):
         "tbpm_moment_pass_kind": (C.c_int, [_P, _P, C.POINTER(Request), C.POINTER(C.c_int)]),
         "tbpm_fp32_fma_peak": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "tbpm_debug_status": (C.c_int, [_P, C.POINTER(C.c_uint64)]),
+        "tbpm_wait_probe": (C.c_int, [_P, C.c_int, C.c_double]),
         "tbpm_states_export": (C.c_int, [_P, _P, C.POINTER(Request), _P, _P]),
         "tbpm_apply_hopping": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
         "tbpm_moments": (C.c_int, [_P, _P, C.POINTER(Request), _P]),
@@ -154,7 +155,7 @@ def exported_symbols():
     """Names of every entry point this binding wraps (all declared in include/tbpm.h)."""
     return ["tbpm_create", "tbpm_destroy", "tbpm_last_error", "tbpm_stream", "tbpm_sync",
             "tbpm_launch_count", "tbpm_set_fusion", "tbpm_profile", "tbpm_profile_read", "tbpm_lattice_create", "tbpm_lattice_destroy", "tbpm_lattice_info",
-            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_fp32_fma_peak", "tbpm_debug_status", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
+            "tbpm_lattice_export", "tbpm_lattice_taps", "tbpm_moment_pass_kind", "tbpm_fp32_fma_peak", "tbpm_debug_status", "tbpm_wait_probe", "tbpm_states_export", "tbpm_apply_hopping", "tbpm_moments",
             "tbpm_moments_device", "tbpm_correlation", "tbpm_correlation_device", "tbpm_dos",
             "tbpm_dos_device", "tbpm_quasi_eigenstates", "tbpm_conductivity", "tbpm_conductivity_overlap",
             "tbpm_fermi_apply",
@@ -353,6 +354,12 @@ def tbpm_debug_status(ctx, lib=None) -> list:
     words = (C.c_uint64 * 3)()
     _check((lib or load()).tbpm_debug_status(ctx, words), lib)
     return [int(w) for w in words]
+
+
+def tbpm_wait_probe(ctx, arrive: bool, budget_s: float):
+    """One-warp run of the register sweep's bounded mbarrier wait; raises
+    TbpmError(TBPM_ETIMEOUT) when nothing arrives within budget_s seconds."""
+    _check(load().tbpm_wait_probe(ctx, int(bool(arrive)), float(budget_s)))
 
 
 def decode_debug_word(word: int):

@@ -115,13 +115,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 
-// Bounded wait for the phase of the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the phase of the given parity: false once budget_ns of wall-clock time has
+// passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait_ns(uint32_t bar, uint32_t parity, uint64_t budget_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (!mbar_try(bar, parity))
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > budget_ns) return false;
   return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  return mbar_wait_ns(bar, parity, kWaitNs);
 }
 
 // 1-D bulk copy global -> shared, completion counted in bytes on the mbarrier.
@@ -558,6 +563,23 @@ __global__ void __launch_bounds__(NT_, Cfg<NT_, K_, NSLOT_>::MINB) k_sweep_momen
   if (tid == 0) *a.counter = 0u;
 }
 
+// Expiry check of the bounded wait above: one warp waits on an mbarrier of its own that expects
+// one arrival.  With `arrive`, thread 0 arrives first and the phase completes; without it nothing
+// ever arrives, no copy is in flight, and every thread's wait gives up after budget_ns.  An
+// expired wait is reported as the sweep reports one: code 1 in the caller's status word.
+__global__ void __launch_bounds__(32) k_wait_probe(int* status, uint64_t budget_ns, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(b);
+  const bool done = mbar_wait_ns(b, 0, budget_ns);
+  if (__syncthreads_or(done ? 0 : 1) && threadIdx.x == 0) atomicExch(status, 1);
+}
+
 }  // namespace sweep
 
 template <int NT, int K, int NSLOT, bool D, bool O, bool W = false>
@@ -704,3 +726,30 @@ int sweep_status(tbpm_ctx* ctx) {
 }  // namespace tbpm
 
 TBPM_DEBUG_UNIT(sweep)
+
+using namespace tbpm;
+
+// One-warp run of the register sweep's bounded mbarrier wait, reported through the sweep's status
+// word and sweep_status(): TBPM_ETIMEOUT when the wait expired.
+extern "C" int tbpm_wait_probe(tbpm_ctx* ctx, int arrive, double budget_s) {
+  clear_error();
+  if (!ctx) {
+    set_error("tbpm_wait_probe: NULL context");
+    return TBPM_EINVAL;
+  }
+  if (!(budget_s > 0.0 && budget_s <= 2.0)) {
+    set_error("tbpm_wait_probe: budget %g s outside (0, 2]", budget_s);
+    return TBPM_EINVAL;
+  }
+  if (ctx->pinned_cap < 256) {
+    set_error("context has no pinned status word");
+    return TBPM_ECUDA;
+  }
+  TBPM_CK(cudaSetDevice(ctx->device));
+  int* status = reinterpret_cast<int*>(ctx->pinned + kSweepStatusSlot);
+  const uint64_t budget_ns = (uint64_t)(budget_s * 1e9);
+  sweep::k_wait_probe<<<1, 32, 0, ctx->stream>>>(status, budget_ns, arrive ? 1 : 0);
+  TBPM_CK_LAUNCH(ctx);
+  TBPM_CK(cudaStreamSynchronize(ctx->stream));
+  return sweep_status(ctx);
+}
