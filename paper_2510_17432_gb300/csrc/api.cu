@@ -56,6 +56,8 @@ static cudaEvent_t take_event(tbpm_ctx* ctx) {
 }
 
 int phase_begin(tbpm_ctx* ctx, int kind) {
+  static const char* const kNames[3] = {"recurrence", "reconstruction", "fused passes"};
+  ctx->nvtx_open.push_back(nvtxRangeStartA(kNames[kind >= 0 && kind < 3 ? kind : 0]));
   if (!ctx->profiling) return -1;
   tbpm_ctx::Phase ph;
   ph.a = take_event(ctx);
@@ -68,6 +70,10 @@ int phase_begin(tbpm_ctx* ctx, int kind) {
 }
 
 void phase_end(tbpm_ctx* ctx, int token) {
+  if (!ctx->nvtx_open.empty()) {
+    nvtxRangeEnd(ctx->nvtx_open.back());
+    ctx->nvtx_open.pop_back();
+  }
   if (token < 0 || token >= (int)ctx->phases.size()) return;
   tbpm_ctx::Phase& ph = ctx->phases[token];
   ph.launches = ctx->launches - ph.launches;
@@ -826,6 +832,7 @@ extern "C" {
 
 int tbpm_lattice_create(tbpm_ctx* ctx, const tbpm_lattice_desc* desc, tbpm_lattice** out) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !desc || !out) {
     set_error("tbpm_lattice_create: NULL argument");
     return TBPM_EINVAL;
@@ -2238,6 +2245,7 @@ int tbpm_moment_pass_kind(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_r
 
 int tbpm_moments_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_mu) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !d_mu) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2255,6 +2263,7 @@ int tbpm_moments_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_req
 
 int tbpm_moments(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* mu) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !mu) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2273,6 +2282,7 @@ int tbpm_moments(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* r
 
 int tbpm_correlation_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* d_C) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !d_C) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2290,6 +2300,7 @@ int tbpm_correlation_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm
 
 int tbpm_correlation(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double* C) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !C) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2313,6 +2324,7 @@ int tbpm_correlation(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reques
 int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* d_E,
                     int64_t nE, double* d_D) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !d_E || !d_D) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2327,6 +2339,7 @@ int tbpm_dos_device(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request
 int tbpm_dos(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* energies,
              int64_t nE, double* D) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !energies || !D) {
     set_error("NULL argument");
     return TBPM_EINVAL;
@@ -2396,6 +2409,7 @@ int tbpm_apply_hopping(tbpm_ctx* ctx, const tbpm_lattice* lat_c, int precision, 
 int tbpm_block_autotune(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int64_t n_steps,
                         int64_t* b_opt, double times_ms[2]) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !lat_c || !req || !b_opt || n_steps < 1) {
     set_error("tbpm_block_autotune: invalid argument");
     return TBPM_EINVAL;
@@ -2416,6 +2430,7 @@ int tbpm_block_autotune(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_req
 int tbpm_quasi_eigenstates(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double* energies,
                            int64_t nE, void* out) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !energies || !out || nE < 1) {
     set_error("tbpm_quasi_eigenstates: invalid argument");
     return TBPM_EINVAL;
@@ -2445,6 +2460,7 @@ int tbpm_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
 int tbpm_conductivity_overlap(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, int direction,
                               const double* energies, int64_t nE, double* C, double* sigma, double* overlap) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !energies || !sigma || nE < 1 || nE > 4096) {
     set_error("tbpm_conductivity: invalid argument");
     return TBPM_EINVAL;
@@ -2474,6 +2490,7 @@ int tbpm_conductivity_overlap(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tb
 int tbpm_fermi_apply(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double mu, double kT,
                      int sqrt_f, void* out) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !out) {
     set_error("tbpm_fermi_apply: invalid argument");
     return TBPM_EINVAL;
@@ -2539,6 +2556,7 @@ int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tb
                               int beta, double mu, double kT, double omega_max, int64_t n_omega, double* C,
                               double* sigma) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !req || !sigma || n_omega < 2 || n_omega > (1 << 20) || !(omega_max > 0.0)) {
     set_error("tbpm_optical_conductivity: invalid argument (n_omega in [2, 2^20], omega_max > 0)");
     return TBPM_EINVAL;
@@ -2580,6 +2598,7 @@ int tbpm_optical_conductivity(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tb
 int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, const double q[3], double mu,
                       double kT, const double* omegas, int64_t n_omega, double* C, double* Pi) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !req || !q || !omegas || !Pi || n_omega < 1 || n_omega > (1 << 20)) {
     set_error("tbpm_polarization: invalid argument");
     return TBPM_EINVAL;
@@ -2612,6 +2631,7 @@ int tbpm_polarization(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_reque
 int tbpm_charge_density(tbpm_ctx* ctx, const tbpm_lattice* lat_c, const tbpm_request* req, double mu, double kT,
                         double* rho) {
   clear_error();
+  TBPM_NVTX_CALL(ctx);
   if (!ctx || !req || !rho) {
     set_error("tbpm_charge_density: invalid argument");
     return TBPM_EINVAL;

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -230,6 +231,9 @@ struct tbpm_ctx {
   };
   std::vector<Phase> phases;
   std::vector<cudaEvent_t> event_pool;
+  // NVTX phase ranges open on this context, innermost last (closed by phase_end, or by the
+  // public call's NvtxCall when an error path skipped phase_end)
+  std::vector<nvtxRangeId_t> nvtx_open;
 };
 
 // One piece of a column run of long-range taps for the matrix-free tap kernel: the taps
@@ -277,9 +281,29 @@ namespace tbpm {
 // grow-only device workspace on the context stream
 int ensure(tbpm_ctx* ctx, DevBuf& b, size_t bytes);
 
-// phase timing: begin returns a token (-1 when profiling is off); end closes it
+// phase timing: begin returns a token (-1 when profiling is off); end closes it.  Both also open
+// and close an NVTX range named after the phase, whether or not profiling is on.
 int phase_begin(tbpm_ctx* ctx, int kind);
 void phase_end(tbpm_ctx* ctx, int token);
+
+// NVTX range over the scope of a public call, named after it, on the calling thread; phase
+// ranges opened inside the call and left open by an error return are closed with it.  NVTX
+// calls do nothing unless a profiler (ncu, nsys) has attached its handler.
+struct NvtxCall {
+  tbpm_ctx* ctx;
+  size_t depth;
+  NvtxCall(tbpm_ctx* c, const char* name) : ctx(c), depth(c ? c->nvtx_open.size() : 0) { nvtxRangePushA(name); }
+  ~NvtxCall() {
+    while (ctx && ctx->nvtx_open.size() > depth) {
+      nvtxRangeEnd(ctx->nvtx_open.back());
+      ctx->nvtx_open.pop_back();
+    }
+    nvtxRangePop();
+  }
+  NvtxCall(const NvtxCall&) = delete;
+  NvtxCall& operator=(const NvtxCall&) = delete;
+};
+#define TBPM_NVTX_CALL(ctx) ::tbpm::NvtxCall tbpm_nvtx_call_((ctx), __func__)
 
 // ------------------------------------------------------------------ launch plumbing
 struct RecurrenceArgs {
