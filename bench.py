@@ -889,7 +889,7 @@ def run_state_based(args, work):
     value = whole_job_rate(c64["concurrent_s"]["site_updates_per_s"], world, 1.0)
     roofline = {"bound": "hbm", "achieved": c64["concurrent_s"]["algorithmic_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": c64["concurrent_s"]["frac_of_hbm"], "traffic": None, "peak_source": peak_kind,
-                "kernel": ("k_accum_step (ELL recurrence into buffer slots) + k_block_flush, complex64"
+                "kernel": ("k_ell_step (ELL recurrence into buffer slots) + k_block_flush_c64 (packed flush), complex64"
                            if c64["concurrent_s"]["b"] >= 2 else "k_accum_step (ELL, complex64, time-block accumulation)"),
                 "bytes_model": ("buffered blocks: per step phi_n, phi_{n-1}, phi_{n+1}, 4z B ELL + D_i per site; per "
                                 "window of <= 32 terms each slot read once per 16 accumulators and each accumulator "
