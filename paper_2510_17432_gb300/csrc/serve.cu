@@ -1,4 +1,4 @@
-// Serving: continuous batching of DOS / LDOS requests into one persistent kernel per step.
+// Serving: continuous batching of DOS / LDOS requests, one kernel launch per Chebyshev step.
 //
 // A scheduler thread admits queued requests by their HBM footprint, keeps their state blocks
 // resident, and advances every active request by one Chebyshev step (moment-based form with
