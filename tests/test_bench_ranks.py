@@ -73,3 +73,30 @@ def test_state_based_schedule_matches_table_one_counts():
         assert len(passes) == c["amxsy"]
         assert apps == c["amxsy"] - blocks
         assert sum(p[0] for p in passes) == c["axpy"]
+
+
+def test_byte_models_of_the_two_forms():
+    """The state-block crossings behind the bench line's HBM fractions and byte ratio.  Moment form:
+    the initial state is written once, the first one-step pass reads phi_0 and writes phi_1, every
+    further one-step pass reads two blocks and writes one, and a four-step pass reads two and writes
+    two in place of four one-step passes (8 crossings saved each).  Sequential form, per time step:
+    each four-term window pass reads two blocks and writes four in place of four one-step passes
+    (6 saved each).  Benchmark figures: M = 4096 moments (2048 steps) and N_t = 1254 steps of
+    N(pi) = 20 terms give 2,056 and 76,494 crossings."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import bessel
+    import math
+    for M in (8, 10, 64, 4096, 8192):
+        steps = (M + (M & 1)) // 2
+        assert bench.concurrent_m_blocks(M, False) == 3 * steps
+        assert bench.concurrent_m_blocks(M, True) == 3 * steps - 8 * ((steps - 1) // 4)
+    for n_terms in (2, 5, 6, 20, 33):
+        plain = bench.sequential_step_blocks(n_terms, False)
+        assert plain == 5 + 3 * (n_terms - 2) + n_terms + 6
+        windows = max(0, (n_terms - 2) // 4)  # terms 2.. in fours while four more fit below n_terms
+        assert bench.sequential_step_blocks(n_terms, True) == plain - 6 * windows
+    n_pi = bessel.truncation_order(math.pi)
+    assert n_pi == 20
+    assert bench.concurrent_m_blocks(4096, True) == 2056
+    assert 1254 * bench.sequential_step_blocks(n_pi, True) == 76494
