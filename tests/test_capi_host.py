@@ -75,3 +75,27 @@ def test_block_opt_matches_oracle(capi):
 def test_invalid_arguments_fail_cleanly(capi):
     with pytest.raises(capi.TbpmError):
         capi.tbpm_block_counts(0, 1, math.pi)
+
+
+def test_plain_c_caller(capi, tmp_path):
+    """The header is strict C99 (pedantic, warnings as errors) and a C program linked against
+    libtbpm.so gets the oracle's truncation orders, Tab. I counts and b_opt, and status codes
+    (never a crash) for invalid arguments, all without a GPU."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not found")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.join(root, "paper_2510_17432_gb300")
+    exe = str(tmp_path / "c_abi_check")
+    subprocess.run(["gcc", "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(root, "include"), "-o", exe, os.path.join(root, "tests", "c_abi_check.c"),
+                    "-L", libdir, "-ltbpm", f"-Wl,-rpath,{libdir}", "-lm"], check=True, capture_output=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = {ln.split()[0]: ln.split()[1:] for ln in r.stdout.splitlines()}
+    assert [int(v) for v in out["truncation"]] == [bessel.truncation_order(k * math.pi) for k in (1, 4, 100)]
+    want = cost.block_counts(2048, 40, math.pi)
+    assert [int(v) for v in out["counts"]] == [want["amxsy"], want["axpy"], want["dot"]]
+    assert int(out["bopt"][0]) == cost.b_opt(2048, 1.0, 0.05, b_max=256)
+    assert out["errors"] == ["ok"]
