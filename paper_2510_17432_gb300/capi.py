@@ -177,6 +177,14 @@ def _host_ptr(a: np.ndarray | None):
     return a.ctypes.data_as(C.c_void_p)
 
 
+def _out_ptr(a: np.ndarray | None, needed: int, what: str):
+    """Host pointer of an output buffer that the library fills with `needed` bytes; a buffer
+    too small for them is refused here, before the library could write past its end."""
+    if a is not None and a.nbytes < needed:
+        raise ValueError(f"{what}: the buffer holds {a.nbytes} bytes, the request writes {needed}")
+    return _host_ptr(a)
+
+
 def _dev_ptr(t):
     if t is None:
         return None
@@ -306,7 +314,10 @@ def tbpm_apply_hopping(ctx, lat, precision: int, n_states: int, x: np.ndarray, y
 
 
 def tbpm_moments(ctx, lat, req: Request, mu: np.ndarray):
-    _check(load().tbpm_moments(ctx, lat, C.byref(req), _host_ptr(mu)))
+    """mu: [S][M][2] float64 (re, im)."""
+    S, M = int(req.n_states), int(req.n_moments)
+    need = 16 * S * M if 1 <= S <= 32 and M >= 2 and M % 2 == 0 else 0  # else the library refuses
+    _check(load().tbpm_moments(ctx, lat, C.byref(req), _out_ptr(mu, need, "tbpm_moments")))
 
 
 def tbpm_moments_device(ctx, lat, req: Request, d_mu):
@@ -314,7 +325,10 @@ def tbpm_moments_device(ctx, lat, req: Request, d_mu):
 
 
 def tbpm_correlation(ctx, lat, req: Request, Cout: np.ndarray):
-    _check(load().tbpm_correlation(ctx, lat, C.byref(req), _host_ptr(Cout)))
+    """Cout: [S][N_t+1][2] float64 (or [S][N_t+1] complex128)."""
+    S, Nt = int(req.n_states), int(req.n_steps)
+    need = 16 * S * (Nt + 1) if 1 <= S <= 32 and Nt >= 1 else 0
+    _check(load().tbpm_correlation(ctx, lat, C.byref(req), _out_ptr(Cout, need, "tbpm_correlation")))
 
 
 def tbpm_correlation_device(ctx, lat, req: Request, d_C):
@@ -322,7 +336,11 @@ def tbpm_correlation_device(ctx, lat, req: Request, d_C):
 
 
 def tbpm_dos(ctx, lat, req: Request, energies: np.ndarray, D: np.ndarray):
-    _check(load().tbpm_dos(ctx, lat, C.byref(req), _host_ptr(energies), int(energies.size), _host_ptr(D)))
+    """energies: [n_energies] float64 (converted if needed); D: [S][n_energies] float64."""
+    e = np.ascontiguousarray(energies, dtype=np.float64)  # no copy for a float64 C-ordered array
+    S = int(req.n_states)
+    need = 8 * S * e.size if 1 <= S <= 32 else 0
+    _check(load().tbpm_dos(ctx, lat, C.byref(req), _host_ptr(e), int(e.size), _out_ptr(D, need, "tbpm_dos")))
 
 
 def tbpm_dos_device(ctx, lat, req: Request, d_energies, n_energies: int, d_D):

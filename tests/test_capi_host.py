@@ -99,3 +99,28 @@ def test_plain_c_caller(capi, tmp_path):
     assert [int(v) for v in out["counts"]] == [want["amxsy"], want["axpy"], want["dot"]]
     assert int(out["bopt"][0]) == cost.b_opt(2048, 1.0, 0.05, b_max=256)
     assert out["errors"] == ["ok"]
+
+
+def test_binding_refuses_output_buffers_too_small(capi):
+    """The binding checks that a host output buffer holds what the request writes before it
+    passes the pointer on; a buffer of the right size reaches the library (here it answers
+    TBPM_EINVAL for the NULL context, with no GPU involved)."""
+    import numpy as np
+    req = capi.request(n_states=4, n_moments=64)
+    with pytest.raises(ValueError, match="tbpm_moments"):
+        capi.tbpm_moments(None, None, req, np.zeros((4, 64)))          # [S][M] instead of [S][M][2]
+    with pytest.raises(capi.TbpmError):
+        capi.tbpm_moments(None, None, req, np.zeros((4, 64, 2)))
+    creq = capi.request(n_states=2, n_steps=10)
+    with pytest.raises(ValueError, match="tbpm_correlation"):
+        capi.tbpm_correlation(None, None, creq, np.zeros((2, 10, 2)))   # N_t entries instead of N_t + 1
+    with pytest.raises(capi.TbpmError):
+        capi.tbpm_correlation(None, None, creq, np.zeros((2, 11), np.complex128))
+    E = np.linspace(-1.0, 1.0, 16)
+    with pytest.raises(ValueError, match="tbpm_dos"):
+        capi.tbpm_dos(None, None, req, E, np.zeros(16))                 # one state's worth for four
+    with pytest.raises(capi.TbpmError):
+        capi.tbpm_dos(None, None, req, E.astype(np.float32), np.zeros((4, 16)))
+    # invalid requests are left to the library, which refuses them before writing anything
+    with pytest.raises(capi.TbpmError):
+        capi.tbpm_moments(None, None, capi.request(n_states=33, n_moments=8), np.zeros((1, 8, 2)))
